@@ -1,0 +1,494 @@
+/*
+ * Plain FP64 CPU oracle for the per-cell chemistry integrator.
+ *
+ * TEST INFRASTRUCTURE ONLY.  The test suite, the smoke check and the CPU-baseline leg
+ * of the benchmark call this library; the GPU product path never does, and this file
+ * shares no code, header or table with it.  It is written to be checked by eye
+ * against the paper, not to be fast: scalar loops, library exp/log/pow, no reordering.
+ *
+ * Each cell is a constant-density, constant-internal-energy adiabatic reactor: the
+ * chemical source term of Eq. 14 changes only the partial densities, so rho and e
+ * stay fixed while the mass fractions Y_k evolve.  What is computed:
+ *   - species thermo from NASA-7 tables, and the mixture internal energy of Eq. 10;
+ *   - temperature from (e, Y) by Newton-Raphson (the calculate_T kernel of Table 1),
+ *     with a bisection fallback;
+ *   - molar production rates by the law of mass action (Eq. 15-16), Arrhenius
+ *     forward rates and reverse rates from the equilibrium constant (Sec. 2.1.2),
+ *     plus third-body and Troe fall-off reactions;
+ *   - the five-stage fourth-order low-storage RK of Eq. 21 (two registers U, X plus
+ *     the error register of the embedded third-order scheme, Sec. 2.2.3), with the
+ *     RK4(3)5[2R+]C coefficients of the paper's ref. [37];
+ *   - the WRMS step-size controller of Eq. 22.
+ *
+ * Readings where the paper is silent (all documented with the design):
+ *   integrated variables are the 9 mass fractions at fixed rho, e; the WRMS norm runs
+ *   over them with |u_i| = max(|y_n,i|, |y_n+1,i|); h_max / h_min of Eq. 22 act as
+ *   growth / shrink factors 5 and 1/5; a step is accepted iff ||e|| <= 1; h0 = dt;
+ *   h is clipped to land on dt; the loop ends when dt - t <= 1e-12 dt; at most
+ *   max_steps attempts, h < 1e-15 dt is an underflow; concentrations are clamped at
+ *   zero inside the rate evaluation only; Newton stops at |dT| <= 1e-12 T within 30
+ *   iterations, then bisects on [200, 6000] K; a trial stage with no temperature root
+ *   or a non-finite error estimate rejects the attempt with the factor 1/5, while no
+ *   root at the accepted state ends the cell (status 3).
+ * Units are SI: kg/mol, J/mol, mol/m^3, Pa, s.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_MAXSP 16
+#define OR_MAXRX 64
+#define OR_NEL 3
+
+static const double R_U = 8.31446261815324;  /* J/(mol K) */
+static const double P_REF = 101325.0;        /* Pa, standard state of the equilibrium constant */
+
+/* The mechanism, as marshalled by the Python side of the oracle. */
+typedef struct {
+  int32_t nsp, nrx;
+  double W[OR_MAXSP];                 /* molar mass, kg/mol */
+  int32_t ncomp[OR_MAXSP][OR_NEL];    /* element counts H, O, N */
+  double Tmid[OR_MAXSP];              /* NASA-7 range switch */
+  double alo[OR_MAXSP][7];            /* NASA-7 coefficients below Tmid */
+  double ahi[OR_MAXSP][7];            /* NASA-7 coefficients at and above Tmid */
+  int32_t rtype[OR_MAXRX];            /* 0 elementary, 1 third body, 2 fall-off */
+  int32_t nuf[OR_MAXRX][OR_MAXSP];    /* reactant stoichiometric coefficients */
+  int32_t nur[OR_MAXRX][OR_MAXSP];    /* product stoichiometric coefficients */
+  double A[OR_MAXRX], b[OR_MAXRX], Ea[OR_MAXRX];     /* Arrhenius (high-pressure limit) */
+  double A0[OR_MAXRX], b0[OR_MAXRX], Ea0[OR_MAXRX];  /* low-pressure limit (fall-off) */
+  double troe[OR_MAXRX][4];           /* alpha, T***, T*, T** */
+  int32_t troe_n[OR_MAXRX];           /* 0 Lindemann, 3 or 4 Troe parameters */
+  double eff[OR_MAXRX][OR_MAXSP];     /* third-body efficiencies */
+  int32_t reversible[OR_MAXRX];
+} omech;
+
+/* ------------------------------------------------------------------ thermo (Eq. 10) */
+
+static const double *nasa(const omech *m, int k, double T) {
+  return (T < m->Tmid[k]) ? m->alo[k] : m->ahi[k];
+}
+
+/* cp/R = a1 + a2 T + a3 T^2 + a4 T^3 + a5 T^4 */
+double oracle_cp_R(const omech *m, int k, double T) {
+  const double *a = nasa(m, k, T);
+  return a[0] + a[1] * T + a[2] * T * T + a[3] * T * T * T + a[4] * T * T * T * T;
+}
+
+/* h/(RT) = a1 + a2 T/2 + a3 T^2/3 + a4 T^3/4 + a5 T^4/5 + a6/T */
+double oracle_h_RT(const omech *m, int k, double T) {
+  const double *a = nasa(m, k, T);
+  return a[0] + a[1] * T / 2.0 + a[2] * T * T / 3.0 + a[3] * T * T * T / 4.0 +
+         a[4] * T * T * T * T / 5.0 + a[5] / T;
+}
+
+/* s/R = a1 ln T + a2 T + a3 T^2/2 + a4 T^3/3 + a5 T^4/4 + a7  (at P_REF) */
+double oracle_s_R(const omech *m, int k, double T) {
+  const double *a = nasa(m, k, T);
+  return a[0] * log(T) + a[1] * T + a[2] * T * T / 2.0 + a[3] * T * T * T / 3.0 +
+         a[4] * T * T * T * T / 4.0 + a[6];
+}
+
+/* Mixture specific internal energy, J/kg: e = sum_k Y_k (h_k - R_u T) / W_k (Eq. 10
+ * with p/rho = R_u T sum_k Y_k/W_k). */
+double oracle_e_mix(const omech *m, const double *Y, double T) {
+  double e = 0.0;
+  for (int k = 0; k < m->nsp; ++k)
+    e += Y[k] * (oracle_h_RT(m, k, T) * R_U * T - R_U * T) / m->W[k];
+  return e;
+}
+
+/* Mixture specific heat at constant volume, J/(kg K): sum_k Y_k (cp_k - R_u) / W_k */
+double oracle_cv_mix(const omech *m, const double *Y, double T) {
+  double cv = 0.0;
+  for (int k = 0; k < m->nsp; ++k)
+    cv += Y[k] * (oracle_cp_R(m, k, T) * R_U - R_U) / m->W[k];
+  return cv;
+}
+
+/* T from (e, Y) by bisection on [200, 6000] K.  Returns 0 on success. */
+int oracle_T_from_e_bisect(const omech *m, const double *Y, double e, double *T_out) {
+  double lo = 200.0, hi = 6000.0;
+  if (oracle_e_mix(m, Y, lo) - e > 0.0 || oracle_e_mix(m, Y, hi) - e < 0.0) return 3;
+  for (int it = 0; it < 200 && hi - lo > 1e-13 * hi; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (oracle_e_mix(m, Y, mid) - e > 0.0) hi = mid; else lo = mid;
+  }
+  *T_out = 0.5 * (lo + hi);
+  return 0;
+}
+
+/* T from (e, Y) by Newton-Raphson, T <- T - (e(T) - e) / cv(T), started from Tguess
+ * (1500 K when Tguess is not a positive finite number).  Stops when |dT| <= 1e-12 T;
+ * after 30 iterations, or on a non-positive or non-finite iterate, falls back to
+ * bisection.  Returns 0 on success, 3 on failure. */
+int oracle_T_from_e(const omech *m, const double *Y, double e, double Tguess, double *T_out,
+                    int32_t *iters) {
+  double T = (isfinite(Tguess) && Tguess > 0.0) ? Tguess : 1500.0;
+  for (int it = 1; it <= 30; ++it) {
+    double f = oracle_e_mix(m, Y, T) - e;
+    double d = oracle_cv_mix(m, Y, T);
+    double dT = f / d;
+    T = T - dT;
+    if (!isfinite(T) || T <= 0.0) break;
+    if (fabs(dT) <= 1e-12 * fabs(T)) {
+      *T_out = T;
+      if (iters) *iters = it;
+      return 0;
+    }
+  }
+  if (iters) *iters = -1;
+  return oracle_T_from_e_bisect(m, Y, e, T_out);
+}
+
+/* ---------------------------------------------------------- kinetics (Eq. 15-16) */
+
+static double ipow(double x, int n) {
+  double r = 1.0;
+  for (int i = 0; i < n; ++i) r *= x;
+  return r;
+}
+
+/* Third-body concentration of reaction j: [M] = sum_k eff_jk c_k */
+static double third_body(const omech *m, int j, const double *c) {
+  double M = 0.0;
+  for (int k = 0; k < m->nsp; ++k) M += m->eff[j][k] * c[k];
+  return M;
+}
+
+/* Troe broadening factor F(Pr, T) (Gilbert, Luther & Troe 1983); 1 for Lindemann. */
+double oracle_troe_F(const omech *m, int j, double T, double Pr) {
+  if (m->troe_n[j] == 0) return 1.0;
+  const double *p = m->troe[j];
+  double Fcent = (1.0 - p[0]) * exp(-T / p[1]) + p[0] * exp(-T / p[2]);
+  if (m->troe_n[j] == 4) Fcent += exp(-p[3] / T);
+  double logFc = log10(Fcent);
+  double cc = -0.4 - 0.67 * logFc;
+  double nn = 0.75 - 1.27 * logFc;
+  double x = log10(Pr) + cc;
+  double f1 = x / (nn - 0.14 * x);
+  double logF = logFc / (1.0 + f1 * f1);
+  return pow(10.0, logF);
+}
+
+/* Forward and reverse rate coefficients of every reaction at T, given the clamped
+ * concentrations c (needed for the fall-off pressure dependence).
+ * Forward: k = A T^b exp(-Ea/(R_u T)); for fall-off, k = k_inf Pr/(1+Pr) F with
+ * Pr = k0 [M] / k_inf.  Reverse: k_r = k_f / K_c with
+ * K_c = exp(-sum_k nu_jk g_k/(R_u T)) (P_REF/(R_u T))^(sum_k nu_jk), nu = nu'' - nu'. */
+void oracle_rate_constants(const omech *m, double T, const double *c, double *kf, double *kr) {
+  double g[OR_MAXSP];
+  for (int k = 0; k < m->nsp; ++k) g[k] = oracle_h_RT(m, k, T) - oracle_s_R(m, k, T);
+  for (int j = 0; j < m->nrx; ++j) {
+    double k_inf = m->A[j] * pow(T, m->b[j]) * exp(-m->Ea[j] / (R_U * T));
+    double k = k_inf;
+    if (m->rtype[j] == 2) {
+      double k0 = m->A0[j] * pow(T, m->b0[j]) * exp(-m->Ea0[j] / (R_U * T));
+      double Pr = k0 * third_body(m, j, c) / k_inf;
+      k = (Pr > 0.0) ? k_inf * (Pr / (1.0 + Pr)) * oracle_troe_F(m, j, T, Pr) : 0.0;
+    }
+    kf[j] = k;
+    double dG = 0.0;
+    int dnu = 0;
+    for (int s = 0; s < m->nsp; ++s) {
+      int nu = m->nur[j][s] - m->nuf[j][s];
+      dG += nu * g[s];
+      dnu += nu;
+    }
+    double Kc = exp(-dG) * pow(P_REF / (R_U * T), (double)dnu);
+    kr[j] = m->reversible[j] ? k / Kc : 0.0;
+  }
+}
+
+/* Forward and reverse rates of progress (mol/m^3/s) of every reaction:
+ * q_f = k_f prod c^nu', q_r = k_r prod c^nu'', both times [M] for third-body reactions. */
+void oracle_progress(const omech *m, double rho, double T, const double *Y, double *qf, double *qr) {
+  double c[OR_MAXSP], kf[OR_MAXRX], kr[OR_MAXRX];
+  for (int k = 0; k < m->nsp; ++k) {
+    double ck = rho * Y[k] / m->W[k];
+    c[k] = ck > 0.0 ? ck : 0.0;
+  }
+  oracle_rate_constants(m, T, c, kf, kr);
+  for (int j = 0; j < m->nrx; ++j) {
+    double f = kf[j], r = kr[j];
+    for (int k = 0; k < m->nsp; ++k) {
+      f *= ipow(c[k], m->nuf[j][k]);
+      r *= ipow(c[k], m->nur[j][k]);
+    }
+    if (m->rtype[j] == 1) {
+      double M = third_body(m, j, c);
+      f *= M;
+      r *= M;
+    }
+    qf[j] = f;
+    qr[j] = r;
+  }
+}
+
+/* Molar production rates (Eq. 16): wdot_k = sum_j (nu''_jk - nu'_jk) (q_f,j - q_r,j). */
+void oracle_wdot(const omech *m, double rho, double T, const double *Y, double *wdot) {
+  double qf[OR_MAXRX], qr[OR_MAXRX];
+  oracle_progress(m, rho, T, Y, qf, qr);
+  for (int k = 0; k < m->nsp; ++k) wdot[k] = 0.0;
+  for (int j = 0; j < m->nrx; ++j)
+    for (int k = 0; k < m->nsp; ++k)
+      wdot[k] += (double)(m->nur[j][k] - m->nuf[j][k]) * (qf[j] - qr[j]);
+}
+
+/* Conserved state from (T, p, Y): rho = p Wbar / (R_u T), e = e(T, Y). */
+void oracle_state_from_TPY(const omech *m, int64_t n, const double *T, const double *p,
+                           const double *Y, int64_t ld, double *rho, double *e) {
+  for (int64_t i = 0; i < n; ++i) {
+    double y[OR_MAXSP], inv_w = 0.0;
+    for (int k = 0; k < m->nsp; ++k) {
+      y[k] = Y[k * ld + i];
+      inv_w += y[k] / m->W[k];
+    }
+    rho[i] = p[i] / (R_U * T[i] * inv_w);
+    e[i] = oracle_e_mix(m, y, T[i]);
+  }
+}
+
+/* ------------------------------------------- low-storage RK (Eq. 21) and control */
+
+/* RK4(3)5[2R+]C of the paper's ref. [37]: sub-diagonal a_{i+1,i}, weights b and the
+ * embedded third-order weights bhat.  All other a_{i,j} (j < i-1) equal b_j. */
+static const double LS_A[4] = {
+    970286171893.0 / 4311952581923.0, 6584761158862.0 / 12103376702013.0,
+    2251764453980.0 / 15575788980749.0, 26877169314380.0 / 34165994151039.0};
+static const double LS_B[5] = {
+    1153189308089.0 / 22510343858157.0, 1772645290293.0 / 4653164025191.0,
+    -1672844663538.0 / 4480602732383.0, 2114624349019.0 / 3568978502595.0,
+    5198255086312.0 / 14908931495163.0};
+static const double LS_BH[5] = {
+    1016888040809.0 / 7410784769900.0, 11231460423587.0 / 58533540763752.0,
+    -1563879915014.0 / 6823010717585.0, 606302364029.0 / 971179775848.0,
+    1097981568119.0 / 3980877426909.0};
+
+void oracle_lsrk_coefficients(double *a, double *b, double *bh) {
+  for (int i = 0; i < 4; ++i) a[i] = LS_A[i];
+  for (int i = 0; i < 5; ++i) { b[i] = LS_B[i]; bh[i] = LS_BH[i]; }
+}
+
+#define OR_MAXN 32
+typedef int (*rhs_fn)(void *ctx, const double *y, double *f);
+
+/* One step of Eq. 21 from X (overwritten with y_n+1).  Register 1 holds U (the stage
+ * input), register 2 holds X; F is the stage derivative; E accumulates the embedded
+ * error sum_i (b_i - bhat_i) h F_i.  Returns 0, or the 1-based stage whose RHS failed. */
+static int lsrk_step(int n, rhs_fn f, void *ctx, double h, double *X, double *E) {
+  double U[OR_MAXN], F[OR_MAXN];
+  for (int i = 0; i < n; ++i) { U[i] = X[i]; E[i] = 0.0; }
+  for (int s = 0; s < 5; ++s) {
+    if (f(ctx, U, F)) return s + 1;
+    for (int i = 0; i < n; ++i) E[i] += (LS_B[s] - LS_BH[s]) * h * F[i];
+    double a = (s < 4) ? LS_A[s] : 0.0;
+    for (int i = 0; i < n; ++i) {
+      U[i] = X[i] + a * h * F[i];               /* register 1 */
+      X[i] = U[i] + (LS_B[s] - a) * h * F[i];   /* register 2 */
+    }
+  }
+  return 0;
+}
+
+/* WRMS error of Eq. 22 over n components, |u_i| = max(|y_n,i|, |y_n+1,i|). */
+static double wrms(int n, const double *E, const double *Xold, const double *Xnew, double rtol,
+                   double atol) {
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double u = fmax(fabs(Xold[i]), fabs(Xnew[i]));
+    double w = E[i] / (rtol * u + atol);
+    s += w * w;
+  }
+  return sqrt(s / n);
+}
+
+typedef struct {
+  int32_t status, nacc, nrej;
+  double margin; /* min over attempted steps of |err - 1| */
+} adapt_out;
+
+/* Adaptive integration of y' = f(y) over [0, dt] with the Eq. 22 controller.
+ * Optional logs (h, err, accepted) of every attempted step. */
+static void integrate_adaptive(int n, rhs_fn f, void *ctx, double dt, double rtol, double atol,
+                               double h0, int32_t max_steps, double *X, adapt_out *out,
+                               double *log_h, double *log_err, int32_t *log_acc, int32_t max_log) {
+  double t = 0.0, h = (h0 > 0.0) ? h0 : dt;
+  double Xs[OR_MAXN], E[OR_MAXN];
+  out->status = 0; out->nacc = 0; out->nrej = 0; out->margin = INFINITY;
+  while (dt - t > 1e-12 * dt) {
+    if (out->nacc + out->nrej >= max_steps) { out->status = 1; break; }
+    if (h < 1e-15 * dt) { out->status = 2; break; }
+    if (h > dt - t) h = dt - t;
+    for (int i = 0; i < n; ++i) Xs[i] = X[i];
+    int k = out->nacc + out->nrej;
+    /* A trial stage (2..5) whose RHS fails (no temperature root) or an error estimate
+     * that is not finite rejects the attempt with the smallest factor 1/5; a failure
+     * at stage 1, the accepted state itself, ends the cell with status 3. */
+    int failed = lsrk_step(n, f, ctx, h, X, E);
+    if (failed == 1) {
+      for (int i = 0; i < n; ++i) X[i] = Xs[i];
+      out->status = 3;
+      break;
+    }
+    double err = failed ? NAN : wrms(n, E, Xs, X, rtol, atol);
+    if (!isfinite(err)) {
+      for (int i = 0; i < n; ++i) X[i] = Xs[i];
+      if (k < max_log) { log_h[k] = h; log_err[k] = err; log_acc[k] = 0; }
+      out->nrej++;
+      h = h * 0.2;
+      continue;
+    }
+    double fac = (err == 0.0) ? 5.0 : fmin(5.0, fmax(0.2, 0.9 * pow(1.0 / err, 0.25)));
+    if (k < max_log) { log_h[k] = h; log_err[k] = err; log_acc[k] = err <= 1.0; }
+    if (fabs(err - 1.0) < out->margin) out->margin = fabs(err - 1.0);
+    if (err <= 1.0) {
+      t += h;
+      out->nacc++;
+    } else {
+      for (int i = 0; i < n; ++i) X[i] = Xs[i];
+      out->nrej++;
+    }
+    h = h * fac;
+  }
+}
+
+/* ------------------------------------------------------------ test problems */
+
+typedef struct { int n; const double *M; } linear_ctx;
+
+static int linear_rhs(void *vctx, const double *y, double *f) {
+  const linear_ctx *c = (const linear_ctx *)vctx;
+  for (int i = 0; i < c->n; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < c->n; ++j) s += c->M[i * c->n + j] * y[j];
+    f[i] = s;
+  }
+  return 0;
+}
+
+/* One Eq. 21 step of y' = M y (M row-major n x n): y is overwritten with y_n+1 and E
+ * receives the embedded error estimate. */
+void oracle_linear_step(int32_t n, const double *M, double h, double *y, double *E) {
+  linear_ctx c = {n, M};
+  lsrk_step(n, linear_rhs, &c, h, y, E);
+}
+
+/* Adaptive integration of y' = M y over [0, dt]; logs every attempted step.
+ * out4 = {status, accepted, rejected}; returns the number of attempts. */
+int32_t oracle_linear_integrate(int32_t n, const double *M, double *y, double dt, double rtol,
+                                double atol, double h0, int32_t max_steps, double *log_h,
+                                double *log_err, int32_t *log_acc, int32_t max_log, int32_t *out3) {
+  linear_ctx c = {n, M};
+  adapt_out o;
+  integrate_adaptive(n, linear_rhs, &c, dt, rtol, atol, h0, max_steps, y, &o, log_h, log_err,
+                     log_acc, max_log);
+  out3[0] = o.status; out3[1] = o.nacc; out3[2] = o.nrej;
+  return o.nacc + o.nrej;
+}
+
+static int quadratic_rhs(void *vctx, const double *y, double *f) {
+  (void)vctx;
+  f[0] = -y[0] * y[0];
+  return 0;
+}
+
+/* Fixed-step integration of y' = -y^2 from y0 over nsteps steps of h, propagating either
+ * the fourth-order solution (embedded = 0) or the third-order embedded one (X - E). */
+double oracle_quadratic_fixed(double y0, double h, int32_t nsteps, int32_t embedded) {
+  double X[1] = {y0}, E[1];
+  for (int s = 0; s < nsteps; ++s) {
+    lsrk_step(1, quadratic_rhs, NULL, h, X, E);
+    if (embedded) X[0] -= E[0];
+  }
+  return X[0];
+}
+
+/* ------------------------------------------------------------ chemistry cells */
+
+typedef struct {
+  const omech *m;
+  double rho, e, T;  /* T: last Newton result, the next warm start */
+} chem_cell;
+
+/* dY_k/dt = W_k wdot_k / rho at fixed (rho, e); T from Newton on (e, Y). */
+static int chem_rhs(void *vctx, const double *Y, double *F) {
+  chem_cell *cc = (chem_cell *)vctx;
+  double T, w[OR_MAXSP];
+  if (oracle_T_from_e(cc->m, Y, cc->e, cc->T, &T, NULL)) return 1;
+  cc->T = T;
+  oracle_wdot(cc->m, cc->rho, T, Y, w);
+  for (int k = 0; k < cc->m->nsp; ++k) F[k] = cc->m->W[k] * w[k] / cc->rho;
+  return 0;
+}
+
+/* dY/dt of one cell at (rho, e, Y), T solved from Tguess; the solved T is returned. */
+double oracle_chem_rhs(const omech *m, double rho, double e, const double *Y, double Tguess,
+                       double *F) {
+  chem_cell cc = {m, rho, e, Tguess};
+  if (chem_rhs(&cc, Y, F)) return NAN;
+  return cc.T;
+}
+
+/* Integrate n independent cells over dt (the hot path's reference).
+ * Y: species planes Y[k * ldY + i], advanced in place.  T: in = Newton guess (or NaN),
+ * out = temperature of the final state.  h0: per-cell initial step (NULL -> dt).
+ * Per cell out: status (0 ok, 1 max steps, 2 h underflow, 3 Newton failure,
+ * 4 non-finite), attempted steps, accepted steps, and the smallest |err - 1| seen
+ * (used to classify cells whose accept/reject decisions sit on a rounding knife-edge). */
+int32_t oracle_integrate(const omech *m, int64_t n, const double *rho, const double *e, double *Y,
+                         int64_t ldY, double *T, double dt, double rtol, double atol,
+                         const double *h0, int32_t max_steps, int32_t *status, int32_t *nsteps,
+                         int32_t *naccept, double *margin, int32_t nthreads) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 8)
+#endif
+  for (int64_t i = 0; i < n; ++i) {
+    double X[OR_MAXN];
+    for (int k = 0; k < m->nsp; ++k) X[k] = Y[k * ldY + i];
+    chem_cell cc = {m, rho[i], e[i], T[i]};
+    adapt_out o;
+    int bad_input = !(isfinite(rho[i]) && rho[i] > 0.0 && isfinite(e[i]));
+    for (int k = 0; k < m->nsp; ++k) bad_input |= !isfinite(X[k]);
+    if (bad_input) {
+      o.status = 4; o.nacc = 0; o.nrej = 0; o.margin = INFINITY;
+    } else {
+      integrate_adaptive(m->nsp, chem_rhs, &cc, dt, rtol, atol, h0 ? h0[i] : 0.0, max_steps, X,
+                         &o, NULL, NULL, NULL, 0);
+    }
+    double Tout = NAN;
+    if (o.status != 4 && oracle_T_from_e(m, X, e[i], cc.T, &Tout, NULL) != 0) {
+      if (o.status == 0) o.status = 3;
+      Tout = NAN;
+    }
+    for (int k = 0; k < m->nsp; ++k) Y[k * ldY + i] = X[k];
+    T[i] = Tout;
+    if (status) status[i] = o.status;
+    if (nsteps) nsteps[i] = o.nacc + o.nrej;
+    if (naccept) naccept[i] = o.nacc;
+    if (margin) margin[i] = o.margin;
+  }
+  return 0;
+}
+
+/* Fixed-step integration of one cell (nsteps steps of h, no error control), recording
+ * T after every step in T_trace[nsteps]; used for the step-halving ignition-delay check. */
+int32_t oracle_chem_fixed(const omech *m, double rho, double e, double *Y, double Tguess, double h,
+                          int32_t nsteps, double *T_trace) {
+  chem_cell cc = {m, rho, e, Tguess};
+  double E[OR_MAXN];
+  for (int s = 0; s < nsteps; ++s) {
+    if (lsrk_step(m->nsp, chem_rhs, &cc, h, Y, E)) return 3;
+    double T;
+    if (oracle_T_from_e(m, Y, e, cc.T, &T, NULL)) return 3;
+    T_trace[s] = T;
+  }
+  return 0;
+}
+
+int32_t oracle_max_species(void) { return OR_MAXSP; }
+int32_t oracle_max_reactions(void) { return OR_MAXRX; }
+int32_t oracle_struct_size(void) { return (int32_t)sizeof(omech); }
