@@ -1,0 +1,316 @@
+"""Benchmark: chemistry cells integrated per second over one hydro dt.
+
+Workload: the uniform 2D detonation slice, 1024 x 1024 = 1,048,576 cells, seeded 1D
+detonation-like profile extruded with +-2 % noise (chem_inputs.workloads.detonation_slice,
+seed 1), dt = 2e-9 s, rtol 1e-6, atol 1e-10, fp64 state.  A step is one integration of
+every cell over dt (the whole hot path: temperature solves, rates, low-storage RK
+stages, step control), from the same pristine state each time; the restore copy and
+an L2 flush (a 256 MB write, the inputs are 96 MB < 129 MB L2) are inside the timed
+region, so the reported rate slightly understates the kernel.
+
+Legs of one run (rank 0 prints one JSON line):
+  value     device-resident throughput (cells/s) of the headline variant;
+  e2e       the same through chem_integrate_host: host buffers (pinned), H2D + D2H
+            copies inside the timed region;
+  roofline  credited FP64 flops per launch / CUDA-event launch time vs the FP64 peak;
+  cpu_baseline  the CPU oracle on a bounded sample of the same workload (rank 0, N=1).
+--impl reference runs only the oracle (the deliberately slow plain CPU program).
+Under torchrun each rank integrates its own full slice (independent cells, weak
+scaling, no collective on the data path); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DT, RTOL, ATOL = 2e-9, 1e-6, 1e-10
+METRIC = "chem cells/s per hydro dt at stated error vs FP64; learned+batched vs plain"
+WORKLOAD = "detonation slice 1024x1024 (1,048,576 cells), H2-air 9 sp / 21 rx, dt=2e-9 s, rtol 1e-6, atol 1e-10"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nx", type=int, default=1024)
+    ap.add_argument("--ny", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=131072)
+    ap.add_argument("--ref-sample", type=int, default=32768)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------- clocks sampler
+class Clocks:
+    """nvidia-smi sampling during the timed region (every 200 ms)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- CPU oracle leg
+def cpu_oracle(sample_cells: int, nx: int, ny: int, gpu_out=None):
+    """Time the CPU oracle on a seeded sample of the workload; optionally compare the
+    GPU result on the same cells (parity of the benchmarked run)."""
+    import oracle
+    from chem_inputs import mechanism, workloads
+    d = workloads.detonation_slice(nx, ny, seed=1)
+    n = d["T"].size
+    rng = np.random.default_rng(2024)
+    idx = np.sort(rng.choice(n, min(sample_cells, n), replace=False))
+    o = oracle.Oracle(mechanism.build(0))
+    rho, e = o.state_from_TPY(d["T"][idx], d["p"][idx], d["Y"][:, idx])
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    ref = o.integrate(rho, e, d["Y"][:, idx], d["T"][idx], DT, RTOL, ATOL, nthreads=cores)
+    el = time.perf_counter() - t0
+    res = {"value": idx.size / el, "unit": "cells/s", "cores": cores, "kind": "oracle",
+           "sample": f"{idx.size} cells drawn uniformly (seed 2024) from the {n}-cell slice, "
+                     f"plain fp64 C, OpenMP over cells, {el:.2f} s wall"}
+    parity = None
+    if gpu_out is not None:
+        Yg, Tg = gpu_out["Y"][:, idx], gpu_out["T"][idx]
+        edge = ref["margin"] < 1e-7
+        relT = np.abs(Tg - ref["T"]) / ref["T"]
+        absY = np.abs(Yg - ref["Y"]).max(axis=0)
+        parity = {"cells": int(idx.size), "knife_edge_cells": int(edge.sum()),
+                  "max_rel_T": float(relT[~edge].max()), "max_abs_Y": float(absY[~edge].max()),
+                  "steps_equal": bool(np.array_equal(gpu_out["nsteps"][idx][~edge], ref["nsteps"][~edge]))}
+    return res, parity
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands on the host cores: W untimed and K timed steps, each one
+    integration of a bounded seeded sample of the workload from the same state."""
+    if rank != 0:
+        return
+    import oracle
+    from chem_inputs import mechanism, workloads
+    d = workloads.detonation_slice(args.nx, args.ny, seed=1)
+    n = d["T"].size
+    rng = np.random.default_rng(2024)
+    idx = np.sort(rng.choice(n, min(args.ref_sample, n), replace=False))
+    o = oracle.Oracle(mechanism.build(0))
+    rho, e = o.state_from_TPY(d["T"][idx], d["p"][idx], d["Y"][:, idx])
+    cores = os.cpu_count() or 1
+    run = lambda: o.integrate(rho, e, d["Y"][:, idx], d["T"][idx], DT, RTOL, ATOL, nthreads=cores)
+    for _ in range(args.warmup):
+        run()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run()
+    el = time.perf_counter() - t0
+    res = {"value": idx.size * args.steps / el, "unit": "cells/s", "cores": cores, "kind": "oracle",
+           "sample": f"{idx.size} cells drawn uniformly (seed 2024) from the {n}-cell slice per step, "
+                     f"{args.steps} timed steps, plain fp64 C, OpenMP over cells"}
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": "cells/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "variant": "cpu oracle"},
+            "cpu_baseline": res,
+            "e2e": {"value": res["value"], "unit": "cells/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- GPU leg
+def run_ours(args, rank, world, local):
+    import torch
+    from chem_inputs import mechanism, workloads
+    from paper_2506_02602_gb300 import build, chem, roofline
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    mech = mechanism.build(0)
+    d = workloads.detonation_slice(args.nx, args.ny, seed=1)
+    n = d["T"].size
+    S = d["Y"].shape[0]
+    ctx = chem.Context(mech, "fp64")
+    T0 = torch.tensor(d["T"], dtype=torch.float64, device=dev)
+    p0 = torch.tensor(d["p"], dtype=torch.float64, device=dev)
+    Y0 = torch.tensor(d["Y"], dtype=torch.float64, device=dev)
+    rho, e = ctx.state_from_TPY(T0, p0, Y0)
+    Y, T = Y0.clone(), T0.clone()
+    status = torch.empty(n, dtype=torch.int32, device=dev)
+    nsteps = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev0=None, ev1=None):
+        Y.copy_(Y0)
+        T.copy_(T0)
+        flush.fill_(1.0)
+        if ev0 is not None:
+            ev0.record(stream)
+        ctx.integrate(rho, e, Y, T, DT, RTOL, ATOL, status=status, nsteps=nsteps, stream=stream)
+        if ev1 is not None:
+            ev1.record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clocks = Clocks(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step(*evs[k])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    elapsed = time.perf_counter() - t0
+    clk = clocks.stop()
+    kernel_ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    if world > 1:
+        t = torch.tensor([elapsed, kernel_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed, kernel_ms = float(t[0]), float(t[1])
+    ms_per_step = 1e3 * elapsed / args.steps
+    value = world * n * args.steps / elapsed
+
+    # per-launch work from the kernel's own step counts (same every step: same input)
+    ns = nsteps.cpu().numpy()
+    st = status.cpu().numpy()
+    flops = roofline.launch_flops(int(ns.sum()), n, mech)
+    achieved = flops / (kernel_ms * 1e-3) / 1e9
+    gpu_res = {"Y": Y.cpu().numpy(), "T": T.cpu().numpy(), "nsteps": ns}
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    pin = lambda a: torch.tensor(a, dtype=torch.float64).pin_memory()
+    h_rho, h_e = pin(rho.cpu().numpy()), pin(e.cpu().numpy())
+    h_Y0, h_T0 = d["Y"].copy(), d["T"].copy()
+    h_Y, h_T = pin(h_Y0), pin(h_T0)
+    h_st = torch.empty(n, dtype=torch.int32).pin_memory()
+    h_ns = torch.empty(n, dtype=torch.int32).pin_memory()
+    hY, hT = h_Y.numpy(), h_T.numpy()
+
+    def e2e_step():
+        hY[...] = h_Y0
+        hT[...] = h_T0
+        ctx.integrate_host(h_rho.numpy(), h_e.numpy(), hY, hT, DT, RTOL, ATOL,
+                           status=h_st.numpy(), nsteps=h_ns.numpy(), stream=stream)
+
+    e2e_step()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e2e_el = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_el], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_el = float(t[0])
+    e2e_match = bool(np.array_equal(hY, gpu_res["Y"]) and np.array_equal(hT, gpu_res["T"]))
+
+    line = None
+    if rank == 0:
+        cpu, parity = (None, None)
+        if world == 1 and not args.no_cpu_baseline:
+            cpu, parity = cpu_oracle(args.cpu_sample, args.nx, args.ny, gpu_res)
+        peak = roofline.FP64_PEAK_GFLOPS
+        line = {
+            "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "variant": "plain fp64 low-storage RK",
+                       "cells": n, "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"{world} independent slices (one per GPU)"},
+            "kernel_ms": kernel_ms,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "note": "fp64 pipe; credited flops (exp/log = 20) per launch / event time; "
+                                 "peak derived: 152 SM x 2 FP64 FMA/clk x 2 x 2.07 GHz"},
+            "work": {"attempted_steps": int(ns.sum()), "mean_steps": float(ns.mean()),
+                     "max_steps": int(ns.max()), "credited_gflop_per_launch": flops / 1e9,
+                     "status_ok": int((st == 0).sum())},
+            "e2e": {"value": world * n * args.steps / e2e_el, "unit": "cells/s",
+                    "h2d_bytes_per_step": n * (3 + S) * 8,
+                    "d2h_bytes_per_step": n * (1 + S) * 8 + 2 * n * 4,
+                    "matches_device_path": e2e_match},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+            "parity_vs_oracle_sample": parity,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return line
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * chem.h -- C ABI of the GB300 per-cell chemistry integrator (libchem.so).
+ *
+ * The library advances every cell of a reacting-flow field through one hydrodynamic
+ * time step of the chemical source term.  Each cell is an independent
+ * constant-density, constant-internal-energy adiabatic reactor: the source term of
+ * Eq. 14 changes only the species partial densities, so (rho, e) stay fixed while the
+ * mass fractions Y_k evolve under the law of mass action (Eq. 15-16) with Arrhenius
+ * forward rates and reverse rates from equilibrium constants (Sec. 2.1.2).  The
+ * temperature is recovered from e by Newton iteration on NASA-7 polynomials (Eq. 10;
+ * calculate_T of Table 1) at every right-hand-side evaluation.  The integrator is the
+ * five-stage fourth-order low-storage embedded Runge-Kutta scheme of Eq. 21 with the
+ * WRMS step-size controller of Eq. 22 (Sec. 2.2.3), one GPU thread per cell
+ * (Sec. 4.1.2).
+ *
+ * Conventions for every entry point:
+ *   - Return value: CHEM_OK (0) or a negative chem_error code.  Arguments are checked
+ *     before anything is launched; chem_last_error() describes the last failure of a
+ *     context.  Per-cell outcomes never fail a call: they go to status[].
+ *   - Pointers named d_* are device pointers (cudaMalloc'd, or any memory the
+ *     device can address); h_* are host pointers.  The caller owns all of them; the
+ *     library never frees a caller pointer.  The library owns its context and the
+ *     scratch it allocates.
+ *   - stream is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Calls that take a stream are asynchronous with respect to the host unless they
+ *     say otherwise; results are ready once the stream has been synchronised.
+ *   - Cell arrays are structure-of-arrays fp64: plane k of Y starts at Y + k * ldY
+ *     (ldY >= ncells), and every plane pointer must be 8-byte aligned.
+ *   - Units are SI: kg/m^3, J/kg, K, Pa, s, kg/mol, J/mol.
+ *   - There is no CPU fallback: without a CUDA device every compute call returns
+ *     CHEM_ERR_CUDA.
+ */
+#ifndef CHEM_H
+#define CHEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CHEM_MAX_SPECIES 16
+#define CHEM_MAX_REACTIONS 32
+#define CHEM_NUM_ELEMENTS 3 /* H, O, N */
+
+typedef enum {
+  CHEM_OK = 0,
+  CHEM_ERR_INVALID = -1,     /* bad argument; nothing was launched */
+  CHEM_ERR_CUDA = -2,        /* a CUDA call or launch failed */
+  CHEM_ERR_UNSUPPORTED = -3, /* valid input this build has no kernel for */
+  CHEM_ERR_NOMEM = -4,       /* a device allocation failed */
+  CHEM_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+  CHEM_ERR_STATE = -6        /* call out of order (e.g. inference before training) */
+} chem_error;
+
+/* Per-cell outcome codes written to status[]. */
+typedef enum {
+  CHEM_CELL_OK = 0,
+  CHEM_CELL_MAX_STEPS = 1,   /* attempted-step limit reached; state = last accepted */
+  CHEM_CELL_H_UNDERFLOW = 2, /* step fell below 1e-15 dt; state = last accepted */
+  CHEM_CELL_NEWTON_FAIL = 3, /* no temperature root for the accepted state */
+  CHEM_CELL_NONFINITE = 4,   /* non-finite or non-positive input */
+  CHEM_CELL_SURROGATE = 5    /* informational: the surrogate's answer was rejected and
+                                the cell was integrated instead */
+} chem_cell_status;
+
+typedef enum {
+  CHEM_VARIANT_FP64 = 0,  /* every operation in fp64 */
+  CHEM_VARIANT_MIXED = 1  /* rates and RK stage derivatives in fp32; temperature solve,
+                             Gibbs/equilibrium terms, solution and error registers and
+                             step control in fp64 */
+} chem_variant;
+
+/*
+ * Reaction mechanism (Eq. 15-16; thermo of Eq. 10).  Species k has molar mass W[k],
+ * element counts ncomp[k][H, O, N] and NASA-7 tables nasa_lo[k] (T < T_mid[k]) and
+ * nasa_hi[k]: cp/R = a1 + a2 T + a3 T^2 + a4 T^3 + a5 T^4, h/RT adds a6/T, s/R adds a7.
+ * Reaction j has stoichiometric coefficients nu_f[j][k] (reactants) and nu_r[j][k]
+ * (products), type rtype[j] (0 elementary, 1 third body: rate times
+ * [M] = sum_k eff[j][k] c_k, 2 fall-off: k = k_inf Pr / (1 + Pr) F with
+ * Pr = k0 [M] / k_inf), Arrhenius k = A T^b exp(-Ea / (R_u T)) (high-pressure limit for
+ * fall-off; low-pressure limit A0, b0, Ea0), Troe parameters troe[j] = {alpha, T***,
+ * T*, T**} with troe_n[j] in {0 (Lindemann), 3, 4}, and reversible[j].  Reverse rates
+ * are k_f / K_c with K_c = exp(-sum_k nu_jk g_k / (R_u T)) (101325 Pa / (R_u T))^sum nu.
+ */
+typedef struct {
+  int32_t n_species;
+  int32_t n_reactions;
+  double W[CHEM_MAX_SPECIES];
+  int32_t ncomp[CHEM_MAX_SPECIES][CHEM_NUM_ELEMENTS];
+  double T_mid[CHEM_MAX_SPECIES];
+  double nasa_lo[CHEM_MAX_SPECIES][7];
+  double nasa_hi[CHEM_MAX_SPECIES][7];
+  int32_t rtype[CHEM_MAX_REACTIONS];
+  int32_t nu_f[CHEM_MAX_REACTIONS][CHEM_MAX_SPECIES];
+  int32_t nu_r[CHEM_MAX_REACTIONS][CHEM_MAX_SPECIES];
+  double A[CHEM_MAX_REACTIONS], b[CHEM_MAX_REACTIONS], Ea[CHEM_MAX_REACTIONS];
+  double A0[CHEM_MAX_REACTIONS], b0[CHEM_MAX_REACTIONS], Ea0[CHEM_MAX_REACTIONS];
+  double troe[CHEM_MAX_REACTIONS][4];
+  int32_t troe_n[CHEM_MAX_REACTIONS];
+  double eff[CHEM_MAX_REACTIONS][CHEM_MAX_SPECIES];
+  int32_t reversible[CHEM_MAX_REACTIONS];
+} chem_mechanism;
+
+/* Options fixed at setup.  Zero-initialised fields take the defaults in brackets. */
+typedef struct {
+  int32_t variant;     /* chem_variant [CHEM_VARIANT_FP64] */
+  int32_t max_steps;   /* attempted-step limit per cell and call [100000] */
+  int32_t block_size;  /* threads per block of the integration kernels [128] */
+  int32_t reserved[5]; /* must be zero */
+} chem_options;
+
+/*
+ * State of ncells cells, all device pointers, structure of arrays.
+ *   d_rho[n], d_e[n]      in: density, specific internal energy (constant over dt)
+ *   d_Y[k * ldY + i]      in/out: mass fractions, advanced in place
+ *   d_T[n]                in: Newton starting guess (NaN or <= 0 -> 1500 K);
+ *                         out: temperature of the final state
+ *   d_h[n]  (nullable)    in: initial step per cell (<= 0 or NaN -> dt);
+ *                         out: the controller's next step, to carry into the next call
+ *   d_status[n] (nullable) out: chem_cell_status
+ *   d_nsteps[n] (nullable) out: attempted steps (accepted + rejected)
+ */
+typedef struct {
+  const double *d_rho;
+  const double *d_e;
+  double *d_Y;
+  int64_t ldY;
+  double *d_T;
+  double *d_h;
+  int32_t *d_status;
+  int32_t *d_nsteps;
+} chem_state;
+
+/* Aggregate counters of one call (filled by warp reductions, one atomic per warp). */
+typedef struct {
+  int64_t cells;
+  int64_t accepted;
+  int64_t rejected;
+  int64_t rhs_evals;
+  int64_t max_steps_cell; /* largest attempted-step count of any cell */
+  int64_t status_count[8];
+} chem_stats;
+
+typedef struct chem_ctx chem_ctx;
+
+/*
+ * Create a context for mechanism *mech (copied; the caller keeps ownership).
+ * Validates the mechanism: element balance of every reaction (integers), NASA-7
+ * continuity of cp, h and s at T_mid (relative 1e-6), a common T_mid, positive molar
+ * masses.  This build's kernels are specialised at compile time to the structure of
+ * the 9-species / 21-reaction H2-O2-N2 mechanism (species H2, O2, H2O, H, O, OH, HO2,
+ * H2O2, N2 in that order; the reaction list of chem_inputs.mechanism): a mechanism
+ * with other stoichiometry or reaction types returns CHEM_ERR_UNSUPPORTED.  Its
+ * coefficients (rates, efficiencies, Troe, thermo) are free.  Needs a CUDA device.
+ * On success *out owns device scratch until chem_teardown.  opt may be NULL.
+ */
+int chem_setup(const chem_mechanism *mech, const chem_options *opt, chem_ctx **out);
+
+/* Free a context and everything it owns.  NULL is accepted.  Synchronises the device. */
+int chem_teardown(chem_ctx *ctx);
+
+/* Message of the last failed call on ctx (or of the last failed chem_setup when ctx
+ * is NULL).  The string stays valid until the next call on the same context. */
+const char *chem_last_error(const chem_ctx *ctx);
+
+/*
+ * Conserved state from (T, p, Y) (Eq. 6 and Eq. 10): rho = p Wbar / (R_u T),
+ * e = sum_k Y_k (h_k(T) - R_u T) / W_k.  d_T, d_p: [n]; d_Y: planes with stride ldY;
+ * outputs d_rho, d_e: [n].  Asynchronous on stream.
+ */
+int chem_state_from_TPY(chem_ctx *ctx, int64_t n, const double *d_T, const double *d_p,
+                        const double *d_Y, int64_t ldY, double *d_rho, double *d_e,
+                        void *stream);
+
+/*
+ * Integrate every cell of *state over [0, dt] (Eq. 20-22), one thread per cell, in the
+ * precision variant chosen at setup.  rtol, atol: the WRMS tolerances of Eq. 22
+ * (the paper uses 1e-6 and 1e-10); the norm runs over the species mass fractions with
+ * |u_i| = max(|y_n,i|, |y_n+1,i|).  Step controller: safety 0.9, exponent 1/4,
+ * growth and shrink factors clamped to [1/5, 5]; accept iff ||e|| <= 1; the step is
+ * clipped to land on dt.  A trial stage without a temperature root rejects the
+ * attempt with factor 1/5.
+ * d_stats (nullable): a device pointer to a chem_stats that the call zeroes and fills.
+ * Errors: ncells < 0, dt <= 0, rtol <= 0, atol < 0, a NULL required pointer or
+ * ldY < ncells -> CHEM_ERR_INVALID.  ncells == 0 is a no-op.  Asynchronous on stream.
+ */
+int chem_integrate(chem_ctx *ctx, const chem_state *state, int64_t ncells, double dt,
+                   double rtol, double atol, void *stream, chem_stats *d_stats);
+
+/*
+ * The same integration with the cells' host copies: copies h_rho, h_e, h_Y (ldY),
+ * h_T (and h_h if given) to device scratch owned by the context, integrates, and
+ * copies Y, T, status, nsteps (and h) back into the host arrays.  Synchronous: it
+ * returns after the results are in host memory.  Pinned host memory gives the
+ * fastest copies.  Same argument rules as chem_integrate; h_status/h_nsteps/h_h are
+ * nullable.
+ */
+int chem_integrate_host(chem_ctx *ctx, int64_t ncells, const double *h_rho,
+                        const double *h_e, double *h_Y, int64_t ldY, double *h_T,
+                        double *h_h, int32_t *h_status, int32_t *h_nsteps, double dt,
+                        double rtol, double atol, void *stream);
+
+/* Library version, as major * 10000 + minor * 100 + patch. */
+int chem_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHEM_H */

@@ -1,0 +1,232 @@
+"""Thin Python binding of libchem.so (include/chem.h): argument marshalling only.
+
+Every step of the integration runs in the library's CUDA kernels.  PyTorch provides
+device memory and streams: the functions here take torch CUDA tensors and pass their
+data pointers and the current stream to the C ABI.  There is no CPU fallback: if
+libchem.so is missing or no GPU is present the calls raise.
+
+Names follow the C ABI: ``Context`` wraps chem_setup / chem_teardown, and its methods
+``integrate``, ``integrate_host`` and ``state_from_TPY`` wrap chem_integrate,
+chem_integrate_host and chem_state_from_TPY.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libchem.so")
+
+MAX_SPECIES = 16
+MAX_REACTIONS = 32
+NUM_ELEMENTS = 3
+
+OK, ERR_INVALID, ERR_CUDA, ERR_UNSUPPORTED, ERR_NOMEM, ERR_TIMEOUT, ERR_STATE = 0, -1, -2, -3, -4, -5, -6
+CELL_OK, CELL_MAX_STEPS, CELL_H_UNDERFLOW, CELL_NEWTON_FAIL, CELL_NONFINITE, CELL_SURROGATE = range(6)
+VARIANTS = {"fp64": 0, "mixed": 1}
+
+
+class ChemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libchem error {code}: {msg}")
+        self.code = code
+
+
+class Mechanism(C.Structure):
+    _fields_ = [
+        ("n_species", C.c_int32), ("n_reactions", C.c_int32),
+        ("W", C.c_double * MAX_SPECIES),
+        ("ncomp", (C.c_int32 * NUM_ELEMENTS) * MAX_SPECIES),
+        ("T_mid", C.c_double * MAX_SPECIES),
+        ("nasa_lo", (C.c_double * 7) * MAX_SPECIES),
+        ("nasa_hi", (C.c_double * 7) * MAX_SPECIES),
+        ("rtype", C.c_int32 * MAX_REACTIONS),
+        ("nu_f", (C.c_int32 * MAX_SPECIES) * MAX_REACTIONS),
+        ("nu_r", (C.c_int32 * MAX_SPECIES) * MAX_REACTIONS),
+        ("A", C.c_double * MAX_REACTIONS), ("b", C.c_double * MAX_REACTIONS),
+        ("Ea", C.c_double * MAX_REACTIONS),
+        ("A0", C.c_double * MAX_REACTIONS), ("b0", C.c_double * MAX_REACTIONS),
+        ("Ea0", C.c_double * MAX_REACTIONS),
+        ("troe", (C.c_double * 4) * MAX_REACTIONS),
+        ("troe_n", C.c_int32 * MAX_REACTIONS),
+        ("eff", (C.c_double * MAX_SPECIES) * MAX_REACTIONS),
+        ("reversible", C.c_int32 * MAX_REACTIONS),
+    ]
+
+
+class Options(C.Structure):
+    _fields_ = [("variant", C.c_int32), ("max_steps", C.c_int32), ("block_size", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
+
+
+class State(C.Structure):
+    _fields_ = [("d_rho", C.c_void_p), ("d_e", C.c_void_p), ("d_Y", C.c_void_p),
+                ("ldY", C.c_int64), ("d_T", C.c_void_p), ("d_h", C.c_void_p),
+                ("d_status", C.c_void_p), ("d_nsteps", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("cells", C.c_int64), ("accepted", C.c_int64), ("rejected", C.c_int64),
+                ("rhs_evals", C.c_int64), ("max_steps_cell", C.c_int64),
+                ("status_count", C.c_int64 * 8)]
+
+
+STATS_WORDS = C.sizeof(Stats) // 8
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load libchem.so (built in-tree by paper_2506_02602_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ChemError(ERR_CUDA, f"{LIB_PATH} is not built; run paper_2506_02602_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i64, dbl = C.c_void_p, C.c_int64, C.c_double
+    sig = {
+        "chem_version": (C.c_int, []),
+        "chem_last_error": (C.c_char_p, [vp]),
+        "chem_setup": (C.c_int, [C.POINTER(Mechanism), C.POINTER(Options), C.POINTER(vp)]),
+        "chem_teardown": (C.c_int, [vp]),
+        "chem_state_from_TPY": (C.c_int, [vp, i64, vp, vp, vp, i64, vp, vp, vp]),
+        "chem_integrate": (C.c_int, [vp, C.POINTER(State), i64, dbl, dbl, dbl, vp, vp]),
+        "chem_integrate_host": (C.c_int, [vp, i64, vp, vp, vp, i64, vp, vp, vp, vp, dbl, dbl, dbl, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def make_mechanism(m: dict) -> Mechanism:
+    """Marshal a mechanism dict (chem_inputs.mechanism layout) into chem_mechanism."""
+    S, R = len(m["W"]), len(m["A"])
+    if S > MAX_SPECIES or R > MAX_REACTIONS:
+        raise ChemError(ERR_INVALID, "mechanism exceeds CHEM_MAX_SPECIES / CHEM_MAX_REACTIONS")
+    c = Mechanism()
+    c.n_species, c.n_reactions = S, R
+    for k in range(S):
+        c.W[k] = float(m["W"][k])
+        c.T_mid[k] = float(m["T_mid"][k])
+        for e in range(NUM_ELEMENTS):
+            c.ncomp[k][e] = int(m["ncomp"][k][e])
+        for i in range(7):
+            c.nasa_lo[k][i] = float(m["nasa_lo"][k][i])
+            c.nasa_hi[k][i] = float(m["nasa_hi"][k][i])
+    for j in range(R):
+        c.rtype[j] = int(m["rtype"][j])
+        c.A[j], c.b[j], c.Ea[j] = float(m["A"][j]), float(m["b"][j]), float(m["Ea"][j])
+        c.A0[j], c.b0[j], c.Ea0[j] = float(m["A0"][j]), float(m["b0"][j]), float(m["Ea0"][j])
+        c.troe_n[j] = int(m["troe_n"][j])
+        for i in range(4):
+            c.troe[j][i] = float(m["troe"][j][i])
+        c.reversible[j] = int(m["reversible"][j])
+        for k in range(S):
+            c.nu_f[j][k] = int(m["nu_f"][j][k])
+            c.nu_r[j][k] = int(m["nu_r"][j][k])
+            c.eff[j][k] = float(m["eff"][j][k])
+    return c
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _check_f64_cuda(name, t, n=None):
+    import torch
+    if t.device.type != "cuda" or t.dtype != torch.float64:
+        raise ChemError(ERR_INVALID, f"{name} must be a float64 CUDA tensor")
+    if n is not None and t.shape[-1] < n:
+        raise ChemError(ERR_INVALID, f"{name} has fewer than {n} cells")
+
+
+class Context:
+    """A chem_ctx bound to one mechanism and precision variant."""
+
+    def __init__(self, mech: dict, variant: str = "fp64", max_steps: int = 0, block_size: int = 0):
+        self.L = load()
+        self._mech = make_mechanism(mech)
+        opt = Options()
+        opt.variant = VARIANTS[variant]
+        opt.max_steps = max_steps
+        opt.block_size = block_size
+        h = C.c_void_p()
+        rc = self.L.chem_setup(C.byref(self._mech), C.byref(opt), C.byref(h))
+        if rc != OK:
+            raise ChemError(rc, self.L.chem_last_error(None).decode())
+        self.h = h
+        self.variant = variant
+        self.n_species = len(mech["W"])
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.chem_teardown(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _raise(self, rc):
+        if rc != OK:
+            raise ChemError(rc, self.L.chem_last_error(self.h).decode())
+
+    def state_from_TPY(self, T, p, Y, rho=None, e=None, stream=None):
+        """rho, e from (T, p, Y) on the device (float64 CUDA tensors; Y is [S, ld])."""
+        import torch
+        n = T.numel()
+        for nm, t in (("T", T), ("p", p), ("Y", Y)):
+            _check_f64_cuda(nm, t)
+        rho = torch.empty_like(T) if rho is None else rho
+        e = torch.empty_like(T) if e is None else e
+        self._raise(self.L.chem_state_from_TPY(self.h, n, _ptr(T), _ptr(p), _ptr(Y), Y.stride(0),
+                                               _ptr(rho), _ptr(e), _stream(stream)))
+        return rho, e
+
+    def integrate(self, rho, e, Y, T, dt, rtol=1e-6, atol=1e-10, h=None, status=None, nsteps=None,
+                  stats=None, stream=None, ncells=None):
+        """Advance Y [S, ld] and T in place over dt (chem_integrate).  status / nsteps
+        (int32 CUDA tensors), h (float64) and stats (int64 tensor of STATS_WORDS) are
+        optional outputs."""
+        n = rho.numel() if ncells is None else ncells
+        for nm, t in (("rho", rho), ("e", e), ("Y", Y), ("T", T)):
+            _check_f64_cuda(nm, t, n)
+        if Y.stride(1) != 1:
+            raise ChemError(ERR_INVALID, "Y planes must be contiguous")
+        st = State(_ptr(rho).value, _ptr(e).value, _ptr(Y).value, Y.stride(0), _ptr(T).value,
+                   None if h is None else h.data_ptr(),
+                   None if status is None else status.data_ptr(),
+                   None if nsteps is None else nsteps.data_ptr())
+        self._raise(self.L.chem_integrate(self.h, C.byref(st), n, float(dt), float(rtol), float(atol),
+                                          _stream(stream), _ptr(stats)))
+
+    def integrate_host(self, rho, e, Y, T, dt, rtol=1e-6, atol=1e-10, h=None, status=None,
+                       nsteps=None, stream=None):
+        """chem_integrate_host on numpy arrays (Y is [S, ld], C-contiguous planes);
+        Y, T and the optional outputs are updated in place."""
+        n = rho.size
+        for nm, a in (("rho", rho), ("e", e), ("Y", Y), ("T", T)):
+            if a.dtype != np.float64 or not a.flags.c_contiguous:
+                raise ChemError(ERR_INVALID, f"{nm} must be a C-contiguous float64 array")
+
+        def p(a):
+            return None if a is None else C.c_void_p(a.ctypes.data)
+
+        self._raise(self.L.chem_integrate_host(self.h, n, p(rho), p(e), p(Y), Y.strides[0] // 8, p(T),
+                                               p(h), p(status), p(nsteps), float(dt), float(rtol),
+                                               float(atol), _stream(stream)))

@@ -1,0 +1,341 @@
+// api.cu -- the extern "C" entry points of libchem.so (declared in include/chem.h):
+// context set-up with mechanism validation and table packing, argument checking,
+// launches on the caller's stream, the host-buffer convenience path, error strings.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "internal.cuh"
+
+using namespace chem;
+
+struct chem_ctx {
+  MechTables tables;
+  chem_options opt;
+  int device = 0;
+  std::string err;
+  // device scratch of chem_integrate_host (grown on demand, freed at teardown)
+  void *host_scratch = nullptr;
+  size_t host_scratch_bytes = 0;
+};
+
+namespace {
+
+thread_local std::string g_setup_err;
+
+int fail(chem_ctx *ctx, int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf; else g_setup_err = buf;
+  return code;
+}
+
+int cuda_fail(chem_ctx *ctx, cudaError_t e, const char *what) {
+  return fail(ctx, CHEM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// NASA-7 helpers for validation (host side).
+double nasa_cp(const double *a, double T) {
+  return a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
+}
+double nasa_h(const double *a, double T) {  // h / R
+  return T * (a[0] + T * (a[1] / 2 + T * (a[2] / 3 + T * (a[3] / 4 + T * a[4] / 5)))) + a[5];
+}
+double nasa_s(const double *a, double T) {  // s / R
+  return a[0] * std::log(T) + T * (a[1] + T * (a[2] / 2 + T * (a[3] / 3 + T * a[4] / 4))) + a[6];
+}
+
+bool close_rel(double x, double y, double tol) {
+  return std::fabs(x - y) <= tol * std::fmax(1.0, std::fmax(std::fabs(x), std::fabs(y)));
+}
+
+// Validate *m and pack it into *t.  Returns CHEM_OK or an error code (message set).
+int build_tables(const chem_mechanism *m, MechTables *t) {
+  if (m->n_species != NSP || m->n_reactions != NRX)
+    return fail(nullptr, CHEM_ERR_UNSUPPORTED,
+                "this build is specialised to %d species / %d reactions (got %d / %d)", NSP, NRX,
+                m->n_species, m->n_reactions);
+  std::memset(t, 0, sizeof *t);
+  const double Tmid = m->T_mid[0];
+  for (int k = 0; k < NSP; ++k) {
+    if (!(m->W[k] > 0.0) || !std::isfinite(m->W[k]))
+      return fail(nullptr, CHEM_ERR_INVALID, "species %d: molar mass must be positive", k);
+    if (m->T_mid[k] != Tmid)
+      return fail(nullptr, CHEM_ERR_UNSUPPORTED, "species %d: NASA-7 T_mid differs from species 0", k);
+    for (int i = 0; i < 7; ++i)
+      if (!std::isfinite(m->nasa_lo[k][i]) || !std::isfinite(m->nasa_hi[k][i]))
+        return fail(nullptr, CHEM_ERR_INVALID, "species %d: non-finite NASA-7 coefficient", k);
+    const double *lo = m->nasa_lo[k], *hi = m->nasa_hi[k];
+    if (!close_rel(nasa_cp(lo, Tmid), nasa_cp(hi, Tmid), 1e-6) ||
+        !close_rel(nasa_h(lo, Tmid), nasa_h(hi, Tmid), 1e-6) ||
+        !close_rel(nasa_s(lo, Tmid), nasa_s(hi, Tmid), 1e-6))
+      return fail(nullptr, CHEM_ERR_INVALID, "species %d: NASA-7 tables discontinuous at T_mid", k);
+  }
+  if (!(Tmid > 0.0)) return fail(nullptr, CHEM_ERR_INVALID, "T_mid must be positive");
+  for (int j = 0; j < NRX; ++j) {
+    // element balance (integers)
+    for (int el = 0; el < CHEM_NUM_ELEMENTS; ++el) {
+      long bal = 0;
+      for (int k = 0; k < NSP; ++k) bal += (long)(m->nu_r[j][k] - m->nu_f[j][k]) * m->ncomp[k][el];
+      if (bal != 0)
+        return fail(nullptr, CHEM_ERR_INVALID, "reaction %d does not balance element %d", j, el);
+    }
+    // stoichiometry and type must match the compiled structure
+    int want_f[NSP] = {0}, want_r[NSP] = {0};
+    const RxStruct &R = kRx[j];
+    if (R.r0 >= 0) want_f[R.r0]++;
+    if (R.r1 >= 0) want_f[R.r1]++;
+    if (R.p0 >= 0) want_r[R.p0]++;
+    if (R.p1 >= 0) want_r[R.p1]++;
+    for (int k = 0; k < NSP; ++k)
+      if (m->nu_f[j][k] != want_f[k] || m->nu_r[j][k] != want_r[k])
+        return fail(nullptr, CHEM_ERR_UNSUPPORTED,
+                    "reaction %d: stoichiometry differs from the compiled H2-O2 structure", j);
+    for (int k = NSP; k < CHEM_MAX_SPECIES; ++k)
+      if (m->nu_f[j][k] || m->nu_r[j][k])
+        return fail(nullptr, CHEM_ERR_INVALID, "reaction %d uses a species beyond n_species", j);
+    if (m->rtype[j] != R.type)
+      return fail(nullptr, CHEM_ERR_UNSUPPORTED, "reaction %d: type %d, compiled type %d", j,
+                  m->rtype[j], R.type);
+    if (R.type == FALLOFF && m->troe_n[j] != R.troe_n)
+      return fail(nullptr, CHEM_ERR_UNSUPPORTED, "reaction %d: %d Troe parameters, compiled %d", j,
+                  m->troe_n[j], R.troe_n);
+    if (!(m->A[j] > 0.0) || !std::isfinite(m->b[j]) || !std::isfinite(m->Ea[j]))
+      return fail(nullptr, CHEM_ERR_INVALID, "reaction %d: Arrhenius parameters invalid", j);
+    if (R.type == FALLOFF && (!(m->A0[j] > 0.0) || !std::isfinite(m->b0[j]) ||
+                              !std::isfinite(m->Ea0[j])))
+      return fail(nullptr, CHEM_ERR_INVALID, "reaction %d: low-pressure parameters invalid", j);
+    if (R.type == FALLOFF && R.troe_n > 0 &&
+        (!(m->troe[j][1] > 0.0) || !(m->troe[j][2] > 0.0) ||
+         (R.troe_n == 4 && !std::isfinite(m->troe[j][3]))))
+      return fail(nullptr, CHEM_ERR_INVALID, "reaction %d: Troe temperatures invalid", j);
+  }
+
+  t->T_mid = Tmid;
+  for (int k = 0; k < NSP; ++k) {
+    t->W[k] = m->W[k];
+    t->invW[k] = 1.0 / m->W[k];
+    for (int r = 0; r < 2; ++r) {
+      const double *a = r ? m->nasa_hi[k] : m->nasa_lo[k];
+      t->ec[r][k][0] = a[0] - 1.0;
+      t->ec[r][k][1] = a[1] / 2.0;
+      t->ec[r][k][2] = a[2] / 3.0;
+      t->ec[r][k][3] = a[3] / 4.0;
+      t->ec[r][k][4] = a[4] / 5.0;
+      t->ec[r][k][5] = a[5];
+      t->hc[r][k][0] = a[0];
+      t->hc[r][k][1] = a[1] / 2.0;
+      t->hc[r][k][2] = a[2] / 3.0;
+      t->hc[r][k][3] = a[3] / 4.0;
+      t->hc[r][k][4] = a[4] / 5.0;
+      t->hc[r][k][5] = a[5];
+      t->sc[r][k][0] = a[0];
+      t->sc[r][k][1] = a[1];
+      t->sc[r][k][2] = a[2] / 2.0;
+      t->sc[r][k][3] = a[3] / 3.0;
+      t->sc[r][k][4] = a[4] / 4.0;
+      t->sc[r][k][5] = a[6];
+    }
+  }
+  for (int j = 0; j < NRX; ++j) {
+    t->A[j] = m->A[j];
+    t->lnA[j] = std::log(m->A[j]);
+    t->beta[j] = m->b[j];
+    t->Ta[j] = m->Ea[j] / R_U;
+    t->kconst[j] = (m->b[j] == 0.0 && m->Ea[j] == 0.0);
+    t->reversible[j] = m->reversible[j] != 0;
+    if (kRx[j].type == FALLOFF) {
+      t->lnA0[j] = std::log(m->A0[j]);
+      t->beta0[j] = m->b0[j];
+      t->Ta0[j] = m->Ea0[j] / R_U;
+      t->troe_a[j] = m->troe[j][0];
+      t->troe_i3[j] = kRx[j].troe_n ? 1.0 / m->troe[j][1] : 0.0;
+      t->troe_i1[j] = kRx[j].troe_n ? 1.0 / m->troe[j][2] : 0.0;
+      t->troe_T2[j] = m->troe[j][3];
+    }
+    int any = 0;
+    for (int k = 0; k < NSP; ++k) {
+      t->effm1[j][k] = kRx[j].type == ELEM ? 0.0 : m->eff[j][k] - 1.0;
+      any |= t->effm1[j][k] != 0.0;
+    }
+    t->has_eff[j] = any;
+  }
+  return CHEM_OK;
+}
+
+bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
+int check_state(chem_ctx *ctx, const chem_state *s, int64_t n) {
+  if (!s) return fail(ctx, CHEM_ERR_INVALID, "state is NULL");
+  if (n < 0) return fail(ctx, CHEM_ERR_INVALID, "ncells < 0");
+  if (n == 0) return CHEM_OK;
+  if (!s->d_rho || !s->d_e || !s->d_Y || !s->d_T)
+    return fail(ctx, CHEM_ERR_INVALID, "rho, e, Y and T are required");
+  if (s->ldY < n) return fail(ctx, CHEM_ERR_INVALID, "ldY (%lld) < ncells (%lld)",
+                              (long long)s->ldY, (long long)n);
+  if (!aligned8(s->d_rho) || !aligned8(s->d_e) || !aligned8(s->d_Y) || !aligned8(s->d_T) ||
+      !aligned8(s->d_h))
+    return fail(ctx, CHEM_ERR_INVALID, "state pointers must be 8-byte aligned");
+  return CHEM_OK;
+}
+
+int check_step(chem_ctx *ctx, double dt, double rtol, double atol) {
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, CHEM_ERR_INVALID, "dt must be > 0");
+  if (!(rtol > 0.0) || !std::isfinite(rtol)) return fail(ctx, CHEM_ERR_INVALID, "rtol must be > 0");
+  if (!(atol >= 0.0) || !std::isfinite(atol)) return fail(ctx, CHEM_ERR_INVALID, "atol must be >= 0");
+  return CHEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int chem_version(void) { return 10000; }
+
+const char *chem_last_error(const chem_ctx *ctx) {
+  return ctx ? ctx->err.c_str() : g_setup_err.c_str();
+}
+
+int chem_setup(const chem_mechanism *mech, const chem_options *opt, chem_ctx **out) {
+  g_setup_err.clear();
+  if (!mech || !out) return fail(nullptr, CHEM_ERR_INVALID, "mech and out are required");
+  *out = nullptr;
+  chem_options o{};
+  if (opt) o = *opt;
+  if (o.variant != CHEM_VARIANT_FP64 && o.variant != CHEM_VARIANT_MIXED)
+    return fail(nullptr, CHEM_ERR_INVALID, "unknown variant %d", o.variant);
+  if (o.max_steps < 0) return fail(nullptr, CHEM_ERR_INVALID, "max_steps < 0");
+  if (o.max_steps == 0) o.max_steps = 100000;
+  if (o.block_size == 0) o.block_size = 128;
+  for (int i = 0; i < 5; ++i)
+    if (o.reserved[i]) return fail(nullptr, CHEM_ERR_INVALID, "reserved options must be zero");
+  MechTables t;
+  int rc = build_tables(mech, &t);
+  if (rc != CHEM_OK) return rc;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(nullptr, CHEM_ERR_CUDA, "no CUDA device available (%s)", cudaGetErrorString(e));
+  }
+  chem_ctx *ctx = new chem_ctx;
+  ctx->tables = t;
+  ctx->opt = o;
+  cudaGetDevice(&ctx->device);
+  *out = ctx;
+  return CHEM_OK;
+}
+
+int chem_teardown(chem_ctx *ctx) {
+  if (!ctx) return CHEM_OK;
+  cudaDeviceSynchronize();
+  if (ctx->host_scratch) cudaFree(ctx->host_scratch);
+  delete ctx;
+  return CHEM_OK;
+}
+
+int chem_state_from_TPY(chem_ctx *ctx, int64_t n, const double *d_T, const double *d_p,
+                        const double *d_Y, int64_t ldY, double *d_rho, double *d_e, void *stream) {
+  if (!ctx) return fail(nullptr, CHEM_ERR_INVALID, "ctx is NULL");
+  if (n < 0) return fail(ctx, CHEM_ERR_INVALID, "n < 0");
+  if (n == 0) return CHEM_OK;
+  if (!d_T || !d_p || !d_Y || !d_rho || !d_e) return fail(ctx, CHEM_ERR_INVALID, "NULL pointer");
+  if (ldY < n) return fail(ctx, CHEM_ERR_INVALID, "ldY < n");
+  cudaError_t e = launch_state_from_TPY(ctx->tables, n, d_T, d_p, d_Y, ldY, d_rho, d_e,
+                                        (cudaStream_t)stream);
+  return e == cudaSuccess ? CHEM_OK : cuda_fail(ctx, e, "state_from_TPY launch");
+}
+
+int chem_integrate(chem_ctx *ctx, const chem_state *state, int64_t ncells, double dt, double rtol,
+                   double atol, void *stream, chem_stats *d_stats) {
+  if (!ctx) return fail(nullptr, CHEM_ERR_INVALID, "ctx is NULL");
+  int rc = check_state(ctx, state, ncells);
+  if (rc) return rc;
+  rc = check_step(ctx, dt, rtol, atol);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (d_stats) {
+    cudaError_t e = cudaMemsetAsync(d_stats, 0, sizeof(chem_stats), s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "clearing stats");
+  }
+  if (ncells == 0) return CHEM_OK;
+  CellArgs a{state->d_rho, state->d_e, state->d_Y, state->ldY, state->d_T, state->d_h,
+             state->d_status, state->d_nsteps, ncells, d_stats};
+  StepParams p{dt, rtol, atol, ctx->opt.max_steps};
+  cudaError_t e = launch_lsrk(ctx->opt.variant, ctx->tables, a, p, ctx->opt.block_size, s);
+  return e == cudaSuccess ? CHEM_OK : cuda_fail(ctx, e, "integration launch");
+}
+
+int chem_integrate_host(chem_ctx *ctx, int64_t n, const double *h_rho, const double *h_e,
+                        double *h_Y, int64_t ldY, double *h_T, double *h_h, int32_t *h_status,
+                        int32_t *h_nsteps, double dt, double rtol, double atol, void *stream) {
+  if (!ctx) return fail(nullptr, CHEM_ERR_INVALID, "ctx is NULL");
+  if (n < 0) return fail(ctx, CHEM_ERR_INVALID, "ncells < 0");
+  int rc = check_step(ctx, dt, rtol, atol);
+  if (rc) return rc;
+  if (n == 0) return CHEM_OK;
+  if (!h_rho || !h_e || !h_Y || !h_T) return fail(ctx, CHEM_ERR_INVALID, "rho, e, Y, T required");
+  if (ldY < n) return fail(ctx, CHEM_ERR_INVALID, "ldY < ncells");
+  // device layout: rho, e, T, h [n] + Y [NSP * n] doubles, then status, nsteps [n] int32
+  const size_t nd = (size_t)n;
+  const size_t need = (4 + NSP) * nd * sizeof(double) + 2 * nd * sizeof(int32_t);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (need > ctx->host_scratch_bytes) {
+    if (ctx->host_scratch) {
+      cudaStreamSynchronize(s);
+      cudaFree(ctx->host_scratch);
+      ctx->host_scratch = nullptr;
+      ctx->host_scratch_bytes = 0;
+    }
+    e = cudaMalloc(&ctx->host_scratch, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, CHEM_ERR_NOMEM, "device scratch of %zu bytes: %s", need,
+                  cudaGetErrorString(e));
+    }
+    ctx->host_scratch_bytes = need;
+  }
+  double *d = static_cast<double *>(ctx->host_scratch);
+  double *d_rho = d, *d_e = d + nd, *d_T = d + 2 * nd, *d_h = d + 3 * nd, *d_Y = d + 4 * nd;
+  int32_t *d_status = reinterpret_cast<int32_t *>(d + (4 + NSP) * nd);
+  int32_t *d_nsteps = d_status + nd;
+  const size_t bytes = nd * sizeof(double);
+#define CK(call, what)                                   \
+  do {                                                   \
+    e = (call);                                          \
+    if (e != cudaSuccess) return cuda_fail(ctx, e, what); \
+  } while (0)
+  CK(cudaMemcpyAsync(d_rho, h_rho, bytes, cudaMemcpyHostToDevice, s), "copy rho");
+  CK(cudaMemcpyAsync(d_e, h_e, bytes, cudaMemcpyHostToDevice, s), "copy e");
+  CK(cudaMemcpyAsync(d_T, h_T, bytes, cudaMemcpyHostToDevice, s), "copy T");
+  if (h_h) CK(cudaMemcpyAsync(d_h, h_h, bytes, cudaMemcpyHostToDevice, s), "copy h");
+  CK(cudaMemcpy2DAsync(d_Y, bytes, h_Y, (size_t)ldY * sizeof(double), bytes, NSP,
+                       cudaMemcpyHostToDevice, s), "copy Y");
+  CellArgs a{d_rho, d_e, d_Y, (int64_t)nd, d_T, h_h ? d_h : nullptr, d_status, d_nsteps, n, nullptr};
+  StepParams p{dt, rtol, atol, ctx->opt.max_steps};
+  CK(launch_lsrk(ctx->opt.variant, ctx->tables, a, p, ctx->opt.block_size, s), "integration launch");
+  CK(cudaMemcpy2DAsync(h_Y, (size_t)ldY * sizeof(double), d_Y, bytes, bytes, NSP,
+                       cudaMemcpyDeviceToHost, s), "copy Y back");
+  CK(cudaMemcpyAsync(h_T, d_T, bytes, cudaMemcpyDeviceToHost, s), "copy T back");
+  if (h_h) CK(cudaMemcpyAsync(h_h, d_h, bytes, cudaMemcpyDeviceToHost, s), "copy h back");
+  if (h_status)
+    CK(cudaMemcpyAsync(h_status, d_status, nd * sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+       "copy status back");
+  if (h_nsteps)
+    CK(cudaMemcpyAsync(h_nsteps, d_nsteps, nd * sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+       "copy nsteps back");
+  CK(cudaStreamSynchronize(s), "synchronising");
+#undef CK
+  return CHEM_OK;
+}
+
+}  // extern "C"

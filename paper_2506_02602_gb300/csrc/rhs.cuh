@@ -1,0 +1,203 @@
+// rhs.cuh -- device right-hand side dY/dt of one constant-(rho, e) cell.
+//
+// Per evaluation: temperature from (e, Y) by Newton on NASA-7 (Eq. 10; calculate_T of
+// Table 1), species Gibbs functions, Arrhenius / third-body / Troe forward rates,
+// reverse rates from equilibrium constants (Sec. 2.1.2), law of mass action (Eq. 16),
+// and F_k = W_k wdot_k / rho (Eq. 14, 20 at constant density).
+//
+// Arithmetic layout (the FP64 pipe of GB300 issues 2 lanes/clk/SM, so every fp64
+// operation counts):
+//   - Newton works on mixture coefficients m_i = sum_k (Y_k / W_k) ec_ki, assembled once
+//     per evaluation (54 FMAs), so each iteration is two Horner chains and a divide;
+//   - equilibrium constants come from per-species G_k = exp(-g_k / RT) and 1/G_k:
+//     1/K_c,j = prod_reactants G * prod_products (1/G) * (R_u T / p_ref)^(sum nu), i.e.
+//     9 exponentials + 9 divides per evaluation instead of one exponential per reaction;
+//   - forward rates are exp(ln A + beta ln T - Ta / T), one exponential per reaction
+//     (none for temperature-independent rates).
+#pragma once
+
+#include <cmath>
+#include <utility>
+
+#include "mech.cuh"
+
+namespace chem {
+
+// Mixture internal-energy coefficients: e/R_u = T (m0 + T (m1 + T (m2 + T (m3 + T m4)))) + m5
+__device__ __forceinline__ void mix_ecoef(const MechTables &mt, int range, const double (&yw)[NSP],
+                                          double (&m)[6]) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) s = fma(yw[k], mt.ec[range][k][i], s);
+    m[i] = s;
+  }
+}
+
+__device__ __forceinline__ double e_over_R(const double (&m)[6], double T) {
+  return fma(T, fma(T, fma(T, fma(T, fma(T, m[4], m[3]), m[2]), m[1]), m[0]), m[5]);
+}
+
+__device__ __forceinline__ double cv_over_R(const double (&m)[6], double T) {
+  return fma(T, fma(T, fma(T, fma(T, 5.0 * m[4], 4.0 * m[3]), 3.0 * m[2]), 2.0 * m[1]), m[0]);
+}
+
+// Temperature from e/R_u and Y/W.  T: in = starting guess (1500 K if not positive and
+// finite), out = root.  Newton stops at |dT| <= 1e-12 T within 30 iterations; on a
+// non-positive / non-finite iterate or no convergence, bisection on [200, 6000] K.
+__device__ __forceinline__ bool solve_T(const MechTables &mt, const double (&yw)[NSP], double eR,
+                                     double &T) {
+  double Tn = (isfinite(T) && T > 0.0) ? T : 1500.0;
+  int range = Tn >= mt.T_mid;
+  double m[6];
+  mix_ecoef(mt, range, yw, m);
+  for (int it = 0; it < 30; ++it) {
+    const int r = Tn >= mt.T_mid;
+    if (r != range) {
+      range = r;
+      mix_ecoef(mt, range, yw, m);
+    }
+    const double dT = (e_over_R(m, Tn) - eR) / cv_over_R(m, Tn);
+    Tn -= dT;
+    if (!isfinite(Tn) || Tn <= 0.0) break;
+    if (fabs(dT) <= 1e-12 * Tn) {
+      T = Tn;
+      return true;
+    }
+  }
+  // bracketed fallback
+  double lo = 200.0, hi = 6000.0, mlo[6], mhi[6];
+  mix_ecoef(mt, lo >= mt.T_mid, yw, mlo);
+  mix_ecoef(mt, hi >= mt.T_mid, yw, mhi);
+  if (e_over_R(mlo, lo) - eR > 0.0 || e_over_R(mhi, hi) - eR < 0.0) return false;
+  for (int it = 0; it < 200 && hi - lo > 1e-13 * hi; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    mix_ecoef(mt, mid >= mt.T_mid, yw, m);
+    if (e_over_R(m, mid) - eR > 0.0) hi = mid; else lo = mid;
+  }
+  T = 0.5 * (lo + hi);
+  return true;
+}
+
+// Quantities shared by every reaction of one evaluation.
+struct RateInputs {
+  double lnT, invT, RTP, PRT, ctot;
+  double c[NSP];   // clamped concentrations, mol/m^3
+  double G[NSP];   // exp(-g_k / (R_u T))
+  double iG[NSP];  // 1 / G_k
+};
+
+// Troe broadening factor (Gilbert, Luther & Troe 1983).
+template <int J>
+__device__ __forceinline__ double troe_F(const MechTables &mt, double T, double invT, double Pr) {
+  constexpr int n = kRx[J].troe_n;
+  if constexpr (n == 0) {
+    return 1.0;
+  } else {
+    const double a = mt.troe_a[J];
+    double Fc = (1.0 - a) * exp(-T * mt.troe_i3[J]) + a * exp(-T * mt.troe_i1[J]);
+    if constexpr (n == 4) Fc += exp(-mt.troe_T2[J] * invT);
+    const double lFc = log10(Fc);
+    const double cc = -0.4 - 0.67 * lFc;
+    const double nn = 0.75 - 1.27 * lFc;
+    const double x = log10(Pr) + cc;
+    const double f1 = x / (nn - 0.14 * x);
+    return exp10(lFc / (1.0 + f1 * f1));
+  }
+}
+
+// Rate of progress of reaction J added into wdot (law of mass action, Eq. 16).
+template <int J>
+__device__ __forceinline__ void reaction(const MechTables &mt, const RateInputs &in, double T,
+                                         double (&wdot)[NSP]) {
+  constexpr RxStruct R = kRx[J];
+  constexpr int dnu = n_prod(R) - n_reac(R);
+  static_assert(dnu >= -1 && dnu <= 1, "compiled structure assumes |sum nu| <= 1");
+  double kf = mt.kconst[J] ? mt.A[J] : exp(fma(mt.beta[J], in.lnT, mt.lnA[J]) - mt.Ta[J] * in.invT);
+  double M = 0.0;
+  if constexpr (R.type != ELEM) {
+    M = in.ctot;
+    if (mt.has_eff[J]) {
+#pragma unroll
+      for (int k = 0; k < NSP; ++k) M = fma(mt.effm1[J][k], in.c[k], M);
+    }
+  }
+  if constexpr (R.type == FALLOFF) {
+    const double k0 = exp(fma(mt.beta0[J], in.lnT, mt.lnA0[J]) - mt.Ta0[J] * in.invT);
+    const double Pr = k0 * M / kf;
+    kf = (Pr > 0.0) ? kf * (Pr / (1.0 + Pr)) * troe_F<J>(mt, T, in.invT, Pr) : 0.0;
+  }
+  double qf = kf * in.c[R.r0];
+  if constexpr (R.r1 >= 0) qf *= in.c[R.r1];
+  double q = qf;
+  if (mt.reversible[J]) {
+    double kr = kf * in.G[R.r0];
+    if constexpr (R.r1 >= 0) kr *= in.G[R.r1];
+    kr *= in.iG[R.p0];
+    if constexpr (R.p1 >= 0) kr *= in.iG[R.p1];
+    if constexpr (dnu == 1) kr *= in.RTP;
+    if constexpr (dnu == -1) kr *= in.PRT;
+    double qr = kr * in.c[R.p0];
+    if constexpr (R.p1 >= 0) qr *= in.c[R.p1];
+    q = qf - qr;
+  }
+  if constexpr (R.type == THIRD_BODY) q *= M;
+  wdot[R.r0] -= q;
+  if constexpr (R.r1 >= 0) wdot[R.r1] -= q;
+  wdot[R.p0] += q;
+  if constexpr (R.p1 >= 0) wdot[R.p1] += q;
+}
+
+template <int... J>
+__device__ __forceinline__ void all_reactions(const MechTables &mt, const RateInputs &in, double T,
+                                              double (&wdot)[NSP], std::integer_sequence<int, J...>) {
+  (reaction<J>(mt, in, T, wdot), ...);
+}
+
+// Molar production rates wdot (mol/m^3/s) at temperature T and clamped concentrations c.
+__device__ __forceinline__ void production_rates(const MechTables &mt, double T,
+                                                 const double (&c)[NSP], double (&wdot)[NSP]) {
+  RateInputs in;
+  in.lnT = log(T);
+  in.invT = 1.0 / T;
+  in.RTP = R_U * T / P_REF;
+  in.PRT = 1.0 / in.RTP;
+  const int range = T >= mt.T_mid;
+  double ctot = 0.0;
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) {
+    in.c[k] = c[k];
+    ctot += c[k];
+    const double *hc = mt.hc[range][k];
+    const double *sc = mt.sc[range][k];
+    const double hRT = fma(T, fma(T, fma(T, fma(T, hc[4], hc[3]), hc[2]), hc[1]), hc[0]) + hc[5] * in.invT;
+    const double sR = fma(sc[0], in.lnT, fma(T, fma(T, fma(T, fma(T, sc[4], sc[3]), sc[2]), sc[1]), sc[5]));
+    // clamp keeps G finite far outside the tables' range
+    const double g = fmin(fmax(hRT - sR, -700.0), 700.0);
+    in.G[k] = exp(-g);
+    in.iG[k] = 1.0 / in.G[k];
+    wdot[k] = 0.0;
+  }
+  in.ctot = ctot;
+  all_reactions(mt, in, T, wdot, std::make_integer_sequence<int, NRX>{});
+}
+
+// dY/dt of one cell at fixed (rho, e).  T: in = Newton guess, out = solved T.
+// Returns false when the temperature solve fails.
+__device__ __forceinline__ bool cell_rhs(const MechTables &mt, const double (&Y)[NSP], double rho,
+                                         double invRho, double eR, double &T, double (&F)[NSP]) {
+  double yw[NSP];
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) yw[k] = Y[k] * mt.invW[k];
+  if (!solve_T(mt, yw, eR, T)) return false;
+  double c[NSP], wdot[NSP];
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) c[k] = fmax(rho * yw[k], 0.0);
+  production_rates(mt, T, c, wdot);
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) F[k] = wdot[k] * mt.W[k] * invRho;
+  return true;
+}
+
+}  // namespace chem

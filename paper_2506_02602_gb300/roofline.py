@@ -1,0 +1,96 @@
+"""Credited floating-point work of the integrator, for the roofline.
+
+The work of one launch is credited from the algorithm, not from what the hardware ran:
+per attempted RK step, five right-hand-side evaluations plus the register updates and
+the WRMS norm of Eq. 21-22; per cell, the final temperature solve.  Each right-hand
+side is counted from the mechanism structure in the formulation the kernels use:
+
+  Newton on mixture coefficients (assembly + 2 iterations), ln T, 1/T, per species the
+  NASA-7 Gibbs function and G_k = exp(-g_k/RT) with its reciprocal, per reaction the
+  Arrhenius exponential, the products of the law of mass action (Eq. 16) with the
+  equilibrium-constant factors, the third-body sums, the Troe fall-off terms, and the
+  conversion F_k = W_k wdot_k / rho.
+
+Add, multiply, compare-free min/max and divide count 1 flop, an FMA 2, and every
+exp / log / exp10 / log10 / sqrt is credited a fixed TRANSCENDENTAL flops.  The FP64
+pipe of GB300 spends about 20 FMA slots (40 flops) on a library exp, so this credit is
+conservative: the reported fraction understates the FP64 pipe's busy time, which the
+ncu summary reports separately.
+"""
+from __future__ import annotations
+
+TRANSCENDENTAL = 20
+
+# compiled reaction structure: (n_reactants, n_products, type, troe_n); type 0/1/2 =
+# elementary / third body / fall-off.  Mirrors csrc/mech.cuh.
+_RX = [
+    (2, 2, 0, 0), (2, 2, 0, 0), (2, 2, 0, 0), (2, 2, 0, 0),
+    (1, 2, 1, 0), (2, 1, 1, 0), (2, 1, 1, 0), (2, 1, 1, 0),
+    (2, 1, 2, 4),
+    (2, 2, 0, 0), (2, 2, 0, 0), (2, 2, 0, 0), (2, 2, 0, 0), (2, 2, 0, 0), (2, 2, 0, 0),
+    (1, 2, 2, 3),
+    (2, 2, 0, 0), (2, 2, 0, 0), (2, 2, 0, 0), (2, 2, 0, 0), (2, 2, 0, 0),
+]
+NSP = 9
+NEWTON_ITERS = 2
+
+
+def newton_flops(iters: int = NEWTON_ITERS) -> int:
+    assembly = NSP + 6 * NSP * 2          # Y/W, 6 mixture coefficients x 9 FMAs
+    per_iter = 5 * 2 + (4 * 2 + 4) + 3 + 1  # e(T) Horner, cv(T) Horner + scalings, update, test
+    return assembly + iters * per_iter
+
+
+def rhs_flops(mech: dict | None = None) -> int:
+    """Credited flops of one right-hand side.  ``mech`` (chem_inputs layout) marks
+    temperature-independent rates (no exponential) and third-body efficiency lists."""
+    T = TRANSCENDENTAL
+    f = newton_flops()
+    f += NSP                                   # concentrations
+    f += T + 1 + 2 + 1 + (NSP - 1)             # ln T, 1/T, RT/p, p/RT, total concentration
+    f += NSP * (10 + 10 + 1 + T + 1)           # h/RT, s/R, g, G = exp(-g), 1/G
+    for j, (nr, npr, typ, troe_n) in enumerate(_RX):
+        kconst = mech is not None and mech["b"][j] == 0.0 and mech["Ea"][j] == 0.0
+        f += 0 if kconst else T + 4            # Arrhenius exponential
+        f += nr                                # forward product
+        f += nr + npr + (1 if nr != npr else 0) + npr + 1  # reverse rate, product, difference
+        f += nr + npr                          # production-rate updates
+        if typ != 0:
+            has_eff = mech is None or any(abs(x - 1.0) > 0 for x in mech["eff"][j])
+            f += 2 * NSP if has_eff else 0     # [M]
+        if typ == 1:
+            f += 1
+        if typ == 2:
+            f += T + 4 + 2                     # k0, Pr
+            f += (3 if troe_n == 4 else 2) * (T + 2) + 3  # F_cent
+            f += 3 * T + 4 + 1 + 3 + 3 + 4     # log10 F_cent, log10 Pr, exp10, Troe algebra
+    f += 2 * NSP                               # F_k = W_k wdot_k / rho
+    return f
+
+
+def step_flops(mech: dict | None = None) -> int:
+    """Credited flops of one attempted step (5 RHS + Eq. 21 updates + Eq. 22 control)."""
+    updates = 5 * (3 + NSP * 3 * 2)            # h a, h b, h e and 3 FMAs per component
+    wrms = NSP * (2 + 1 + 2 + 1 + 2) + 2 + T_SQRT
+    control = 2 * T_SQRT + 1 + 3 + 1
+    return 5 * rhs_flops(mech) + updates + wrms + control
+
+
+T_SQRT = TRANSCENDENTAL
+
+
+def cell_flops(mech: dict | None = None) -> int:
+    """Per-cell work outside the step loop: 1/rho, e/R and the final temperature solve."""
+    return 2 + newton_flops()
+
+
+def launch_flops(total_attempted_steps: int, ncells: int, mech: dict | None = None) -> float:
+    """Credited flops of one launch from the attempted-step total the kernel reports."""
+    return float(total_attempted_steps) * step_flops(mech) + float(ncells) * cell_flops(mech)
+
+
+# FP64 peak of GB300 derived from unit counts and clocks: 152 SMs x 2 FP64 FMA lanes per
+# clock per SM (measured: 1192.8 GFLOP/s at ~1.96 GHz) x 2 flops x 2.070 GHz max clock.
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+# FP32: 152 SMs x 128 FMA lanes x 2 flops x 2.070 GHz (measured 72.9 TFLOP/s at ~1.96 GHz)
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070

@@ -1,0 +1,125 @@
+"""Host-side checks of the C ABI (no GPU needed).
+
+* libchem.so builds, loads and exports every entry point include/chem.h declares;
+* the ctypes structures have the sizes and field offsets of the C header (compiled
+  with gcc here);
+* chem_setup's validation: wrong structure -> UNSUPPORTED, unbalanced reaction or
+  discontinuous NASA-7 tables -> INVALID, and a valid mechanism without a device ->
+  CUDA error (no CPU fallback).
+"""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from chem_inputs import mechanism as M
+from paper_2506_02602_gb300 import build as B
+from paper_2506_02602_gb300 import chem
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "chem.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return chem.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(chem_[A-Za-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 7
+    out = subprocess.run(["nm", "-D", "--defined-only", chem.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (chem_[A-Za-z_0-9]+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        getattr(lib, n)
+
+
+def test_struct_layout_matches_header(tmp_path):
+    prog = tmp_path / "sizes.c"
+    prog.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "chem.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\n", sizeof(chem_mechanism), sizeof(chem_options), sizeof(chem_state),
+         sizeof(chem_stats));
+  printf("%zu %zu %zu %zu\n", offsetof(chem_mechanism, eff), offsetof(chem_mechanism, reversible),
+         offsetof(chem_state, d_nsteps), offsetof(chem_stats, status_count));
+  return 0;
+}''')
+    exe = tmp_path / "sizes"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)
+    a, b = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
+    assert [int(x) for x in a.split()] == [C.sizeof(chem.Mechanism), C.sizeof(chem.Options),
+                                          C.sizeof(chem.State), C.sizeof(chem.Stats)]
+    assert [int(x) for x in b.split()] == [chem.Mechanism.eff.offset, chem.Mechanism.reversible.offset,
+                                          chem.State.d_nsteps.offset, chem.Stats.status_count.offset]
+
+
+def _setup_rc(lib, mech, variant=0):
+    m = chem.make_mechanism(mech)
+    opt = chem.Options()
+    opt.variant = variant
+    h = C.c_void_p()
+    rc = lib.chem_setup(C.byref(m), C.byref(opt), C.byref(h))
+    msg = lib.chem_last_error(None).decode()
+    if rc == 0:
+        lib.chem_teardown(h)
+    return rc, msg
+
+
+def test_setup_rejects_other_structure(lib):
+    m = M.build(0)
+    m["nu_r"] = m["nu_r"].copy()
+    m["nu_f"] = m["nu_f"].copy()
+    # swap the products of two reactions: still balanced, but not the compiled structure
+    m["nu_r"][[9, 10]] = m["nu_r"][[10, 9]]
+    rc, msg = _setup_rc(lib, m)
+    assert rc == chem.ERR_UNSUPPORTED and "stoichiometry" in msg
+    small = M.custom(["X"], [0.028], [[0, 0, 2]], np.ones((1, 7)), np.ones((1, 7)), [])
+    rc, msg = _setup_rc(lib, small)
+    assert rc == chem.ERR_UNSUPPORTED
+
+
+def test_setup_rejects_unbalanced_reaction(lib):
+    m = M.build(0)
+    m["nu_r"] = m["nu_r"].copy()
+    m["nu_r"][0, M.SPECIES.index("OH")] = 0
+    m["nu_r"][0, M.SPECIES.index("H")] = 1  # H + O2 -> O + H: loses an oxygen
+    rc, msg = _setup_rc(lib, m)
+    assert rc == chem.ERR_INVALID and "balance" in msg
+
+
+def test_setup_rejects_discontinuous_thermo(lib):
+    m = M.build(0)
+    m["nasa_hi"] = m["nasa_hi"].copy()
+    m["nasa_hi"][2, 5] += 50.0
+    rc, msg = _setup_rc(lib, m)
+    assert rc == chem.ERR_INVALID and "discontinuous" in msg
+
+
+def test_setup_rejects_bad_options(lib):
+    rc, msg = _setup_rc(lib, M.build(0), variant=7)
+    assert rc == chem.ERR_INVALID
+
+
+def test_valid_mechanism_needs_a_device(lib):
+    import torch
+    rc, msg = _setup_rc(lib, M.build(0))
+    if torch.cuda.is_available():
+        assert rc == chem.OK
+    else:
+        assert rc == chem.ERR_CUDA and "CUDA device" in msg
