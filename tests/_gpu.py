@@ -39,25 +39,46 @@ def run_device(ctx, rho, e, Y, T, dt, rtol=1e-6, atol=1e-10, h=None, ld=None, st
     return out
 
 
+def sensitivity(o, rho, e, Y, T, dt, rel=1e-13, **kw):
+    """The oracle's own conditioning: how far its result moves when e is perturbed by
+    rel (about 100x the rounding of one step).  Returns (|dT|/T, max_k |dY_k|) per cell."""
+    a = o.integrate(rho, e, Y, T, dt, **kw)
+    b = o.integrate(rho, e * (1.0 + rel), Y, T, dt, **kw)
+    return np.abs(a["T"] - b["T"]) / np.abs(a["T"]), np.max(np.abs(a["Y"] - b["Y"]), axis=0)
+
+
 def compare(gpu, ref, tol_T=FP64_TOL_T, tol_Y=FP64_TOL_Y, knife=KNIFE_EDGE, loose_T=1e-4,
-            loose_Y=1e-6, max_knife_frac=0.01, check_steps=True):
+            loose_Y=1e-6, max_knife_frac=0.01, check_steps=True, cond=None):
     """Element-wise parity.  Cells whose oracle decisions were on a rounding knife edge
     (margin < knife) may take another step sequence: they are counted and held to the
-    rtol-level bound instead.  Returns a dict of the observed errors."""
+    rtol-level bound instead.  With cond = sensitivity(...), cells where the oracle's
+    own result moves by more than 1e-11 under a 1e-13 input perturbation (ignition in
+    progress at the end of dt) are ill-conditioned: they get the same rtol-level bound.
+    Every other cell meets the strict bound with equal step counts.  Returns a dict of
+    the observed errors."""
     np.testing.assert_array_equal(gpu["status"], ref["status"])
     ok = ref["status"] == 0
     edge = ref["margin"] < knife
     strict = ok & ~edge
     relT = np.abs(gpu["T"] - ref["T"]) / np.abs(ref["T"])
     absY = np.max(np.abs(gpu["Y"] - ref["Y"]), axis=0)
+    ill = np.zeros(relT.shape, bool)
+    if cond is not None:
+        # a 1e-13 input perturbation grown 100-fold: rounding differences of two fp64
+        # implementations grow alike and can flip later accept/reject decisions
+        ill = (cond[0] > 1e-11) | (cond[1] > 1e-11)
+    strict = strict & ~ill
+    loose = ok & (edge | ill)
     res = {"n": gpu["T"].size, "strict": int(strict.sum()), "edge": int((ok & edge).sum()),
+           "ill_conditioned": int((ok & ill & ~edge).sum()),
            "max_relT": float(relT[strict].max(initial=0.0)),
-           "max_absY": float(absY[strict].max(initial=0.0))}
+           "max_absY": float(absY[strict].max(initial=0.0)),
+           "max_relT_loose": float(relT[loose].max(initial=0.0)),
+           "max_absY_loose": float(absY[loose].max(initial=0.0))}
     assert res["edge"] <= max(1, max_knife_frac * res["n"]), res
     assert res["max_relT"] <= tol_T, res
     assert res["max_absY"] <= tol_Y, res
     if check_steps:
         np.testing.assert_array_equal(gpu["nsteps"][strict], ref["nsteps"][strict])
-    if (ok & edge).any():
-        assert relT[ok & edge].max() <= loose_T and absY[ok & edge].max() <= loose_Y, res
+    assert res["max_relT_loose"] <= loose_T and res["max_absY_loose"] <= loose_Y, res
     return res
