@@ -201,6 +201,16 @@ int chem_integrate_host(chem_ctx *ctx, int64_t ncells, const double *h_rho,
                         double *h_h, int32_t *h_status, int32_t *h_nsteps, double dt,
                         double rtol, double atol, void *stream);
 
+/*
+ * Diagnostic: evaluate one of the device math routines the integration kernels use on
+ * n fp64 arguments (device pointers d_x -> d_y), so tests can check them against the
+ * CUDA library.  op: 0 table-driven exp, 1 table-driven log (Tang's methods, used by
+ * the kernels), 2 library exp, 3 library log.  Not part of the integration path; the
+ * paper has no counterpart.  Errors: unknown op or n < 0 -> CHEM_ERR_INVALID.
+ * Asynchronous on stream.
+ */
+int chem_diag_math(int op, int64_t n, const double *d_x, double *d_y, void *stream);
+
 /* Library version, as major * 10000 + minor * 100 + patch. */
 int chem_version(void);
 

@@ -95,6 +95,7 @@ def load() -> C.CDLL:
         "chem_state_from_TPY": (C.c_int, [vp, i64, vp, vp, vp, i64, vp, vp, vp]),
         "chem_integrate": (C.c_int, [vp, C.POINTER(State), i64, dbl, dbl, dbl, vp, vp]),
         "chem_integrate_host": (C.c_int, [vp, i64, vp, vp, vp, i64, vp, vp, vp, vp, dbl, dbl, dbl, vp]),
+        "chem_diag_math": (C.c_int, [C.c_int, i64, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -102,6 +103,18 @@ def load() -> C.CDLL:
         fn.argtypes = args
     _lib = L
     return L
+
+
+def diag_math(op: int, x, stream=None):
+    """chem_diag_math: 0 table exp, 1 table log, 2 library exp, 3 library log on a
+    float64 CUDA tensor; returns a new tensor."""
+    import torch
+    _check_f64_cuda("x", x)
+    y = torch.empty_like(x)
+    rc = load().chem_diag_math(op, x.numel(), _ptr(x), _ptr(y), _stream(stream))
+    if rc != OK:
+        raise ChemError(rc, "chem_diag_math failed")
+    return y
 
 
 def make_mechanism(m: dict) -> Mechanism:

@@ -131,18 +131,13 @@ int build_tables(const chem_mechanism *m, MechTables *t) {
       t->ec[r][k][3] = a[3] / 4.0;
       t->ec[r][k][4] = a[4] / 5.0;
       t->ec[r][k][5] = a[5];
-      t->hc[r][k][0] = a[0];
-      t->hc[r][k][1] = a[1] / 2.0;
-      t->hc[r][k][2] = a[2] / 3.0;
-      t->hc[r][k][3] = a[3] / 4.0;
-      t->hc[r][k][4] = a[4] / 5.0;
-      t->hc[r][k][5] = a[5];
-      t->sc[r][k][0] = a[0];
-      t->sc[r][k][1] = a[1];
-      t->sc[r][k][2] = a[2] / 2.0;
-      t->sc[r][k][3] = a[3] / 3.0;
-      t->sc[r][k][4] = a[4] / 4.0;
-      t->sc[r][k][5] = a[6];
+      t->gc[r][k][0] = a[0];
+      t->gc[r][k][1] = -a[1] / 2.0;
+      t->gc[r][k][2] = -a[2] / 6.0;
+      t->gc[r][k][3] = -a[3] / 12.0;
+      t->gc[r][k][4] = -a[4] / 20.0;
+      t->gc[r][k][5] = a[5];
+      t->gc[r][k][6] = -a[6];
     }
   }
   for (int j = 0; j < NRX; ++j) {
@@ -150,7 +145,7 @@ int build_tables(const chem_mechanism *m, MechTables *t) {
     t->lnA[j] = std::log(m->A[j]);
     t->beta[j] = m->b[j];
     t->Ta[j] = m->Ea[j] / R_U;
-    t->kconst[j] = (m->b[j] == 0.0 && m->Ea[j] == 0.0);
+    t->kconst[j] = m->Ea[j] != 0.0 ? 0 : m->b[j] == 0.0 ? 1 : m->b[j] == -1.0 ? 2 : m->b[j] == -2.0 ? 3 : 0;
     t->reversible[j] = m->reversible[j] != 0;
     if (kRx[j].type == FALLOFF) {
       t->lnA0[j] = std::log(m->A0[j]);
@@ -167,6 +162,26 @@ int build_tables(const chem_mechanism *m, MechTables *t) {
       any |= t->effm1[j][k] != 0.0;
     }
     t->has_eff[j] = any;
+  }
+  // fp32 copies for the mixed-precision kernel
+  t->ln_R_over_Pref = std::log(R_U / P_REF);
+  for (int k = 0; k < NSP; ++k) {
+    t->f.W[k] = (float)t->W[k];
+    t->f.invW[k] = (float)t->invW[k];
+  }
+  for (int j = 0; j < NRX; ++j) {
+    t->f.A[j] = (float)t->A[j];
+    t->f.lnA[j] = (float)t->lnA[j];
+    t->f.beta[j] = (float)t->beta[j];
+    t->f.Ta[j] = (float)t->Ta[j];
+    t->f.lnA0[j] = (float)t->lnA0[j];
+    t->f.beta0[j] = (float)t->beta0[j];
+    t->f.Ta0[j] = (float)t->Ta0[j];
+    t->f.troe_a[j] = (float)t->troe_a[j];
+    t->f.troe_i3[j] = (float)t->troe_i3[j];
+    t->f.troe_i1[j] = (float)t->troe_i1[j];
+    t->f.troe_T2[j] = (float)t->troe_T2[j];
+    for (int k = 0; k < NSP; ++k) t->f.effm1[j][k] = (float)t->effm1[j][k];
   }
   return CHEM_OK;
 }

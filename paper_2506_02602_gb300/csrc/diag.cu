@@ -1,0 +1,34 @@
+// diag.cu -- chem_diag_math: the kernels' device math routines on caller arrays, for
+// accuracy tests against the CUDA library.
+#include <cuda_runtime.h>
+
+#include "fastmath.cuh"
+#include "internal.cuh"
+
+namespace chem {
+
+__global__ void k_diag_math(int op, int64_t n, const double *__restrict__ x, double *__restrict__ y) {
+  load_math_tables();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  double r;
+  switch (op) {
+    case 0: r = exp_t(v); break;
+    case 1: r = log_t(v); break;
+    case 2: r = exp(v); break;
+    default: r = log(v); break;
+  }
+  y[i] = r;
+}
+
+}  // namespace chem
+
+extern "C" int chem_diag_math(int op, int64_t n, const double *d_x, double *d_y, void *stream) {
+  if (op < 0 || op > 3 || n < 0) return CHEM_ERR_INVALID;
+  if (n == 0) return CHEM_OK;
+  if (!d_x || !d_y) return CHEM_ERR_INVALID;
+  const int block = 256;
+  chem::k_diag_math<<<(unsigned)((n + block - 1) / block), block, 0, (cudaStream_t)stream>>>(op, n, d_x, d_y);
+  return cudaGetLastError() == cudaSuccess ? CHEM_OK : CHEM_ERR_CUDA;
+}

@@ -17,8 +17,11 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include <type_traits>
+
 #include "internal.cuh"
 #include "rhs.cuh"
+#include "rhs_mixed.cuh"
 
 namespace chem {
 
@@ -77,10 +80,16 @@ __device__ __forceinline__ void accumulate_stats(chem_stats *st, bool live, int 
 }
 
 // Integrate one cell in place.  Returns the status; counts attempts and RHS calls.
+// V = CHEM_VARIANT_FP64: every register fp64.  V = CHEM_VARIANT_MIXED: the stage
+// register U and the stage derivative F are fp32 (cell_rhs_mixed); the solution X, the
+// saved y_n, the error register E, the WRMS norm and the controller stay fp64.
+template <int V>
 __device__ __forceinline__ int integrate_cell(const MechTables &mt, double rho, double e,
                                               double (&X)[NSP], double &T, double &h,
                                               const StepParams &p, int &nacc, int &nrej,
                                               int &nrhs) {
+  constexpr bool kMixed = V == CHEM_VARIANT_MIXED;
+  using SReal = std::conditional_t<kMixed, float, double>;
   bool bad = !(isfinite(rho) && rho > 0.0 && isfinite(e));
 #pragma unroll
   for (int k = 0; k < NSP; ++k) bad |= !isfinite(X[k]);
@@ -90,6 +99,7 @@ __device__ __forceinline__ int integrate_cell(const MechTables &mt, double rho, 
   }
   const double dt = p.dt;
   const double invRho = 1.0 / rho;
+  const float rho_f = (float)rho, invRho_f = (float)invRho;
   const double eR = e / R_U;
   int status = CHEM_CELL_OK;
   double t = 0.0;
@@ -97,21 +107,36 @@ __device__ __forceinline__ int integrate_cell(const MechTables &mt, double rho, 
     if (nacc + nrej >= p.max_steps) { status = CHEM_CELL_MAX_STEPS; break; }
     if (h < 1e-15 * dt) { status = CHEM_CELL_H_UNDERFLOW; break; }
     if (h > dt - t) h = dt - t;
-    double Xs[NSP], U[NSP], E[NSP];
+    double Xs[NSP], E[NSP];
+    SReal U[NSP];
 #pragma unroll
-    for (int k = 0; k < NSP; ++k) { Xs[k] = X[k]; U[k] = X[k]; E[k] = 0.0; }
+    for (int k = 0; k < NSP; ++k) { Xs[k] = X[k]; U[k] = (SReal)X[k]; E[k] = 0.0; }
     int failed = 0;
 #pragma unroll 1
     for (int s = 0; s < 5; ++s) {
-      double F[NSP];
+      SReal F[NSP];
       ++nrhs;
-      if (!cell_rhs(mt, U, rho, invRho, eR, T, F)) { failed = s + 1; break; }
+      bool ok;
+      if constexpr (kMixed) ok = cell_rhs_mixed(mt, U, rho_f, invRho_f, eR, T, F);
+      else ok = cell_rhs(mt, U, rho, invRho, eR, T, F);
+      if (!ok) { failed = s + 1; break; }
       const double ha = h * c_ls_a[s], hb = h * c_ls_b[s], he = h * c_ls_e[s];
+      if constexpr (kMixed) {
+        const float ha_f = (float)ha;
 #pragma unroll
-      for (int k = 0; k < NSP; ++k) {
-        E[k] = fma(he, F[k], E[k]);
-        U[k] = fma(ha, F[k], X[k]);
-        X[k] = fma(hb, F[k], X[k]);
+        for (int k = 0; k < NSP; ++k) {
+          U[k] = fmaf(ha_f, F[k], (float)X[k]);
+          const double Fk = (double)F[k];
+          E[k] = fma(he, Fk, E[k]);
+          X[k] = fma(hb, Fk, X[k]);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) {
+          E[k] = fma(he, F[k], E[k]);
+          U[k] = fma(ha, F[k], X[k]);
+          X[k] = fma(hb, F[k], X[k]);
+        }
       }
     }
     if (failed == 1) {
@@ -160,8 +185,10 @@ __device__ __forceinline__ int integrate_cell(const MechTables &mt, double rho, 
   return status;
 }
 
-__global__ void __launch_bounds__(128) k_lsrk_fp64(const __grid_constant__ MechTables mt,
-                                                   const CellArgs a, const StepParams p) {
+template <int V>
+__global__ void __launch_bounds__(128) k_lsrk(const __grid_constant__ MechTables mt,
+                                              const CellArgs a, const StepParams p) {
+  load_math_tables();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = i < a.n;
   int nacc = 0, nrej = 0, nrhs = 0, status = 0;
@@ -175,7 +202,7 @@ __global__ void __launch_bounds__(128) k_lsrk_fp64(const __grid_constant__ MechT
       const double h0 = a.h[i];
       if (isfinite(h0) && h0 > 0.0) h = h0;
     }
-    status = integrate_cell(mt, a.rho[i], a.e[i], X, T, h, p, nacc, nrej, nrhs);
+    status = integrate_cell<V>(mt, a.rho[i], a.e[i], X, T, h, p, nacc, nrej, nrhs);
 #pragma unroll
     for (int k = 0; k < NSP; ++k) a.Y[k * a.ld + i] = X[k];
     a.T[i] = T;
@@ -210,8 +237,10 @@ cudaError_t launch_lsrk(int variant, const MechTables &mt, const CellArgs &a, co
   if (a.n <= 0) return cudaSuccess;
   if (block != 128) block = 128;  // the kernel's launch bounds
   const int64_t grid = (a.n + block - 1) / block;
-  (void)variant;
-  k_lsrk_fp64<<<(unsigned)grid, block, 0, s>>>(mt, a, p);
+  if (variant == CHEM_VARIANT_MIXED)
+    k_lsrk<CHEM_VARIANT_MIXED><<<(unsigned)grid, block, 0, s>>>(mt, a, p);
+  else
+    k_lsrk<CHEM_VARIANT_FP64><<<(unsigned)grid, block, 0, s>>>(mt, a, p);
   return cudaGetLastError();
 }
 

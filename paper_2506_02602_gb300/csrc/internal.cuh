@@ -6,7 +6,7 @@
 
 #include <cstdint>
 
-#include "../../include/chem.h"
+#include "chem.h"
 #include "mech.cuh"
 
 namespace chem {

@@ -59,6 +59,17 @@ constexpr RxStruct kRx[NRX] = {
 __host__ __device__ constexpr int n_reac(const RxStruct &r) { return (r.r0 >= 0) + (r.r1 >= 0); }
 __host__ __device__ constexpr int n_prod(const RxStruct &r) { return (r.p0 >= 0) + (r.p1 >= 0); }
 
+// fp32 copies of the rate coefficients for the mixed-precision variant.
+struct MechTablesF32 {
+  float A[NRX];
+  float W[NSP];
+  float invW[NSP];
+  float lnA[NRX], beta[NRX], Ta[NRX];
+  float lnA0[NRX], beta0[NRX], Ta0[NRX];
+  float troe_a[NRX], troe_i3[NRX], troe_i1[NRX], troe_T2[NRX];
+  float effm1[NRX][NSP];
+};
+
 // Per-context tables (host-built from chem_mechanism by build_tables()).
 struct MechTables {
   double T_mid;
@@ -66,12 +77,12 @@ struct MechTables {
   double invW[NSP];
   // e_k W_k / R_u = sum_i ec[i] T^(i+1) + ec[5]: {a1 - 1, a2/2, a3/3, a4/4, a5/5, a6}
   double ec[2][NSP][6];
-  // h_k / (R_u T) = hc0 + hc1 T + hc2 T^2 + hc3 T^3 + hc4 T^4 + hc5 / T
-  double hc[2][NSP][6];
-  // s_k / R_u = sc0 ln T + sc1 T + sc2 T^2 + sc3 T^3 + sc4 T^4 + sc5
-  double sc[2][NSP][6];
-  // Arrhenius: k = exp(lnA + beta ln T - Ta / T); Ta = Ea / R_u.  kconst marks
-  // beta == Ta == 0 (k = A, no exponential).
+  // g_k / (R_u T) = h/RT - s/R = gc0 (1 - ln T) + gc1 T + gc2 T^2 + gc3 T^3 + gc4 T^4
+  //                 + gc5 / T + gc6  with {a1, -a2/2, -a3/6, -a4/12, -a5/20, a6, -a7}
+  double gc[2][NSP][7];
+  // Arrhenius: k = exp(lnA + beta ln T - Ta / T); Ta = Ea / R_u.  kconst selects a form
+  // without the exponential when Ea == 0: 1 for b == 0 (k = A), 2 for b == -1 (A / T),
+  // 3 for b == -2 (A / T^2); 0 otherwise.
   double lnA[NRX], beta[NRX], Ta[NRX], A[NRX];
   int32_t kconst[NRX];
   int32_t reversible[NRX];
@@ -81,6 +92,8 @@ struct MechTables {
   // third-body efficiencies minus one: [M] = sum_k c_k + sum_k effm1 c_k
   double effm1[NRX][NSP];
   int32_t has_eff[NRX];
+  double ln_R_over_Pref;  // ln(R_u / p_ref): ln(R_u T / p_ref) = ln T + this
+  MechTablesF32 f;
 };
 
 static_assert(sizeof(MechTables) < 16384, "MechTables must fit a kernel parameter block");

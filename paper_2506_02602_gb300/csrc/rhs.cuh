@@ -7,18 +7,21 @@
 //
 // Arithmetic layout (the FP64 pipe of GB300 issues 2 lanes/clk/SM, so every fp64
 // operation counts):
+//   - exponentials and logarithms are the table-driven exp_t / log_t (fastmath.cuh);
+//   - g_k / RT comes from one combined NASA-7 polynomial per species (6 FMAs);
 //   - Newton works on mixture coefficients m_i = sum_k (Y_k / W_k) ec_ki, assembled once
 //     per evaluation (54 FMAs), so each iteration is two Horner chains and a divide;
 //   - equilibrium constants come from per-species G_k = exp(-g_k / RT) and 1/G_k:
 //     1/K_c,j = prod_reactants G * prod_products (1/G) * (R_u T / p_ref)^(sum nu), i.e.
 //     9 exponentials + 9 divides per evaluation instead of one exponential per reaction;
 //   - forward rates are exp(ln A + beta ln T - Ta / T), one exponential per reaction
-//     (none for temperature-independent rates).
+//     (none for temperature-independent rates or A T^-1, A T^-2 with no activation).
 #pragma once
 
 #include <cmath>
 #include <utility>
 
+#include "fastmath.cuh"
 #include "mech.cuh"
 
 namespace chem {
@@ -39,8 +42,17 @@ __device__ __forceinline__ double e_over_R(const double (&m)[6], double T) {
   return fma(T, fma(T, fma(T, fma(T, fma(T, m[4], m[3]), m[2]), m[1]), m[0]), m[5]);
 }
 
-__device__ __forceinline__ double cv_over_R(const double (&m)[6], double T) {
-  return fma(T, fma(T, fma(T, fma(T, 5.0 * m[4], 4.0 * m[3]), 3.0 * m[2]), 2.0 * m[1]), m[0]);
+// cv/R = d(e/R)/dT from the scaled coefficients d = {m0, 2 m1, 3 m2, 4 m3, 5 m4}
+__device__ __forceinline__ double cv_over_R(const double (&d)[5], double T) {
+  return fma(T, fma(T, fma(T, fma(T, d[4], d[3]), d[2]), d[1]), d[0]);
+}
+
+__device__ __forceinline__ void cv_coef(const double (&m)[6], double (&d)[5]) {
+  d[0] = m[0];
+  d[1] = 2.0 * m[1];
+  d[2] = 3.0 * m[2];
+  d[3] = 4.0 * m[3];
+  d[4] = 5.0 * m[4];
 }
 
 // Temperature from e/R_u and Y/W.  T: in = starting guess (1500 K if not positive and
@@ -50,15 +62,17 @@ __device__ __forceinline__ bool solve_T(const MechTables &mt, const double (&yw)
                                      double &T) {
   double Tn = (isfinite(T) && T > 0.0) ? T : 1500.0;
   int range = Tn >= mt.T_mid;
-  double m[6];
+  double m[6], d[5];
   mix_ecoef(mt, range, yw, m);
+  cv_coef(m, d);
   for (int it = 0; it < 30; ++it) {
     const int r = Tn >= mt.T_mid;
     if (r != range) {
       range = r;
       mix_ecoef(mt, range, yw, m);
+      cv_coef(m, d);
     }
-    const double dT = (e_over_R(m, Tn) - eR) / cv_over_R(m, Tn);
+    const double dT = (e_over_R(m, Tn) - eR) / cv_over_R(d, Tn);
     Tn -= dT;
     if (!isfinite(Tn) || Tn <= 0.0) break;
     if (fabs(dT) <= 1e-12 * Tn) {
@@ -96,14 +110,14 @@ __device__ __forceinline__ double troe_F(const MechTables &mt, double T, double 
     return 1.0;
   } else {
     const double a = mt.troe_a[J];
-    double Fc = (1.0 - a) * exp(-T * mt.troe_i3[J]) + a * exp(-T * mt.troe_i1[J]);
-    if constexpr (n == 4) Fc += exp(-mt.troe_T2[J] * invT);
-    const double lFc = log10(Fc);
+    double Fc = (1.0 - a) * exp_t(-T * mt.troe_i3[J]) + a * exp_t(-T * mt.troe_i1[J]);
+    if constexpr (n == 4) Fc += exp_t(-mt.troe_T2[J] * invT);
+    const double lFc = log10_t(Fc);
     const double cc = -0.4 - 0.67 * lFc;
     const double nn = 0.75 - 1.27 * lFc;
-    const double x = log10(Pr) + cc;
+    const double x = log10_t(Pr) + cc;
     const double f1 = x / (nn - 0.14 * x);
-    return exp10(lFc / (1.0 + f1 * f1));
+    return exp10_t(lFc / (1.0 + f1 * f1));
   }
 }
 
@@ -114,7 +128,13 @@ __device__ __forceinline__ void reaction(const MechTables &mt, const RateInputs 
   constexpr RxStruct R = kRx[J];
   constexpr int dnu = n_prod(R) - n_reac(R);
   static_assert(dnu >= -1 && dnu <= 1, "compiled structure assumes |sum nu| <= 1");
-  double kf = mt.kconst[J] ? mt.A[J] : exp(fma(mt.beta[J], in.lnT, mt.lnA[J]) - mt.Ta[J] * in.invT);
+  // kconst: 0 Arrhenius exponential; 1 constant (b = Ea = 0); 2, 3: A T^-1, A T^-2 (Ea = 0)
+  const int kc = mt.kconst[J];
+  double kf;
+  if (kc == 0) kf = exp_t(fma(mt.beta[J], in.lnT, mt.lnA[J]) - mt.Ta[J] * in.invT);
+  else if (kc == 1) kf = mt.A[J];
+  else if (kc == 2) kf = mt.A[J] * in.invT;
+  else kf = mt.A[J] * in.invT * in.invT;
   double M = 0.0;
   if constexpr (R.type != ELEM) {
     M = in.ctot;
@@ -124,7 +144,7 @@ __device__ __forceinline__ void reaction(const MechTables &mt, const RateInputs 
     }
   }
   if constexpr (R.type == FALLOFF) {
-    const double k0 = exp(fma(mt.beta0[J], in.lnT, mt.lnA0[J]) - mt.Ta0[J] * in.invT);
+    const double k0 = exp_t(fma(mt.beta0[J], in.lnT, mt.lnA0[J]) - mt.Ta0[J] * in.invT);
     const double Pr = k0 * M / kf;
     kf = (Pr > 0.0) ? kf * (Pr / (1.0 + Pr)) * troe_F<J>(mt, T, in.invT, Pr) : 0.0;
   }
@@ -159,23 +179,23 @@ __device__ __forceinline__ void all_reactions(const MechTables &mt, const RateIn
 __device__ __forceinline__ void production_rates(const MechTables &mt, double T,
                                                  const double (&c)[NSP], double (&wdot)[NSP]) {
   RateInputs in;
-  in.lnT = log(T);
+  in.lnT = log_t(T);
   in.invT = 1.0 / T;
   in.RTP = R_U * T / P_REF;
   in.PRT = 1.0 / in.RTP;
+  const double oml = 1.0 - in.lnT;
   const int range = T >= mt.T_mid;
   double ctot = 0.0;
 #pragma unroll
   for (int k = 0; k < NSP; ++k) {
     in.c[k] = c[k];
     ctot += c[k];
-    const double *hc = mt.hc[range][k];
-    const double *sc = mt.sc[range][k];
-    const double hRT = fma(T, fma(T, fma(T, fma(T, hc[4], hc[3]), hc[2]), hc[1]), hc[0]) + hc[5] * in.invT;
-    const double sR = fma(sc[0], in.lnT, fma(T, fma(T, fma(T, fma(T, sc[4], sc[3]), sc[2]), sc[1]), sc[5]));
+    const double *gc = mt.gc[range][k];
+    double g = fma(T, fma(T, fma(T, fma(T, gc[4], gc[3]), gc[2]), gc[1]), fma(gc[5], in.invT, gc[6]));
+    g = fma(gc[0], oml, g);
     // clamp keeps G finite far outside the tables' range
-    const double g = fmin(fmax(hRT - sR, -700.0), 700.0);
-    in.G[k] = exp(-g);
+    g = fmin(fmax(g, -700.0), 700.0);
+    in.G[k] = exp_t(-g);
     in.iG[k] = 1.0 / in.G[k];
     wdot[k] = 0.0;
   }

@@ -1,0 +1,133 @@
+// rhs_mixed.cuh -- mixed-precision right-hand side of one constant-(rho, e) cell.
+//
+// The same right-hand side as rhs.cuh (Eq. 10, 14-16), split by precision:
+//   fp64: the temperature solve (Newton on the mixture NASA-7 coefficients), ln T, 1/T,
+//         the Gibbs functions g_k / RT and the equilibrium exponents
+//         ln(1 / K_c,j) = sum_k nu_jk g_k + (sum_k nu_jk) ln(R_u T / p_ref);
+//   fp32: forward rate coefficients, third-body sums, Troe fall-off, reverse rates
+//         k_r = exp(ln k_f + ln(1 / K_c)) (one fp32 exponential of an fp64-assembled
+//         exponent), the law-of-mass-action products, production rates and F.
+// The fp32 work runs on the FMA/MUFU pipes, 64x the FP64 pipe's throughput on GB300;
+// what stays in fp64 is the part whose accuracy decides the temperature and the
+// equilibrium state.
+#pragma once
+
+#include "rhs.cuh"
+
+namespace chem {
+
+struct RateInputsF {
+  float lnT, invT, T, ctot;
+  float c[NSP];
+};
+
+template <int J>
+__device__ __forceinline__ float troe_F_f32(const MechTables &mt, float T, float invT, float Pr) {
+  constexpr int n = kRx[J].troe_n;
+  if constexpr (n == 0) {
+    return 1.0f;
+  } else {
+    const float a = mt.f.troe_a[J];
+    float Fc = (1.0f - a) * expf(-T * mt.f.troe_i3[J]) + a * expf(-T * mt.f.troe_i1[J]);
+    if constexpr (n == 4) Fc += expf(-mt.f.troe_T2[J] * invT);
+    const float lFc = log10f(Fc);
+    const float cc = -0.4f - 0.67f * lFc;
+    const float nn = 0.75f - 1.27f * lFc;
+    const float x = log10f(Pr) + cc;
+    const float f1 = x / (nn - 0.14f * x);
+    return exp10f(lFc / (1.0f + f1 * f1));
+  }
+}
+
+template <int J>
+__device__ __forceinline__ void reaction_mixed(const MechTables &mt, const RateInputsF &in,
+                                               const double (&g)[NSP], double lnRTP,
+                                               float (&wdot)[NSP]) {
+  constexpr RxStruct R = kRx[J];
+  constexpr int dnu = n_prod(R) - n_reac(R);
+  float lnkf = fmaf(mt.f.beta[J], in.lnT, mt.f.lnA[J]) - mt.f.Ta[J] * in.invT;
+  float kf = mt.kconst[J] == 1 ? mt.f.A[J] : expf(lnkf);
+  float M = 0.0f;
+  if constexpr (R.type != ELEM) {
+    M = in.ctot;
+    if (mt.has_eff[J]) {
+#pragma unroll
+      for (int k = 0; k < NSP; ++k) M = fmaf(mt.f.effm1[J][k], in.c[k], M);
+    }
+  }
+  if constexpr (R.type == FALLOFF) {
+    const float k0 = expf(fmaf(mt.f.beta0[J], in.lnT, mt.f.lnA0[J]) - mt.f.Ta0[J] * in.invT);
+    const float Pr = k0 * M / kf;
+    kf = (Pr > 0.0f) ? kf * (Pr / (1.0f + Pr)) * troe_F_f32<J>(mt, in.T, in.invT, Pr) : 0.0f;
+    lnkf = logf(kf);
+  }
+  float qf = kf * in.c[R.r0];
+  if constexpr (R.r1 >= 0) qf *= in.c[R.r1];
+  float q = qf;
+  if (mt.reversible[J]) {
+    // ln(1/K_c) in fp64: products' g minus reactants' g plus (sum nu) ln(R_u T / p_ref)
+    double lnQ = g[R.p0] - g[R.r0];
+    if constexpr (R.p1 >= 0) lnQ += g[R.p1];
+    if constexpr (R.r1 >= 0) lnQ -= g[R.r1];
+    if constexpr (dnu == 1) lnQ += lnRTP;
+    if constexpr (dnu == -1) lnQ -= lnRTP;
+    const float kr = (kf > 0.0f) ? expf(lnkf + (float)lnQ) : 0.0f;
+    float qr = kr * in.c[R.p0];
+    if constexpr (R.p1 >= 0) qr *= in.c[R.p1];
+    q = qf - qr;
+  }
+  if constexpr (R.type == THIRD_BODY) q *= M;
+  wdot[R.r0] -= q;
+  if constexpr (R.r1 >= 0) wdot[R.r1] -= q;
+  wdot[R.p0] += q;
+  if constexpr (R.p1 >= 0) wdot[R.p1] += q;
+}
+
+template <int... J>
+__device__ __forceinline__ void all_reactions_mixed(const MechTables &mt, const RateInputsF &in,
+                                                    const double (&g)[NSP], double lnRTP,
+                                                    float (&wdot)[NSP],
+                                                    std::integer_sequence<int, J...>) {
+  (reaction_mixed<J>(mt, in, g, lnRTP, wdot), ...);
+}
+
+// dY/dt (fp32) of one cell at fixed (rho, e) from the fp32 stage state U.
+// T: in = Newton guess, out = solved T (fp64).  Returns false when the solve fails.
+__device__ __forceinline__ bool cell_rhs_mixed(const MechTables &mt, const float (&U)[NSP],
+                                               float rho_f, float invRho_f, double eR, double &T,
+                                               float (&F)[NSP]) {
+  double yw[NSP];
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) yw[k] = (double)U[k] * mt.invW[k];
+  if (!solve_T(mt, yw, eR, T)) return false;
+  const double lnT = log_t(T);
+  const double invT = 1.0 / T;
+  const double oml = 1.0 - lnT;
+  const int range = T >= mt.T_mid;
+  double g[NSP];
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) {
+    const double *gc = mt.gc[range][k];
+    double gk = fma(T, fma(T, fma(T, fma(T, gc[4], gc[3]), gc[2]), gc[1]), fma(gc[5], invT, gc[6]));
+    g[k] = fma(gc[0], oml, gk);
+  }
+  const double lnRTP = lnT + mt.ln_R_over_Pref;
+  RateInputsF in;
+  in.lnT = (float)lnT;
+  in.invT = (float)invT;
+  in.T = (float)T;
+  float ctot = 0.0f, wdot[NSP];
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) {
+    in.c[k] = fmaxf(rho_f * U[k] * mt.f.invW[k], 0.0f);
+    ctot += in.c[k];
+    wdot[k] = 0.0f;
+  }
+  in.ctot = ctot;
+  all_reactions_mixed(mt, in, g, lnRTP, wdot, std::make_integer_sequence<int, NRX>{});
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) F[k] = wdot[k] * mt.f.W[k] * invRho_f;
+  return true;
+}
+
+}  // namespace chem

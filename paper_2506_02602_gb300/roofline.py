@@ -6,7 +6,8 @@ the WRMS norm of Eq. 21-22; per cell, the final temperature solve.  Each right-h
 side is counted from the mechanism structure in the formulation the kernels use:
 
   Newton on mixture coefficients (assembly + 2 iterations), ln T, 1/T, per species the
-  NASA-7 Gibbs function and G_k = exp(-g_k/RT) with its reciprocal, per reaction the
+  NASA-7 Gibbs function (one combined polynomial) and G_k = exp(-g_k/RT) with its
+  reciprocal, per reaction the
   Arrhenius exponential, the products of the law of mass action (Eq. 16) with the
   equilibrium-constant factors, the third-body sums, the Troe fall-off terms, and the
   conversion F_k = W_k wdot_k / rho.
@@ -47,8 +48,8 @@ def rhs_flops(mech: dict | None = None) -> int:
     T = TRANSCENDENTAL
     f = newton_flops()
     f += NSP                                   # concentrations
-    f += T + 1 + 2 + 1 + (NSP - 1)             # ln T, 1/T, RT/p, p/RT, total concentration
-    f += NSP * (10 + 10 + 1 + T + 1)           # h/RT, s/R, g, G = exp(-g), 1/G
+    f += T + 1 + 2 + 1 + 1 + (NSP - 1)         # ln T, 1/T, RT/p, p/RT, 1 - ln T, total conc.
+    f += NSP * (12 + T + 1)                    # g/RT (6 FMAs), G = exp(-g), 1/G
     for j, (nr, npr, typ, troe_n) in enumerate(_RX):
         kconst = mech is not None and mech["b"][j] == 0.0 and mech["Ea"][j] == 0.0
         f += 0 if kconst else T + 4            # Arrhenius exponential
@@ -87,6 +88,32 @@ def cell_flops(mech: dict | None = None) -> int:
 def launch_flops(total_attempted_steps: int, ncells: int, mech: dict | None = None) -> float:
     """Credited flops of one launch from the attempted-step total the kernel reports."""
     return float(total_attempted_steps) * step_flops(mech) + float(ncells) * cell_flops(mech)
+
+
+def rhs_flops_mixed_fp64(mech: dict | None = None) -> int:
+    """The part of one mixed-precision right-hand side that stays fp64: the temperature
+    solve, ln T, 1/T, the Gibbs functions and the equilibrium exponents ln(1/K_c)."""
+    T = TRANSCENDENTAL
+    f = NSP + newton_flops()                   # Y/W from the fp32 stage state, Newton
+    f += T + 1 + 1 + 1                         # ln T, 1/T, 1 - ln T, ln(R T / p)
+    f += NSP * 12                              # g_k / RT: 6 FMAs each
+    for j, (nr, npr, typ, troe_n) in enumerate(_RX):
+        f += (nr + npr - 1) + (1 if nr != npr else 0)  # ln(1/K_c)
+    return f
+
+
+def step_flops_mixed_fp64(mech: dict | None = None) -> int:
+    """fp64 credited flops of one mixed-precision attempted step: 5 right-hand sides'
+    fp64 part, the fp64 solution and error registers (2 FMAs per component and stage)
+    and the fp64 WRMS norm and control."""
+    updates = 5 * (2 + NSP * 2 * 2)
+    wrms = NSP * (2 + 1 + 2 + 1 + 2) + 2 + T_SQRT
+    control = 2 * T_SQRT + 1 + 3 + 1
+    return 5 * rhs_flops_mixed_fp64(mech) + updates + wrms + control
+
+
+def launch_flops_mixed_fp64(total_attempted_steps: int, ncells: int, mech: dict | None = None) -> float:
+    return float(total_attempted_steps) * step_flops_mixed_fp64(mech) + float(ncells) * cell_flops(mech)
 
 
 # FP64 peak of GB300 derived from unit counts and clocks: 152 SMs x 2 FP64 FMA lanes per

@@ -1,0 +1,107 @@
+"""GPU parity of the mixed-precision integrator (fp32 rates and stages, fp64 temperature
+solve, Gibbs/equilibrium terms, solution/error registers and control) against the FP64
+CPU oracle.
+
+Bar: 1e-5 relative on T per cell.  Mass fractions are reported and bounded at 1e-6
+absolute.  The fp32 stage derivatives do not conserve elements bit-exactly, so the element and mass
+drift is bounded by fp32 rounding of h F summed over the steps (1e-7 here), not by the
+fp64 1e-12 bar.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from chem_inputs import mechanism as M
+from chem_inputs import workloads as W
+from tests._gpu import run_device, to_dev
+
+pytestmark = pytest.mark.gpu
+
+MECH = M.build(0)
+O = oracle.Oracle(MECH)
+TOL_T = 1e-5
+TOL_Y = 1e-6
+AMASS = np.array([M.ATOMIC_MASS[e] for e in M.ELEMENTS])
+
+
+def _elements(Y):
+    return (MECH["ncomp"] * AMASS[None, :] / MECH["W"][:, None]).T @ Y
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2506_02602_gb300 import build, chem
+    build.build()
+    c = chem.Context(MECH, "mixed")
+    yield c
+    c.close()
+
+
+def _check(gpu, ref, Y0, e):
+    assert np.all(gpu["status"] == ref["status"])
+    relT = np.abs(gpu["T"] - ref["T"]) / ref["T"]
+    absY = np.abs(gpu["Y"] - ref["Y"]).max(axis=0)
+    assert relT.max() <= TOL_T, relT.max()
+    assert absY.max() <= TOL_Y, absY.max()
+    drift = np.abs(_elements(gpu["Y"]) - _elements(Y0)).max()
+    assert drift <= 1e-7, drift
+    assert np.abs(gpu["Y"].sum(axis=0) - 1.0).max() <= 1e-7
+    e_out = np.array([O.e_mix(gpu["Y"][:, i], gpu["T"][i]) for i in range(gpu["T"].size)])
+    # T is always solved from e in fp64: |dT| <= 1e-12 T leaves |de| <~ cv 1e-12 T ~ 1e-6 J/kg
+    np.testing.assert_allclose(e_out, e, rtol=1e-12, atol=1e-5)
+    return {"max_relT": float(relT.max()), "max_absY": float(absY.max()), "elem_drift": float(drift)}
+
+
+@pytest.mark.parametrize("dt", [1e-7, 1e-6])
+def test_reactors_mixed(ctx, dt):
+    r = W.reactors(4096, seed=0)
+    rho, e = O.state_from_TPY(r["T"], r["p"], r["Y"])
+    ref = O.integrate(rho, e, r["Y"], r["T"], dt)
+    gpu = run_device(ctx, rho, e, r["Y"], r["T"], dt)
+    print(dt, _check(gpu, ref, r["Y"], e))
+
+
+@pytest.mark.parametrize("n", [1, 33, 1000])
+def test_ragged_mixed(ctx, n):
+    r = W.reactors(n, seed=13)
+    rho, e = O.state_from_TPY(r["T"], r["p"], r["Y"])
+    ref = O.integrate(rho, e, r["Y"], r["T"], 5e-7)
+    gpu = run_device(ctx, rho, e, r["Y"], r["T"], 5e-7, ld=n + 3)
+    _check(gpu, ref, r["Y"], e)
+
+
+def test_amr_classes_mixed(ctx):
+    b = W.amr_batch()
+    idx = np.concatenate([np.flatnonzero(b["cls"] == c)[:200] for c in (0, 1, 2)])
+    r = {"T": b["T"][idx], "p": b["p"][idx], "Y": b["Y"][:, idx]}
+    rho, e = O.state_from_TPY(r["T"], r["p"], r["Y"])
+    ref = O.integrate(rho, e, r["Y"], r["T"], 1e-7)
+    gpu = run_device(ctx, rho, e, r["Y"], r["T"], 1e-7)
+    print(_check(gpu, ref, r["Y"], e))
+
+
+def test_detonation_slice_mixed_vs_fp64_full_grid(ctx):
+    # the benchmark's configuration: plain FP64 vs mixed on all 1M cells, and both vs the
+    # oracle on a seeded sample
+    import torch
+    from paper_2506_02602_gb300 import chem
+    d = W.detonation_slice()
+    f64 = chem.Context(MECH, "fp64")
+    T0, p0, Y0 = to_dev(d["T"]), to_dev(d["p"]), to_dev(d["Y"])
+    rho, e = f64.state_from_TPY(T0, p0, Y0)
+    Ya, Ta = Y0.clone(), T0.clone()
+    Yb, Tb = Y0.clone(), T0.clone()
+    f64.integrate(rho, e, Ya, Ta, 2e-9)
+    ctx.integrate(rho, e, Yb, Tb, 2e-9)
+    torch.cuda.synchronize()
+    relT = ((Tb - Ta).abs() / Ta).max().item()
+    absY = (Yb - Ya).abs().max().item()
+    f64.close()
+    assert relT <= TOL_T and absY <= TOL_Y, (relT, absY)
+    n = T0.numel()
+    idx = np.sort(np.random.default_rng(3).choice(n, 2000, replace=False))
+    ref = O.integrate(rho.cpu().numpy()[idx], e.cpu().numpy()[idx], d["Y"][:, idx], d["T"][idx], 2e-9)
+    relT_o = np.abs(Tb.cpu().numpy()[idx] - ref["T"]) / ref["T"]
+    assert relT_o.max() <= TOL_T
+    print("mixed vs fp64 (full grid): relT %.2e absY %.2e; vs oracle sample relT %.2e"
+          % (relT, absY, relT_o.max()))
