@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--nx", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-amr", action="store_true", help="skip the AMR-batch comparison leg")
     ap.add_argument("--cpu-sample", type=int, default=131072)
     ap.add_argument("--ref-sample", type=int, default=32768)
     return ap.parse_args()
@@ -177,6 +178,66 @@ def run_reference(args, rank, world):
 VARIANTS = (("fp64", 0.0), ("mixed", 1e-5))  # (variant, stated error bound on T vs FP64)
 
 
+def amr_leg(ctx, steps, dev):
+    """Ragged AMR-like batch (256 boxes, edges {8,16,24,32}^3, 3 levels with 2^l substeps
+    of 1e-7/2^l s, heavy-tailed stiffness): the persistent work-stealing launch against
+    the plain path of one chem_integrate launch per box and substep on 8 streams (one
+    stream per box, round robin).  Both run the same per-cell arithmetic, so their
+    results must be bit-identical."""
+    import torch
+    from chem_inputs import workloads
+    b = workloads.amr_batch()
+    n = b["T"].size
+    T0 = torch.tensor(b["T"], dtype=torch.float64, device=dev)
+    p0 = torch.tensor(b["p"], dtype=torch.float64, device=dev)
+    Y0 = torch.tensor(b["Y"], dtype=torch.float64, device=dev)
+    rho, e = ctx.state_from_TPY(T0, p0, Y0)
+    off_h = b["box_offset"]
+    off = torch.tensor(off_h, dtype=torch.int64, device=dev)
+    dts = torch.tensor(b["box_dt"], dtype=torch.float64, device=dev)
+    nsub = torch.tensor(b["box_nsub"], dtype=torch.int32, device=dev)
+    Y, T = Y0.clone(), T0.clone()
+    h = torch.empty(n, dtype=torch.float64, device=dev)
+    ns = torch.empty(n, dtype=torch.int32, device=dev)
+    streams = [torch.cuda.Stream(dev) for _ in range(8)]
+
+    def persistent():
+        Y.copy_(Y0); T.copy_(T0); h.fill_(float("nan"))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.integrate_batched(rho, e, Y, T, off, dts, nsub, RTOL, ATOL, h=h, nsteps=ns)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    def per_box():
+        Y.copy_(Y0); T.copy_(T0); h.fill_(float("nan"))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for j in range(len(off_h) - 1):
+            a, z = int(off_h[j]), int(off_h[j + 1])
+            st = streams[j % len(streams)]
+            for _ in range(int(b["box_nsub"][j])):
+                ctx.integrate(rho[a:z], e[a:z], Y[:, a:z], T[a:z], float(b["box_dt"][j]), RTOL, ATOL,
+                              h=h[a:z], stream=st, ncells=z - a)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    persistent()
+    tp = min(persistent() for _ in range(steps))
+    Yp, Tp, steps_p = Y.cpu().numpy(), T.cpu().numpy(), ns.cpu().numpy()
+    per_box()
+    tb = min(per_box() for _ in range(steps))
+    same = bool(np.array_equal(Y.cpu().numpy(), Yp) and np.array_equal(T.cpu().numpy(), Tp))
+    subs = int((b["box_nsub"].astype(np.int64) * np.diff(off_h)).sum())
+    return {"workload": f"AMR-like batch: 256 boxes, {n} cells, {subs} cell-substeps, 3 levels",
+            "variant": ctx.variant,
+            "persistent_cells_per_s": n / tp, "persistent_ms": 1e3 * tp,
+            "per_box_cells_per_s": n / tb, "per_box_ms": 1e3 * tb,
+            "speedup": tb / tp, "cell_substeps_per_s": subs / tp,
+            "attempted_steps": int(steps_p.sum()), "max_steps": int(steps_p.max()),
+            "identical_results": same}
+
+
 def run_ours(args, rank, world, local):
     import torch
     from chem_inputs import mechanism, workloads
@@ -300,6 +361,10 @@ def run_ours(args, rank, world, local):
         e2e_el = float(t[0])
     e2e_match = bool(np.array_equal(hY, res[head]["Y"]) and np.array_equal(hT, res[head]["T"]))
 
+    amr = None
+    if not args.no_amr:
+        amr = amr_leg(ctxs[head], max(2, min(args.steps, 3)), dev)
+
     line = None
     if rank == 0:
         cpu, parity = (None, {})
@@ -325,6 +390,7 @@ def run_ours(args, rank, world, local):
                     "d2h_bytes_per_step": n * (1 + S) * 8 + 2 * n * 4,
                     "matches_device_path": e2e_match},
             "gpu_launches": args.steps * len(VARIANTS),
+            "amr_batch": amr,
             "clocks": clk,
             "cpu_baseline": cpu,
             "parity_vs_oracle_sample": parity,

@@ -201,6 +201,60 @@ int chem_integrate_host(chem_ctx *ctx, int64_t ncells, const double *h_rho,
                         double *h_h, int32_t *h_status, int32_t *h_nsteps, double dt,
                         double rtol, double atol, void *stream);
 
+/* Queue order of the batched integrator. */
+typedef enum {
+  CHEM_ORDER_STIFFNESS = 0, /* cells sorted by a stiffness key, most expensive first */
+  CHEM_ORDER_NATURAL = 1    /* cells taken in index order */
+} chem_queue_order;
+
+/*
+ * A ragged batch of boxes (the boxes of an AMR hierarchy, Sec. 3.1).  Box b owns the
+ * contiguous cells [d_box_offset[b], d_box_offset[b+1]) of the state and advances them
+ * by d_box_nsub[b] successive substeps of d_box_dt[b] seconds each (a level subcycled
+ * per Alg. 1 takes 2^l substeps of dt / 2^l).  All three arrays are device memory:
+ * d_box_offset[nboxes + 1] (int64, nondecreasing, d_box_offset[0] = 0,
+ * d_box_offset[nboxes] = ncells), d_box_dt[nboxes] (> 0), d_box_nsub[nboxes] (>= 1).
+ * Offsets that break these rules assign cells to the wrong box but never address memory
+ * outside the state.
+ */
+typedef struct {
+  int32_t nboxes;
+  const int64_t *d_box_offset;
+  const double *d_box_dt;
+  const int32_t *d_box_nsub;
+} chem_batch;
+
+/* Options of chem_integrate_batched.  Zero-initialised = the defaults. */
+typedef struct {
+  int32_t order;               /* chem_queue_order [CHEM_ORDER_STIFFNESS] */
+  int32_t ctas_per_sm;         /* persistent CTAs per SM; 0 = all that fit [0] */
+  int32_t use_graph;           /* 1: capture the call's launches in a CUDA graph and
+                                  replay it while the arguments are unchanged [0] */
+  int32_t reserved;            /* must be zero */
+  const int32_t *d_cost_hint;  /* nullable device [ncells]: per-cell cost used as the
+                                  stiffness key instead of the probe (e.g. d_nsteps of
+                                  the previous call) */
+} chem_batch_options;
+
+/*
+ * Integrate a ragged batch in one persistent launch with work stealing (Eq. 21-22 per
+ * cell, as chem_integrate).  The state covers all ncells cells of all boxes.  Steps:
+ * a stiffness key per cell (the cost hint, or one right-hand side giving accuracy and
+ * stability step estimates, times the box's substeps), a counting sort of the cells
+ * into descending-cost order, then a persistent kernel whose lanes take cells from the
+ * sorted queue through an atomic cursor and integrate all their substeps; a lane that
+ * finishes takes the next cell.  d_h carries the step across substeps; d_nsteps counts
+ * attempts over all substeps; max_steps applies per cell and call.  Results do not
+ * depend on the queue order.  The context owns the queue scratch (5 bytes per cell plus
+ * 520 bytes), allocated on the first call that needs more: make one uncaptured call of
+ * the largest size before capturing calls in a CUDA graph.  opt may be NULL.
+ * Errors: as chem_integrate, plus nboxes < 1, NULL box arrays, unknown order, nonzero
+ * reserved -> CHEM_ERR_INVALID; allocation failure -> CHEM_ERR_NOMEM.  Asynchronous.
+ */
+int chem_integrate_batched(chem_ctx *ctx, const chem_state *state, int64_t ncells,
+                           const chem_batch *batch, double rtol, double atol,
+                           const chem_batch_options *opt, void *stream, chem_stats *d_stats);
+
 /*
  * Diagnostic: evaluate one of the device math routines the integration kernels use on
  * n fp64 arguments (device pointers d_x -> d_y), so tests can check them against the

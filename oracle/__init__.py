@@ -89,7 +89,7 @@ def lib():
             "oracle_chem_rhs": (C.c_double, [mp, C.c_double, C.c_double, dp, C.c_double, dp]),
             "oracle_integrate": (C.c_int32, [mp, C.c_int64, dp, dp, dp, C.c_int64, dp, C.c_double,
                                              C.c_double, C.c_double, dp, C.c_int32, ip, ip, ip, dp,
-                                             C.c_int32]),
+                                             dp, C.c_int32]),
             "oracle_chem_fixed": (C.c_int32, [mp, C.c_double, C.c_double, dp, C.c_double,
                                               C.c_double, C.c_int32, dp]),
             "oracle_struct_size": (C.c_int32, []),
@@ -228,7 +228,7 @@ class Oracle:
     def integrate(self, rho, e, Y, T, dt, rtol=1e-6, atol=1e-10, h0=None, max_steps=100000,
                   nthreads=0):
         """Integrate every cell over dt.  Returns a dict with Y [S, n], T, status,
-        nsteps (attempted), naccept and margin (min |err - 1|)."""
+        nsteps (attempted), naccept, margin (min |err - 1|) and h (next step)."""
         rho, e = _f64(rho), _f64(e)
         Y = np.array(Y, dtype=np.float64, order="C", copy=True)
         T = np.array(T, dtype=np.float64, copy=True)
@@ -237,12 +237,14 @@ class Oracle:
         nsteps = np.zeros(n, dtype=np.int32)
         nacc = np.zeros(n, dtype=np.int32)
         margin = np.zeros(n)
-        h0p = _dp(_f64(h0)) if h0 is not None else None
+        hout = np.zeros(n)
+        h0a = _f64(h0) if h0 is not None else None
+        h0p = _dp(h0a) if h0 is not None else None
         self.L.oracle_integrate(self._mp, n, _dp(rho), _dp(e), _dp(Y), Y.shape[1], _dp(T), dt, rtol,
                                 atol, h0p, max_steps, _ip(status), _ip(nsteps), _ip(nacc),
-                                _dp(margin), nthreads)
+                                _dp(margin), _dp(hout), nthreads)
         return {"Y": Y, "T": T, "status": status, "nsteps": nsteps, "naccept": nacc,
-                "margin": margin}
+                "margin": margin, "h": hout}
 
     def chem_fixed(self, rho, e, Y, T, h, nsteps):
         Y = np.array(Y, dtype=np.float64, copy=True)

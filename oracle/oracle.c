@@ -308,6 +308,7 @@ static double wrms(int n, const double *E, const double *Xold, const double *Xne
 typedef struct {
   int32_t status, nacc, nrej;
   double margin; /* min over attempted steps of |err - 1| */
+  double h_next; /* the controller's next step after the last attempt */
 } adapt_out;
 
 /* Adaptive integration of y' = f(y) over [0, dt] with the Eq. 22 controller.
@@ -317,7 +318,7 @@ static void integrate_adaptive(int n, rhs_fn f, void *ctx, double dt, double rto
                                double *log_h, double *log_err, int32_t *log_acc, int32_t max_log) {
   double t = 0.0, h = (h0 > 0.0) ? h0 : dt;
   double Xs[OR_MAXN], E[OR_MAXN];
-  out->status = 0; out->nacc = 0; out->nrej = 0; out->margin = INFINITY;
+  out->status = 0; out->nacc = 0; out->nrej = 0; out->margin = INFINITY; out->h_next = h;
   while (dt - t > 1e-12 * dt) {
     if (out->nacc + out->nrej >= max_steps) { out->status = 1; break; }
     if (h < 1e-15 * dt) { out->status = 2; break; }
@@ -353,6 +354,7 @@ static void integrate_adaptive(int n, rhs_fn f, void *ctx, double dt, double rto
     }
     h = h * fac;
   }
+  out->h_next = h;
 }
 
 /* ------------------------------------------------------------ test problems */
@@ -436,12 +438,13 @@ double oracle_chem_rhs(const omech *m, double rho, double e, const double *Y, do
  * Y: species planes Y[k * ldY + i], advanced in place.  T: in = Newton guess (or NaN),
  * out = temperature of the final state.  h0: per-cell initial step (NULL -> dt).
  * Per cell out: status (0 ok, 1 max steps, 2 h underflow, 3 Newton failure,
- * 4 non-finite), attempted steps, accepted steps, and the smallest |err - 1| seen
- * (used to classify cells whose accept/reject decisions sit on a rounding knife-edge). */
+ * 4 non-finite), attempted steps, accepted steps, the smallest |err - 1| seen
+ * (used to classify cells whose accept/reject decisions sit on a rounding knife-edge)
+ * and the controller's next step h_out (to carry into a following call). */
 int32_t oracle_integrate(const omech *m, int64_t n, const double *rho, const double *e, double *Y,
                          int64_t ldY, double *T, double dt, double rtol, double atol,
                          const double *h0, int32_t max_steps, int32_t *status, int32_t *nsteps,
-                         int32_t *naccept, double *margin, int32_t nthreads) {
+                         int32_t *naccept, double *margin, double *h_out, int32_t nthreads) {
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 8)
@@ -455,8 +458,10 @@ int32_t oracle_integrate(const omech *m, int64_t n, const double *rho, const dou
     for (int k = 0; k < m->nsp; ++k) bad_input |= !isfinite(X[k]);
     if (bad_input) {
       o.status = 4; o.nacc = 0; o.nrej = 0; o.margin = INFINITY;
+      o.h_next = (h0 && isfinite(h0[i]) && h0[i] > 0.0) ? h0[i] : dt;
     } else {
-      integrate_adaptive(m->nsp, chem_rhs, &cc, dt, rtol, atol, h0 ? h0[i] : 0.0, max_steps, X,
+      double hi = (h0 && isfinite(h0[i]) && h0[i] > 0.0) ? h0[i] : 0.0;
+      integrate_adaptive(m->nsp, chem_rhs, &cc, dt, rtol, atol, hi, max_steps, X,
                          &o, NULL, NULL, NULL, 0);
     }
     double Tout = NAN;
@@ -470,6 +475,7 @@ int32_t oracle_integrate(const omech *m, int64_t n, const double *rho, const dou
     if (nsteps) nsteps[i] = o.nacc + o.nrej;
     if (naccept) naccept[i] = o.nacc;
     if (margin) margin[i] = o.margin;
+    if (h_out) h_out[i] = o.h_next;
   }
   return 0;
 }

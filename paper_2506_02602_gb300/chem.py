@@ -73,6 +73,17 @@ class Stats(C.Structure):
                 ("status_count", C.c_int64 * 8)]
 
 
+class Batch(C.Structure):
+    _fields_ = [("nboxes", C.c_int32), ("d_box_offset", C.c_void_p), ("d_box_dt", C.c_void_p),
+                ("d_box_nsub", C.c_void_p)]
+
+
+class BatchOptions(C.Structure):
+    _fields_ = [("order", C.c_int32), ("ctas_per_sm", C.c_int32), ("use_graph", C.c_int32),
+                ("reserved", C.c_int32), ("d_cost_hint", C.c_void_p)]
+
+
+ORDER_STIFFNESS, ORDER_NATURAL = 0, 1
 STATS_WORDS = C.sizeof(Stats) // 8
 
 _lib = None
@@ -96,6 +107,8 @@ def load() -> C.CDLL:
         "chem_integrate": (C.c_int, [vp, C.POINTER(State), i64, dbl, dbl, dbl, vp, vp]),
         "chem_integrate_host": (C.c_int, [vp, i64, vp, vp, vp, i64, vp, vp, vp, vp, dbl, dbl, dbl, vp]),
         "chem_diag_math": (C.c_int, [C.c_int, i64, vp, vp, vp]),
+        "chem_integrate_batched": (C.c_int, [vp, C.POINTER(State), i64, C.POINTER(Batch), dbl, dbl,
+                                             C.POINTER(BatchOptions), vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -227,6 +240,27 @@ class Context:
                    None if nsteps is None else nsteps.data_ptr())
         self._raise(self.L.chem_integrate(self.h, C.byref(st), n, float(dt), float(rtol), float(atol),
                                           _stream(stream), _ptr(stats)))
+
+    def integrate_batched(self, rho, e, Y, T, box_offset, box_dt, box_nsub, rtol=1e-6, atol=1e-10,
+                          h=None, status=None, nsteps=None, stats=None, order=ORDER_STIFFNESS,
+                          ctas_per_sm=0, use_graph=False, cost_hint=None, stream=None):
+        """chem_integrate_batched: box_offset (int64 [nb+1]), box_dt (float64 [nb]) and
+        box_nsub (int32 [nb]) are CUDA tensors; the state tensors are as in integrate."""
+        import torch
+        n = rho.numel()
+        for nm, t in (("rho", rho), ("e", e), ("Y", Y), ("T", T)):
+            _check_f64_cuda(nm, t, n)
+        if box_offset.dtype != torch.int64 or box_nsub.dtype != torch.int32 or box_dt.dtype != torch.float64:
+            raise ChemError(ERR_INVALID, "box_offset int64, box_dt float64, box_nsub int32 expected")
+        st = State(_ptr(rho).value, _ptr(e).value, _ptr(Y).value, Y.stride(0), _ptr(T).value,
+                   None if h is None else h.data_ptr(),
+                   None if status is None else status.data_ptr(),
+                   None if nsteps is None else nsteps.data_ptr())
+        b = Batch(box_dt.numel(), box_offset.data_ptr(), box_dt.data_ptr(), box_nsub.data_ptr())
+        o = BatchOptions(order, ctas_per_sm, int(bool(use_graph)), 0,
+                         None if cost_hint is None else cost_hint.data_ptr())
+        self._raise(self.L.chem_integrate_batched(self.h, C.byref(st), n, C.byref(b), float(rtol),
+                                                  float(atol), C.byref(o), _stream(stream), _ptr(stats)))
 
     def integrate_host(self, rho, e, Y, T, dt, rtol=1e-6, atol=1e-10, h=None, status=None,
                        nsteps=None, stream=None):

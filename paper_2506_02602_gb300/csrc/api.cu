@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <cstdint>
 #include <string>
 
 #include "internal.cuh"
@@ -22,6 +23,14 @@ struct chem_ctx {
   // device scratch of chem_integrate_host (grown on demand, freed at teardown)
   void *host_scratch = nullptr;
   size_t host_scratch_bytes = 0;
+  // queue scratch of chem_integrate_batched (grown on demand)
+  void *batch_scratch = nullptr;
+  int64_t batch_cap = 0;
+  // cached CUDA graph of the last batched call and the arguments it was captured with
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream the graph is captured on
+  unsigned char graph_key[512];
+  size_t graph_key_len = 0;
 };
 
 namespace {
@@ -253,6 +262,9 @@ int chem_teardown(chem_ctx *ctx) {
   if (!ctx) return CHEM_OK;
   cudaDeviceSynchronize();
   if (ctx->host_scratch) cudaFree(ctx->host_scratch);
+  if (ctx->batch_scratch) cudaFree(ctx->batch_scratch);
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
   return CHEM_OK;
 }
@@ -287,6 +299,133 @@ int chem_integrate(chem_ctx *ctx, const chem_state *state, int64_t ncells, doubl
   StepParams p{dt, rtol, atol, ctx->opt.max_steps};
   cudaError_t e = launch_lsrk(ctx->opt.variant, ctx->tables, a, p, ctx->opt.block_size, s);
   return e == cudaSuccess ? CHEM_OK : cuda_fail(ctx, e, "integration launch");
+}
+
+// Grow the batched path's queue scratch to hold n cells.
+static int batch_scratch(chem_ctx *ctx, int64_t n, BatchScratch *out) {
+  if (n > ctx->batch_cap) {
+    if (ctx->batch_scratch) {
+      cudaDeviceSynchronize();
+      cudaFree(ctx->batch_scratch);
+      ctx->batch_scratch = nullptr;
+      ctx->batch_cap = 0;
+    }
+    if (ctx->graph) {  // the cached graph points into the old scratch
+      cudaGraphExecDestroy(ctx->graph);
+      ctx->graph = nullptr;
+      ctx->graph_key_len = 0;
+    }
+    const size_t bytes = 256 + kBatchBuckets * sizeof(int32_t) + (size_t)n * 5 + 256;
+    cudaError_t e = cudaMalloc(&ctx->batch_scratch, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      ctx->batch_scratch = nullptr;
+      return fail(ctx, CHEM_ERR_NOMEM, "batch scratch of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    }
+    ctx->batch_cap = n;
+  }
+  char *base = static_cast<char *>(ctx->batch_scratch);
+  out->cursor = reinterpret_cast<unsigned long long *>(base);
+  out->hist = reinterpret_cast<int32_t *>(base + 256);
+  out->order = reinterpret_cast<int32_t *>(base + 256 + kBatchBuckets * sizeof(int32_t));
+  out->bucket = reinterpret_cast<uint8_t *>(out->order + ctx->batch_cap);
+  return CHEM_OK;
+}
+
+int chem_integrate_batched(chem_ctx *ctx, const chem_state *state, int64_t ncells,
+                           const chem_batch *batch, double rtol, double atol,
+                           const chem_batch_options *opt, void *stream, chem_stats *d_stats) {
+  if (!ctx) return fail(nullptr, CHEM_ERR_INVALID, "ctx is NULL");
+  int rc = check_state(ctx, state, ncells);
+  if (rc) return rc;
+  rc = check_step(ctx, 1.0, rtol, atol);
+  if (rc) return rc;
+  if (ncells > INT32_MAX) return fail(ctx, CHEM_ERR_INVALID, "batched calls hold at most 2^31-1 cells");
+  chem_batch_options o{};
+  if (opt) o = *opt;
+  if (o.order != CHEM_ORDER_STIFFNESS && o.order != CHEM_ORDER_NATURAL)
+    return fail(ctx, CHEM_ERR_INVALID, "unknown queue order %d", o.order);
+  if (o.reserved || o.ctas_per_sm < 0)
+    return fail(ctx, CHEM_ERR_INVALID, "invalid batch options");
+  if (!batch || batch->nboxes < 1 || !batch->d_box_offset || !batch->d_box_dt || !batch->d_box_nsub)
+    return fail(ctx, CHEM_ERR_INVALID, "batch needs nboxes >= 1 and its three device arrays");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (ncells == 0) {
+    if (d_stats) {
+      cudaError_t e = cudaMemsetAsync(d_stats, 0, sizeof(chem_stats), s);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "clearing stats");
+    }
+    return CHEM_OK;
+  }
+  BatchScratch sc;
+  rc = batch_scratch(ctx, ncells, &sc);
+  if (rc) return rc;
+  BatchArgs a{state->d_rho, state->d_e, state->d_Y, state->ldY, state->d_T, state->d_h,
+              state->d_status, state->d_nsteps, ncells, batch->d_box_offset, batch->d_box_dt,
+              batch->d_box_nsub, batch->nboxes, o.d_cost_hint, d_stats};
+  StepParams p{0.0, rtol, atol, ctx->opt.max_steps};
+  auto issue = [&](cudaStream_t st) -> cudaError_t {
+    if (d_stats) {
+      cudaError_t e = cudaMemsetAsync(d_stats, 0, sizeof(chem_stats), st);
+      if (e != cudaSuccess) return e;
+    }
+    return launch_batched(ctx->opt.variant, ctx->tables, a, p, sc, o.order, o.ctas_per_sm, st);
+  };
+  if (!o.use_graph) {
+    cudaError_t e = issue(s);
+    return e == cudaSuccess ? CHEM_OK : cuda_fail(ctx, e, "batched launch");
+  }
+  // graph path: replay the cached graph when every argument is unchanged
+  unsigned char key[512];
+  size_t kl = 0;
+  auto put = [&](const void *v, size_t nbytes) {
+    std::memcpy(key + kl, v, nbytes);
+    kl += nbytes;
+  };
+  put(&a, sizeof a);
+  put(&p, sizeof p);
+  put(&sc, sizeof sc);
+  put(&o, sizeof o);
+  cudaError_t e;
+  if (!(ctx->graph && kl == ctx->graph_key_len && std::memcmp(key, ctx->graph_key, kl) == 0)) {
+    cudaStreamCaptureStatus cap;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "querying capture");
+    if (cap != cudaStreamCaptureStatusNone) {  // already inside the caller's capture
+      e = issue(s);
+      return e == cudaSuccess ? CHEM_OK : cuda_fail(ctx, e, "batched launch");
+    }
+    if (ctx->graph) {
+      cudaGraphExecDestroy(ctx->graph);
+      ctx->graph = nullptr;
+      ctx->graph_key_len = 0;
+    }
+    // capture on a private stream (the caller's may be the legacy default stream,
+    // which cannot be captured); the graph then runs on the caller's stream
+    if (!ctx->cap_stream) {
+      e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "creating the capture stream");
+    }
+    e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "beginning capture");
+    cudaError_t le = issue(ctx->cap_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(ctx->cap_stream, &g);
+    if (le != cudaSuccess || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(ctx, le != cudaSuccess ? le : e, "capturing the batched launch");
+    }
+    e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      ctx->graph = nullptr;
+      return cuda_fail(ctx, e, "instantiating the batched graph");
+    }
+    std::memcpy(ctx->graph_key, key, kl);
+    ctx->graph_key_len = kl;
+  }
+  e = cudaGraphLaunch(ctx->graph, s);
+  return e == cudaSuccess ? CHEM_OK : cuda_fail(ctx, e, "graph launch");
 }
 
 int chem_integrate_host(chem_ctx *ctx, int64_t n, const double *h_rho, const double *h_e,

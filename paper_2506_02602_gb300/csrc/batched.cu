@@ -1,0 +1,241 @@
+// batched.cu -- ragged AMR-like batches in one persistent launch with work stealing.
+//
+// A batch is a set of boxes; box b owns the contiguous cells [off[b], off[b+1]) of the
+// state and advances them through nsub[b] successive substeps of dt[b] (a subcycled
+// level of Alg. 1 takes 2^l substeps of dt/2^l).  Per-cell cost is heavy-tailed: an
+// ignition front needs ~100x the steps of inert gas.  The paper fills the GPU with large
+// boxes and one stream per box (Sec. 4.1); here the whole batch is one launch:
+//
+//   1. k_probe: a stiffness key per cell -- the caller's cost hint (for example the
+//      attempted steps of the previous call), or one right-hand side giving an
+//      accuracy estimate (dt max|F| / tol)^(1/4) and a stability estimate
+//      dt max_k (consumption rate of k / c_k) / 3 -- times the box's substeps, binned
+//      into half-octave buckets with a block histogram;
+//   2. k_scan + k_scatter: a counting sort of the cell indices into descending-cost
+//      order (warp-aggregated atomics per bucket);
+//   3. k_lsrk_persistent: one CTA set sized to the resident capacity; every iteration of
+//      its loop is one attempted RK step for each lane's current cell, so lanes stay
+//      converged inside the right-hand side; a lane whose cell finishes (all substeps)
+//      stores it and takes the next cell from the queue through one warp-aggregated
+//      atomicAdd on a global cursor.  Expensive cells start first, so the tail is short.
+//
+// The per-cell arithmetic is cell.cuh, identical to the one-pass kernel, so results
+// do not depend on the processing order.  No CTA ever waits on another: a CTA that finds
+// the queue empty exits.
+#include <cuda_runtime.h>
+
+#include "cell.cuh"
+#include "internal.cuh"
+
+namespace chem {
+
+__device__ __forceinline__ int find_box(const int64_t *off, int nb, int64_t i) {
+  int lo = 0, hi = nb;  // off[lo] <= i < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= i) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(128) k_probe(const __grid_constant__ MechTables mt,
+                                               const BatchArgs a, double rtol, double atol,
+                                               uint8_t *__restrict__ bucket,
+                                               int32_t *__restrict__ hist) {
+  __shared__ int sh[kBatchBuckets];
+  load_math_tables();
+  for (int t = threadIdx.x; t < kBatchBuckets; t += blockDim.x) sh[t] = 0;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.n) {
+    const int b = find_box(a.box_off, a.nboxes, i);
+    const double dt = a.box_dt[b];
+    double key = 1.0;
+    if (a.cost_hint) {
+      key = (double)max(a.cost_hint[i], 1);
+    } else {
+      const double rho = a.rho[i];
+      double Y[NSP], yw[NSP], T = a.T[i];
+#pragma unroll
+      for (int k = 0; k < NSP; ++k) {
+        Y[k] = a.Y[k * a.ld + i];
+        yw[k] = Y[k] * mt.invW[k];
+      }
+      if (isfinite(rho) && rho > 0.0 && solve_T(mt, yw, a.e[i] / R_U, T)) {
+        double c[NSP], wdot[NSP], dflux[NSP];
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) c[k] = fmax(rho * yw[k], 0.0);
+        production_rates<true>(mt, T, c, wdot, dflux);
+        double acc = 0.0, stab = 0.0;
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) {
+          const double F = wdot[k] * mt.W[k] / rho;
+          acc = fmax(acc, fabs(F) * dt / (rtol * fabs(Y[k]) + atol));
+          if (c[k] > 1e-30) stab = fmax(stab, dflux[k] / c[k] * dt);
+        }
+        key = fmax(1.0, fmax(sqrt(sqrt(acc)), stab * (1.0 / 3.0)));
+        if (!isfinite(key)) key = 1.0;
+      }
+      key *= (double)a.box_nsub[b];
+    }
+    const int bk = min(kBatchBuckets - 1, max(0, (int)(2.0f * log2f((float)key))));
+    bucket[i] = (uint8_t)bk;
+    atomicAdd(&sh[bk], 1);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < kBatchBuckets; t += blockDim.x)
+    if (sh[t]) atomicAdd(&hist[t], sh[t]);
+}
+
+// Exclusive scan of the bucket counts in descending-cost order; resets the cursor.
+__global__ void k_scan(int32_t *hist, unsigned long long *cursor) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int run = 0;
+    for (int b = kBatchBuckets - 1; b >= 0; --b) {
+      const int cnt = hist[b];
+      hist[b] = run;
+      run += cnt;
+    }
+    *cursor = 0ull;
+  }
+}
+
+__global__ void k_scatter(int64_t n, const uint8_t *__restrict__ bucket, int32_t *offs,
+                          int32_t *__restrict__ order) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = i < n;
+  const int bk = live ? bucket[i] : -1;
+  const unsigned mask = __ballot_sync(0xffffffffu, live);
+  if (!live) return;
+  // lanes with the same bucket share one atomicAdd
+  const unsigned peers = __match_any_sync(mask, bk);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(&offs[bk], __popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  order[base + __popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
+}
+
+template <int V>
+__global__ void __launch_bounds__(128) k_lsrk_persistent(const __grid_constant__ MechTables mt,
+                                                         const BatchArgs a, const StepParams p,
+                                                         const int32_t *__restrict__ order,
+                                                         unsigned long long *cursor) {
+  load_math_tables();
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  CellState c;
+  c.done = true;
+  c.nacc = c.nrej = c.nrhs = 0;
+  c.status = CHEM_CELL_OK;
+  int64_t cell = -1;
+  int sub_left = 0;
+  bool need = true;
+  int done_cells = 0, tot_acc = 0, tot_rej = 0, tot_rhs = 0, max_steps = 0;
+  int hist[6] = {0, 0, 0, 0, 0, 0};
+  for (;;) {
+    const unsigned needmask = __ballot_sync(FULL, need);
+    if (needmask) {
+      const int leader = __ffs(needmask) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(cursor, (unsigned long long)__popc(needmask));
+      base = __shfl_sync(FULL, base, leader);
+      if (need) {
+        need = false;
+        const unsigned long long slot = base + __popc(needmask & ((1u << lane) - 1u));
+        if (slot < (unsigned long long)a.n) {
+          cell = order ? (int64_t)order[slot] : (int64_t)slot;
+          const int b = find_box(a.box_off, a.nboxes, cell);
+          sub_left = a.box_nsub[b];
+#pragma unroll
+          for (int k = 0; k < NSP; ++k) c.X[k] = a.Y[k * a.ld + cell];
+          c.T = a.T[cell];
+          c.h = a.h ? a.h[cell] : CUDART_NAN;
+          c.nacc = c.nrej = c.nrhs = 0;
+          cell_begin(c, a.rho[cell], a.e[cell], a.box_dt[b]);
+        } else {
+          cell = -1;
+        }
+      }
+    }
+    if (__ballot_sync(FULL, cell >= 0) == 0) break;
+    if (cell >= 0) {
+      if (!c.done) cell_attempt<V>(mt, c, p);
+      if (c.done) {
+        if (c.status == CHEM_CELL_OK && --sub_left > 0) {
+          c.t = 0.0;  // next substep from the current state; h and the T guess carry
+          c.done = false;
+        } else {
+          cell_finish(mt, c);
+#pragma unroll
+          for (int k = 0; k < NSP; ++k) a.Y[k * a.ld + cell] = c.X[k];
+          a.T[cell] = c.T;
+          if (a.h) a.h[cell] = c.h;
+          if (a.status) a.status[cell] = c.status;
+          if (a.nsteps) a.nsteps[cell] = c.nacc + c.nrej;
+          ++done_cells;
+          tot_acc += c.nacc;
+          tot_rej += c.nrej;
+          tot_rhs += c.nrhs;
+          max_steps = max(max_steps, c.nacc + c.nrej);
+          if (c.status >= 0 && c.status < 6) ++hist[c.status];
+          cell = -1;
+          need = true;
+        }
+      }
+    }
+  }
+  if (a.stats) accumulate_stats(a.stats, done_cells, tot_acc, tot_rej, tot_rhs, max_steps, hist);
+}
+
+static int g_persist_ctas[2] = {0, 0};  // resident CTAs per SM of each variant (cached)
+
+int persistent_capacity(int variant, int *num_sms) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(num_sms, cudaDevAttrMultiProcessorCount, dev);
+  const int v = variant == CHEM_VARIANT_MIXED ? 1 : 0;
+  if (g_persist_ctas[v] == 0) {
+    int per = 0;
+    if (v)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lsrk_persistent<CHEM_VARIANT_MIXED>, 128, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lsrk_persistent<CHEM_VARIANT_FP64>, 128, 0);
+    g_persist_ctas[v] = per > 0 ? per : 1;
+  }
+  return g_persist_ctas[v];
+}
+
+cudaError_t launch_batched(int variant, const MechTables &mt, const BatchArgs &a,
+                           const StepParams &p, const BatchScratch &s, int order_mode,
+                           int ctas_per_sm, cudaStream_t st) {
+  if (a.n <= 0) return cudaSuccess;
+  const int block = 128;
+  const unsigned grid_cells = (unsigned)((a.n + block - 1) / block);
+  cudaError_t e;
+  const int32_t *order = nullptr;
+  if (order_mode == CHEM_ORDER_STIFFNESS) {
+    e = cudaMemsetAsync(s.hist, 0, kBatchBuckets * sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    k_probe<<<grid_cells, block, 0, st>>>(mt, a, p.rtol, p.atol, s.bucket, s.hist);
+    k_scan<<<1, 32, 0, st>>>(s.hist, s.cursor);
+    k_scatter<<<grid_cells, block, 0, st>>>(a.n, s.bucket, s.hist, s.order);
+    order = s.order;
+  } else {
+    e = cudaMemsetAsync(s.cursor, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+  }
+  int sms = 0;
+  const int cap = persistent_capacity(variant, &sms);
+  const int per = (ctas_per_sm > 0 && ctas_per_sm < cap) ? ctas_per_sm : cap;
+  const int64_t cap_ctas = (int64_t)sms * per;
+  const unsigned grid = (unsigned)(cap_ctas < (int64_t)grid_cells ? cap_ctas : (int64_t)grid_cells);
+  if (variant == CHEM_VARIANT_MIXED)
+    k_lsrk_persistent<CHEM_VARIANT_MIXED><<<grid, block, 0, st>>>(mt, a, p, order, s.cursor);
+  else
+    k_lsrk_persistent<CHEM_VARIANT_FP64><<<grid, block, 0, st>>>(mt, a, p, order, s.cursor);
+  return cudaGetLastError();
+}
+
+}  // namespace chem

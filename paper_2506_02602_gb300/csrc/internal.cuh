@@ -30,9 +30,41 @@ struct StepParams {
   int32_t max_steps;
 };
 
+constexpr int kBatchBuckets = 64;
+
+// A ragged batch (device pointers).
+struct BatchArgs {
+  const double *rho;
+  const double *e;
+  double *Y;
+  int64_t ld;
+  double *T;
+  double *h;
+  int32_t *status;
+  int32_t *nsteps;
+  int64_t n;
+  const int64_t *box_off;
+  const double *box_dt;
+  const int32_t *box_nsub;
+  int32_t nboxes;
+  const int32_t *cost_hint;
+  chem_stats *stats;
+};
+
+// Context-owned queue scratch of the batched path.
+struct BatchScratch {
+  int32_t *order;                // [n] cell indices in queue order
+  uint8_t *bucket;               // [n] stiffness bucket per cell
+  int32_t *hist;                 // [kBatchBuckets] counts, then running offsets
+  unsigned long long *cursor;    // [1] next queue slot
+};
+
 // Launchers (integrate.cu).  Return the cudaError_t of the launch.
 cudaError_t launch_lsrk(int variant, const MechTables &mt, const CellArgs &a, const StepParams &p,
                         int block, cudaStream_t s);
+cudaError_t launch_batched(int variant, const MechTables &mt, const BatchArgs &a,
+                           const StepParams &p, const BatchScratch &s, int order_mode,
+                           int ctas_per_sm, cudaStream_t st);
 cudaError_t launch_state_from_TPY(const MechTables &mt, int64_t n, const double *T,
                                   const double *p, const double *Y, int64_t ld, double *rho,
                                   double *e, cudaStream_t s);

@@ -121,10 +121,12 @@ __device__ __forceinline__ double troe_F(const MechTables &mt, double T, double 
   }
 }
 
-// Rate of progress of reaction J added into wdot (law of mass action, Eq. 16).
-template <int J>
+// Rate of progress of reaction J added into wdot (law of mass action, Eq. 16).  With
+// kDestr, the one-way fluxes that consume each species are also summed into dflux
+// (used by the stiffness probe: consumption rate per unit concentration).
+template <int J, bool kDestr = false>
 __device__ __forceinline__ void reaction(const MechTables &mt, const RateInputs &in, double T,
-                                         double (&wdot)[NSP]) {
+                                         double (&wdot)[NSP], double *dflux = nullptr) {
   constexpr RxStruct R = kRx[J];
   constexpr int dnu = n_prod(R) - n_reac(R);
   static_assert(dnu >= -1 && dnu <= 1, "compiled structure assumes |sum nu| <= 1");
@@ -150,7 +152,7 @@ __device__ __forceinline__ void reaction(const MechTables &mt, const RateInputs 
   }
   double qf = kf * in.c[R.r0];
   if constexpr (R.r1 >= 0) qf *= in.c[R.r1];
-  double q = qf;
+  double q = qf, qr = 0.0;
   if (mt.reversible[J]) {
     double kr = kf * in.G[R.r0];
     if constexpr (R.r1 >= 0) kr *= in.G[R.r1];
@@ -158,26 +160,37 @@ __device__ __forceinline__ void reaction(const MechTables &mt, const RateInputs 
     if constexpr (R.p1 >= 0) kr *= in.iG[R.p1];
     if constexpr (dnu == 1) kr *= in.RTP;
     if constexpr (dnu == -1) kr *= in.PRT;
-    double qr = kr * in.c[R.p0];
+    qr = kr * in.c[R.p0];
     if constexpr (R.p1 >= 0) qr *= in.c[R.p1];
     q = qf - qr;
   }
   if constexpr (R.type == THIRD_BODY) q *= M;
+  if constexpr (kDestr) {
+    const double m = (R.type == THIRD_BODY) ? M : 1.0;
+    dflux[R.r0] += m * qf;
+    if constexpr (R.r1 >= 0) dflux[R.r1] += m * qf;
+    dflux[R.p0] += m * qr;
+    if constexpr (R.p1 >= 0) dflux[R.p1] += m * qr;
+  }
   wdot[R.r0] -= q;
   if constexpr (R.r1 >= 0) wdot[R.r1] -= q;
   wdot[R.p0] += q;
   if constexpr (R.p1 >= 0) wdot[R.p1] += q;
 }
 
-template <int... J>
+template <bool kDestr, int... J>
 __device__ __forceinline__ void all_reactions(const MechTables &mt, const RateInputs &in, double T,
-                                              double (&wdot)[NSP], std::integer_sequence<int, J...>) {
-  (reaction<J>(mt, in, T, wdot), ...);
+                                              double (&wdot)[NSP], double *dflux,
+                                              std::integer_sequence<int, J...>) {
+  (reaction<J, kDestr>(mt, in, T, wdot, dflux), ...);
 }
 
 // Molar production rates wdot (mol/m^3/s) at temperature T and clamped concentrations c.
+// kDestr: also the consumption fluxes per species into dflux (zeroed here).
+template <bool kDestr = false>
 __device__ __forceinline__ void production_rates(const MechTables &mt, double T,
-                                                 const double (&c)[NSP], double (&wdot)[NSP]) {
+                                                 const double (&c)[NSP], double (&wdot)[NSP],
+                                                 double *dflux = nullptr) {
   RateInputs in;
   in.lnT = log_t(T);
   in.invT = 1.0 / T;
@@ -198,9 +211,10 @@ __device__ __forceinline__ void production_rates(const MechTables &mt, double T,
     in.G[k] = exp_t(-g);
     in.iG[k] = 1.0 / in.G[k];
     wdot[k] = 0.0;
+    if constexpr (kDestr) dflux[k] = 0.0;
   }
   in.ctot = ctot;
-  all_reactions(mt, in, T, wdot, std::make_integer_sequence<int, NRX>{});
+  all_reactions<kDestr>(mt, in, T, wdot, dflux, std::make_integer_sequence<int, NRX>{});
 }
 
 // dY/dt of one cell at fixed (rho, e).  T: in = Newton guess, out = solved T.

@@ -55,6 +55,14 @@ def test_reactors_through_ignition(ctx):
     ref = O.integrate(rho, e, r["Y"], r["T"], 1e-5)
     cond = sensitivity(O, rho, e, r["Y"], r["T"], 1e-5)
     gpu = run_device(ctx, rho, e, r["Y"], r["T"], 1e-5)
+    ill = (cond[0] > 1e-11) | (cond[1] > 1e-11) | cond[2]
+    dY = np.abs(gpu["Y"] - ref["Y"]).max(axis=0)
+    worst = np.argsort(np.where(ill, -1.0, dY))[::-1][:5]
+    for i in worst:  # diagnostics of the worst well-conditioned cells
+        print("cell", i, "dY %.2e dT/T %.2e" % (dY[i], abs(gpu["T"][i] - ref["T"][i]) / ref["T"][i]),
+              "T0 %.1f p %.3g" % (r["T"][i], r["p"][i]), "T1 %.1f" % ref["T"][i],
+              "steps gpu/or", gpu["nsteps"][i], ref["nsteps"][i], "margin %.2e" % ref["margin"][i],
+              "cond %.2e %.2e" % (cond[0][i], cond[1][i]))
     res = compare(gpu, ref, cond=cond)
     print(res)
     assert res["strict"] > 0.25 * res["n"]
