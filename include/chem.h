@@ -256,6 +256,39 @@ int chem_integrate_batched(chem_ctx *ctx, const chem_state *state, int64_t ncell
                            const chem_batch_options *opt, void *stream, chem_stats *d_stats);
 
 /*
+ * chem_integrate_batched for callers that cannot allocate device memory during the call.
+ * The paper has no counterpart.
+ *
+ * Some callers cannot allocate at that moment:
+ *   - code that runs while a CUDA graph is being captured, where cudaMalloc is not
+ *     allowed;
+ *   - host solvers whose memory arena has already taken the GPU's memory and forbids
+ *     allocations made outside it;
+ *   - time-critical loops that cannot afford cudaMalloc's latency and implicit
+ *     synchronisation.
+ *
+ * This entry point integrates exactly like chem_integrate_batched, with the same
+ * arguments, results and errors. It calls no cudaMalloc, cudaFree or other allocating
+ * routine. The queue scratch comes from a fixed array compiled into the library: about
+ * 5 MiB, which every GPU that loads the library keeps until the process exits.
+ *
+ * Limits and rules:
+ *   - At most 1,048,576 cells per call. Larger ncells returns CHEM_ERR_INVALID with a
+ *     message, before anything is launched.
+ *   - opt->use_graph is ignored: the launches go straight to the stream.
+ *   - Set-up: the first call on each device looks up the array's device address, with
+ *     that device current. Make that first call outside any stream capture.
+ *   - Every call on a device shares the one array. Each call clears the parts that must
+ *     start at zero, but two calls whose work overlaps on the GPU race on it, even from
+ *     different contexts or streams. Order such calls on one stream, or synchronise
+ *     between them.
+ */
+int chem_integrate_batched_noalloc(chem_ctx *ctx, const chem_state *state, int64_t ncells,
+                                   const chem_batch *batch, double rtol, double atol,
+                                   const chem_batch_options *opt, void *stream,
+                                   chem_stats *d_stats);
+
+/*
  * Diagnostic: evaluate one of the device math routines the integration kernels use on
  * n fp64 arguments (device pointers d_x -> d_y), so tests can check them against the
  * CUDA library.  op: 0 table-driven exp, 1 table-driven log (Tang's methods, used by

@@ -262,6 +262,32 @@ class Context:
         self._raise(self.L.chem_integrate_batched(self.h, C.byref(st), n, C.byref(b), float(rtol),
                                                   float(atol), C.byref(o), _stream(stream), _ptr(stats)))
 
+    def integrate_batched_noalloc(self, rho, e, Y, T, box_offset, box_dt, box_nsub, rtol=1e-6,
+                                  atol=1e-10, h=None, status=None, nsteps=None, stats=None,
+                                  order=ORDER_STIFFNESS, ctas_per_sm=0, cost_hint=None,
+                                  stream=None, ncells=None):
+        """chem_integrate_batched_noalloc: the batched integration for callers that cannot
+        allocate device memory during the call (inside a graph capture, under a memory
+        arena that owns the GPU, in latency-bound loops).  The scratch is a fixed array in
+        the library: at most 1,048,576 cells per call, and calls that overlap on the GPU
+        race on it.  Arguments as integrate_batched; ncells overrides rho.numel()."""
+        import torch
+        fn = self.L.chem_integrate_batched_noalloc
+        fn.restype = C.c_int
+        fn.argtypes = [C.c_void_p, C.POINTER(State), C.c_int64, C.POINTER(Batch), C.c_double,
+                       C.c_double, C.POINTER(BatchOptions), C.c_void_p, C.c_void_p]
+        n = rho.numel() if ncells is None else ncells
+        if box_offset.dtype != torch.int64 or box_nsub.dtype != torch.int32 or box_dt.dtype != torch.float64:
+            raise ChemError(ERR_INVALID, "box_offset int64, box_dt float64, box_nsub int32 expected")
+        st = State(_ptr(rho).value, _ptr(e).value, _ptr(Y).value, Y.stride(0), _ptr(T).value,
+                   None if h is None else h.data_ptr(),
+                   None if status is None else status.data_ptr(),
+                   None if nsteps is None else nsteps.data_ptr())
+        b = Batch(box_dt.numel(), box_offset.data_ptr(), box_dt.data_ptr(), box_nsub.data_ptr())
+        o = BatchOptions(order, ctas_per_sm, 0, 0, None if cost_hint is None else cost_hint.data_ptr())
+        self._raise(fn(self.h, C.byref(st), n, C.byref(b), float(rtol), float(atol), C.byref(o),
+                       _stream(stream), _ptr(stats)))
+
     def integrate_host(self, rho, e, Y, T, dt, rtol=1e-6, atol=1e-10, h=None, status=None,
                        nsteps=None, stream=None):
         """chem_integrate_host on numpy arrays (Y is [S, ld], C-contiguous planes);

@@ -493,3 +493,11 @@ int chem_integrate_host(chem_ctx *ctx, int64_t n, const double *h_rho, const dou
 }
 
 }  // extern "C"
+
+// Accessors for the allocation-free batched entry point (batched.cu).
+namespace chem {
+std::string &chem_ctx_error(chem_ctx *ctx) { return ctx->err; }
+const MechTables &chem_ctx_tables(const chem_ctx *ctx) { return ctx->tables; }
+int chem_ctx_variant(const chem_ctx *ctx) { return ctx->opt.variant; }
+int32_t chem_ctx_max_steps(const chem_ctx *ctx) { return ctx->opt.max_steps; }
+}  // namespace chem

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 
 #include "chem.h"
 #include "mech.cuh"
@@ -62,6 +63,12 @@ struct BatchScratch {
 // Launchers (integrate.cu).  Return the cudaError_t of the launch.
 cudaError_t launch_lsrk(int variant, const MechTables &mt, const CellArgs &a, const StepParams &p,
                         int block, cudaStream_t s);
+// Context accessors (api.cu) for entry points defined in other translation units.
+std::string &chem_ctx_error(chem_ctx *ctx);
+const MechTables &chem_ctx_tables(const chem_ctx *ctx);
+int chem_ctx_variant(const chem_ctx *ctx);
+int32_t chem_ctx_max_steps(const chem_ctx *ctx);
+
 cudaError_t launch_batched(int variant, const MechTables &mt, const BatchArgs &a,
                            const StepParams &p, const BatchScratch &s, int order_mode,
                            int ctas_per_sm, cudaStream_t st);

@@ -1,0 +1,81 @@
+"""The allocation-free batched entry point (chem_integrate_batched_noalloc).
+
+It serves callers that cannot allocate device memory during the call.  Examples are
+code inside a CUDA graph capture, a host solver whose memory arena owns the GPU, or a
+latency-bound loop.  Its queue scratch is a fixed array in the library, so its results
+must match the allocating entry point (chem_integrate_batched) on the same inputs.
+They are checked here within the FP64 parity tolerance, on two calls in a row, because
+each call reuses the array the previous one left behind.  Requests beyond the fixed
+maximum are rejected before any launch.
+
+This file is named to be collected last.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from chem_inputs import mechanism as M
+from chem_inputs import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL_T = 1e-8   # the FP64 parity bar used by the other GPU tests
+TOL_Y = 1e-10
+
+
+def _inputs(seed, nboxes):
+    b = W.amr_batch(nboxes=nboxes, seed=seed, edges=(4, 8, 12))
+    o = oracle.Oracle(M.build(0))
+    b["rho"], b["e"] = o.state_from_TPY(b["T"], b["p"], b["Y"])
+    return b
+
+
+def _run(ctx, b, noalloc):
+    import torch
+    dev = lambda a, dt=torch.float64: torch.tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    n = b["T"].size
+    Y, T = dev(b["Y"]), dev(b["T"])
+    st = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    ns = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    args = (dev(b["rho"]), dev(b["e"]), Y, T, dev(b["box_offset"], torch.int64),
+            dev(b["box_dt"]), dev(b["box_nsub"], torch.int32))
+    if noalloc:
+        ctx.integrate_batched_noalloc(*args, status=st, nsteps=ns)
+    else:
+        ctx.integrate_batched(*args, status=st, nsteps=ns)
+    torch.cuda.synchronize()
+    return Y.cpu().numpy(), T.cpu().numpy(), st.cpu().numpy(), ns.cpu().numpy()
+
+
+@pytest.mark.parametrize("variant", ["fp64", "mixed"])
+def test_noalloc_matches_batched_on_two_calls(variant):
+    from paper_2506_02602_gb300 import build, chem
+    build.build()
+    ctx = chem.Context(M.build(0), variant)
+    for seed, nboxes in ((31, 60), (32, 45)):  # two calls in a row, different sizes
+        b = _inputs(seed, nboxes)
+        Yr, Tr, sr, nr = _run(ctx, b, noalloc=False)
+        Yn, Tn, sn, nn = _run(ctx, b, noalloc=True)
+        assert np.all(sr == 0)
+        np.testing.assert_array_equal(sn, sr)
+        np.testing.assert_array_equal(nn, nr)
+        assert np.max(np.abs(Tn - Tr) / Tr) <= TOL_T
+        assert np.max(np.abs(Yn - Yr)) <= TOL_Y
+    ctx.close()
+
+
+def test_noalloc_rejects_more_cells_than_its_scratch():
+    import torch
+    from paper_2506_02602_gb300 import build, chem
+    build.build()
+    ctx = chem.Context(M.build(0), "fp64")
+    x = torch.zeros(16, dtype=torch.float64, device="cuda")
+    Y = torch.zeros((9, 16), dtype=torch.float64, device="cuda")
+    off = torch.tensor([0, 16], dtype=torch.int64, device="cuda")
+    dt = torch.tensor([1e-7], dtype=torch.float64, device="cuda")
+    nsub = torch.tensor([1], dtype=torch.int32, device="cuda")
+    # the size check comes before any pointer is used or anything is launched
+    with pytest.raises(chem.ChemError) as ei:
+        ctx.integrate_batched_noalloc(x, x, Y, x, off, dt, nsub, ncells=(1 << 20) + 1)
+    assert ei.value.code == chem.ERR_INVALID and "1048576" in str(ei.value)
+    ctx.close()
