@@ -255,6 +255,103 @@ int chem_integrate_batched(chem_ctx *ctx, const chem_state *state, int64_t ncell
                            const chem_batch *batch, double rtol, double atol,
                            const chem_batch_options *opt, void *stream, chem_stats *d_stats);
 
+/* ---------------------------------------------------------------- learned surrogate
+ *
+ * A multilayer perceptron 12 -> 256 -> 256 -> 256 -> 9 (GELU, BF16 weights and
+ * activations, FP32 accumulation and master weights) that maps a cell's state and step
+ * to the change of its Box-Cox-transformed mass fractions over the step.  The paper
+ * names learning the chemical source term as future work (Sec. 7).  Inputs (z-scored
+ * with training statistics): T, ln p, log10 dt, BC(Y_k) = (max(Y_k, 1e-30)^lam - 1) / lam;
+ * outputs: BC(Y_k(t + dt)) - BC(Y_k(t)).  After inference the predicted mass fractions
+ * are projected in fp64 onto the element (H, O, N) mass fractions of the input (weighted
+ * least squares), the temperature is solved from (e, Y) in fp64, and a gate decides per
+ * cell whether the answer stands; rejected cells are integrated by the cell's precision
+ * variant of chem_integrate instead.
+ */
+
+/* Training pairs, all device arrays of n entries (Y planes with stride ld). */
+typedef struct {
+  const double *d_rho;
+  const double *d_e;
+  const double *d_Y0;  /* mass fractions at t (planes, stride ldY0) */
+  int64_t ldY0;
+  const double *d_T0;  /* nullable: temperature guess at t */
+  const double *d_dt;  /* step of each pair, s */
+  const double *d_Y1;  /* mass fractions at t + dt (planes, stride ldY1) */
+  int64_t ldY1;
+} chem_pairs;
+
+/* Training configuration.  Zero-initialised fields take the defaults in brackets. */
+typedef struct {
+  int32_t epochs;       /* [20] */
+  int32_t batch;        /* [4096] rows per Adam step */
+  float lr;             /* [1e-3] Adam learning rate, cosine-decayed to lr_final */
+  float lr_final;       /* [lr / 20] */
+  float boxcox_lambda;  /* [0.1] */
+  int32_t reserved0;    /* must be zero */
+  uint64_t seed;        /* weight initialisation and shuffling [0] */
+} chem_train_cfg;
+
+/* Inference gate.  Zero-initialised fields take the defaults in brackets. */
+typedef struct {
+  float ood_margin;  /* [0.05] accepted feature range: training range widened by this fraction */
+  float resid_max;   /* [0.02] largest relative element-mass residual before projection */
+  float neg_tol;     /* [1e-6] most negative mass fraction allowed after projection */
+  float max_dT;      /* [25] largest accepted |T(t + dt) - T(t)|, K */
+} chem_surrogate_gate;
+
+/* Number of float parameters of the network (flat layout W0 [256x16], b0 [256], W1
+ * [256x256], b1, W2 [256x256], b2, W3 [16x256], b3 [16]; input columns 12..15 and output
+ * rows 9..15 are padding and stay zero). */
+int64_t chem_surrogate_param_count(void);
+
+/*
+ * Train the surrogate on npairs pairs (fresh weights from cfg->seed): featurise all
+ * pairs, take the normalisation statistics and feature ranges, then per epoch a seeded
+ * shuffle and floor(npairs / batch) Adam steps of forward, mean-squared error over the
+ * 9 outputs, and backward, all on the GPU.  h_epoch_loss (nullable, host [epochs])
+ * receives the mean loss of each epoch.  Synchronous (returns when training is done).
+ * Errors: npairs < batch or NULL arrays -> CHEM_ERR_INVALID; allocation -> CHEM_ERR_NOMEM.
+ */
+int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
+                         const chem_train_cfg *cfg, void *stream, float *h_epoch_loss);
+
+/*
+ * Advance the state over dt with the surrogate (chem_state as in chem_integrate).  Per
+ * cell: features -> network -> inverse transform -> fp64 projection -> fp64 temperature
+ * -> gate (feature range, element residual, negativity, temperature solve, |dT|).
+ * Accepted cells get the projected Y, its T, status CHEM_CELL_OK and nsteps 0; rejected
+ * cells are integrated with rtol, atol (one thread per cell, the context's variant) and
+ * get status CHEM_CELL_SURROGATE, or the integrator's failure code, and their attempted
+ * steps.  d_fallback_mask (nullable, device uint8 [ncells]) receives 1 for rejected
+ * cells.  d_stats (nullable): status_count[CHEM_CELL_SURROGATE] counts fallbacks.
+ * gate may be NULL.  Errors: no trained or loaded network -> CHEM_ERR_STATE; arguments
+ * as chem_integrate.  Asynchronous on stream.
+ */
+int chem_surrogate_infer(chem_ctx *ctx, const chem_state *state, int64_t ncells, double dt,
+                         double rtol, double atol, const chem_surrogate_gate *gate, void *stream,
+                         uint8_t *d_fallback_mask, chem_stats *d_stats);
+
+/* Write / read the trained network (parameters, Box-Cox lambda, normalisation and
+ * feature ranges) to / from a binary file.  Synchronous.  Errors: I/O -> CHEM_ERR_INVALID;
+ * save without a network -> CHEM_ERR_STATE. */
+int chem_surrogate_save(chem_ctx *ctx, const char *path);
+int chem_surrogate_load(chem_ctx *ctx, const char *path);
+
+/* Copy the flat fp32 parameters out (h_out) and / or in (h_in, resets Adam); n must equal
+ * chem_surrogate_param_count().  Synchronous. */
+int chem_surrogate_params(chem_ctx *ctx, float *h_out, const float *h_in, int64_t n);
+
+/*
+ * One forward and backward pass on a given batch without updating the weights, for
+ * checks: d_X [B x 16] normalised features, d_T [B x 16] normalised targets (fp32 device),
+ * d_Y [B x 16] (fp32 device, out) network output, h_grad (host, flat like the parameters,
+ * out) gradient of the mean squared error over the 9 outputs, h_loss (host, out).
+ * Synchronous.
+ */
+int chem_surrogate_grad(chem_ctx *ctx, const float *d_X, const float *d_T, int64_t B, float *d_Y,
+                        float *h_grad, float *h_loss, void *stream);
+
 /*
  * chem_integrate_batched for callers that cannot allocate device memory during the call.
  * The paper has no counterpart.

@@ -83,6 +83,21 @@ class BatchOptions(C.Structure):
                 ("reserved", C.c_int32), ("d_cost_hint", C.c_void_p)]
 
 
+class Pairs(C.Structure):
+    _fields_ = [("d_rho", C.c_void_p), ("d_e", C.c_void_p), ("d_Y0", C.c_void_p), ("ldY0", C.c_int64),
+                ("d_T0", C.c_void_p), ("d_dt", C.c_void_p), ("d_Y1", C.c_void_p), ("ldY1", C.c_int64)]
+
+
+class TrainCfg(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("lr_final", C.c_float),
+                ("boxcox_lambda", C.c_float), ("reserved0", C.c_int32), ("seed", C.c_uint64)]
+
+
+class Gate(C.Structure):
+    _fields_ = [("ood_margin", C.c_float), ("resid_max", C.c_float), ("neg_tol", C.c_float),
+                ("max_dT", C.c_float)]
+
+
 ORDER_STIFFNESS, ORDER_NATURAL = 0, 1
 STATS_WORDS = C.sizeof(Stats) // 8
 
@@ -109,6 +124,14 @@ def load() -> C.CDLL:
         "chem_diag_math": (C.c_int, [C.c_int, i64, vp, vp, vp]),
         "chem_integrate_batched": (C.c_int, [vp, C.POINTER(State), i64, C.POINTER(Batch), dbl, dbl,
                                              C.POINTER(BatchOptions), vp, vp]),
+        "chem_surrogate_param_count": (C.c_int64, []),
+        "chem_surrogate_train": (C.c_int, [vp, C.POINTER(Pairs), i64, C.POINTER(TrainCfg), vp, vp]),
+        "chem_surrogate_infer": (C.c_int, [vp, C.POINTER(State), i64, dbl, dbl, dbl, C.POINTER(Gate),
+                                           vp, vp, vp]),
+        "chem_surrogate_save": (C.c_int, [vp, C.c_char_p]),
+        "chem_surrogate_load": (C.c_int, [vp, C.c_char_p]),
+        "chem_surrogate_params": (C.c_int, [vp, vp, vp, i64]),
+        "chem_surrogate_grad": (C.c_int, [vp, vp, vp, i64, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -287,6 +310,66 @@ class Context:
         o = BatchOptions(order, ctas_per_sm, 0, 0, None if cost_hint is None else cost_hint.data_ptr())
         self._raise(fn(self.h, C.byref(st), n, C.byref(b), float(rtol), float(atol), C.byref(o),
                        _stream(stream), _ptr(stats)))
+
+    # learned surrogate ------------------------------------------------------------
+    def surrogate_train(self, rho, e, Y0, dt, Y1, T0=None, epochs=20, batch=4096, lr=1e-3,
+                        lr_final=0.0, boxcox_lambda=0.1, seed=0, stream=None):
+        """chem_surrogate_train on CUDA tensors (Y0, Y1: [S, n] planes; dt: [n]).
+        Returns the mean loss of every epoch (numpy)."""
+        n = rho.numel()
+        for nm, t in (("rho", rho), ("e", e), ("Y0", Y0), ("dt", dt), ("Y1", Y1)):
+            _check_f64_cuda(nm, t, n)
+        pr = Pairs(rho.data_ptr(), e.data_ptr(), Y0.data_ptr(), Y0.stride(0),
+                   None if T0 is None else T0.data_ptr(), dt.data_ptr(), Y1.data_ptr(), Y1.stride(0))
+        cfg = TrainCfg(epochs, batch, lr, lr_final, boxcox_lambda, 0, seed)
+        loss = np.zeros(max(epochs, 1), dtype=np.float32)
+        self._raise(self.L.chem_surrogate_train(self.h, C.byref(pr), n, C.byref(cfg), _stream(stream),
+                                                loss.ctypes.data_as(C.c_void_p)))
+        return loss[:epochs]
+
+    def surrogate_infer(self, rho, e, Y, T, dt, rtol=1e-6, atol=1e-10, status=None, nsteps=None,
+                        mask=None, stats=None, gate=None, stream=None):
+        """chem_surrogate_infer: advance Y, T in place over dt; gate is a dict of
+        ood_margin / resid_max / neg_tol / max_dT (0 or missing = default)."""
+        n = rho.numel()
+        st = State(_ptr(rho).value, _ptr(e).value, _ptr(Y).value, Y.stride(0), _ptr(T).value, None,
+                   None if status is None else status.data_ptr(),
+                   None if nsteps is None else nsteps.data_ptr())
+        g = Gate(**(gate or {}))
+        self._raise(self.L.chem_surrogate_infer(self.h, C.byref(st), n, float(dt), float(rtol),
+                                                float(atol), C.byref(g), _stream(stream), _ptr(mask),
+                                                _ptr(stats)))
+
+    def surrogate_save(self, path):
+        self._raise(self.L.chem_surrogate_save(self.h, os.fsencode(path)))
+
+    def surrogate_load(self, path):
+        self._raise(self.L.chem_surrogate_load(self.h, os.fsencode(path)))
+
+    def surrogate_params(self, new=None):
+        """Flat fp32 parameters (numpy); with `new`, upload them first (resets Adam)."""
+        n = self.L.chem_surrogate_param_count()
+        out = np.zeros(n, dtype=np.float32)
+        src = None
+        if new is not None:
+            src = np.ascontiguousarray(new, dtype=np.float32)
+            assert src.size == n
+        self._raise(self.L.chem_surrogate_params(self.h, out.ctypes.data_as(C.c_void_p),
+                                                 None if src is None else src.ctypes.data_as(C.c_void_p), n))
+        return out
+
+    def surrogate_grad(self, X, T, stream=None):
+        """chem_surrogate_grad on fp32 CUDA tensors X, T [B, 16]: returns (Y [B, 16] tensor,
+        flat gradient numpy, loss)."""
+        import torch
+        B = X.shape[0]
+        Y = torch.empty((B, 16), dtype=torch.float32, device=X.device)
+        g = np.zeros(self.L.chem_surrogate_param_count(), dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        self._raise(self.L.chem_surrogate_grad(self.h, _ptr(X), _ptr(T), B, _ptr(Y),
+                                               g.ctypes.data_as(C.c_void_p), loss.ctypes.data_as(C.c_void_p),
+                                               _stream(stream)))
+        return Y, g, float(loss[0])
 
     def integrate_host(self, rho, e, Y, T, dt, rtol=1e-6, atol=1e-10, h=None, status=None,
                        nsteps=None, stream=None):

@@ -31,6 +31,8 @@ struct chem_ctx {
   cudaStream_t cap_stream = nullptr;  // private stream the graph is captured on
   unsigned char graph_key[512];
   size_t graph_key_len = 0;
+  // learned surrogate (surrogate.cu), created by training or loading
+  void *sur = nullptr;
 };
 
 namespace {
@@ -172,6 +174,14 @@ int build_tables(const chem_mechanism *m, MechTables *t) {
     }
     t->has_eff[j] = any;
   }
+  // element matrix (standard atomic masses of H, O, N)
+  const double amass[CHEM_NUM_ELEMENTS] = {1.008e-3, 15.999e-3, 14.007e-3};
+  for (int k = 0; k < NSP; ++k) {
+    double wk = 0.0;
+    for (int el = 0; el < CHEM_NUM_ELEMENTS; ++el) wk += m->ncomp[k][el] * amass[el];
+    for (int el = 0; el < CHEM_NUM_ELEMENTS; ++el)
+      t->Emat[el][k] = wk > 0.0 ? m->ncomp[k][el] * amass[el] / wk : 0.0;
+  }
   // fp32 copies for the mixed-precision kernel
   t->ln_R_over_Pref = std::log(R_U / P_REF);
   for (int k = 0; k < NSP; ++k) {
@@ -265,6 +275,7 @@ int chem_teardown(chem_ctx *ctx) {
   if (ctx->batch_scratch) cudaFree(ctx->batch_scratch);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->sur) surrogate_destroy(ctx->sur);
   delete ctx;
   return CHEM_OK;
 }
@@ -500,4 +511,5 @@ std::string &chem_ctx_error(chem_ctx *ctx) { return ctx->err; }
 const MechTables &chem_ctx_tables(const chem_ctx *ctx) { return ctx->tables; }
 int chem_ctx_variant(const chem_ctx *ctx) { return ctx->opt.variant; }
 int32_t chem_ctx_max_steps(const chem_ctx *ctx) { return ctx->opt.max_steps; }
+void *&chem_ctx_sur(chem_ctx *ctx) { return ctx->sur; }
 }  // namespace chem

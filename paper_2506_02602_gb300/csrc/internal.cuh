@@ -68,6 +68,8 @@ std::string &chem_ctx_error(chem_ctx *ctx);
 const MechTables &chem_ctx_tables(const chem_ctx *ctx);
 int chem_ctx_variant(const chem_ctx *ctx);
 int32_t chem_ctx_max_steps(const chem_ctx *ctx);
+void *&chem_ctx_sur(chem_ctx *ctx);
+void surrogate_destroy(void *sur);
 
 cudaError_t launch_batched(int variant, const MechTables &mt, const BatchArgs &a,
                            const StepParams &p, const BatchScratch &s, int order_mode,

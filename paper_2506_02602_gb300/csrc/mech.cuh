@@ -93,6 +93,9 @@ struct MechTables {
   double effm1[NRX][NSP];
   int32_t has_eff[NRX];
   double ln_R_over_Pref;  // ln(R_u / p_ref): ln(R_u T / p_ref) = ln T + this
+  // element mass fraction (H, O, N) per unit mass fraction of species k:
+  // n_ke A_e / sum_e' n_ke' A_e' (columns sum to 1, so conserving elements conserves sum Y)
+  double Emat[3][NSP];
   MechTablesF32 f;
 };
 

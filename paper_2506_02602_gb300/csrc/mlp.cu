@@ -1,0 +1,259 @@
+// mlp.cu -- tensor-core building blocks of the learned surrogate: a BF16 GEMM with
+// FP32 accumulation and a fused epilogue, and the elementwise kernels of training
+// (GELU backward, MSE gradient, bias-gradient reduction, Adam with FP32 master weights
+// and BF16 shadows, row gather).
+//
+// GEMM: C[m, n] = alpha * sum_k A(m, k) B(n, k) (+ bias[n]), with A(m, k) = A[m*sam + k*sak]
+// and B(n, k) = B[n*sbn + k*sbk] in BF16, so one kernel serves the forward layer
+// (X W^T), the input gradient (dZ W) and the weight gradient (X^T dZ) through strides.
+// A 128 x 128 CTA tile, 8 warps of 32 x 64, K in steps of 32 staged in shared memory
+// (k-contiguous rows, padded against bank conflicts), ldmatrix fragments and
+// mma.sync.m16n8k16 BF16 -> FP32.  Epilogue: alpha, optional bias, FP32 store and/or
+// BF16 store of the value or of GELU(value).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.cuh"
+#include "mlp.cuh"
+
+namespace chem {
+
+constexpr int GBM = 128, GBN = 128, GBK = 32, GPAD = 8;
+constexpr int GTHREADS = 256;
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
+__device__ __forceinline__ float gelu_grad_f(float x) {
+  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+}
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const void *smem) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
+__device__ __forceinline__ void ldmatrix_x2(uint32_t (&r)[2], const void *smem) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(a));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(GTHREADS) k_gemm_bf16(GemmArgs g) {
+  __shared__ __align__(16) __nv_bfloat16 As[GBM][GBK + GPAD];
+  __shared__ __align__(16) __nv_bfloat16 Bs[GBN][GBK + GPAD];
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int wm = (warp & 3) * 32;   // warp row offset in the CTA tile
+  const int wn = (warp >> 2) * 64;  // warp column offset
+  const int64_t m0 = (int64_t)blockIdx.y * GBM;
+  const int64_t n0 = (int64_t)blockIdx.x * GBN;
+  float acc[2][8][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
+  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+  for (int64_t k0 = 0; k0 < g.K; k0 += GBK) {
+    // stage the A and B tiles (16 elements per thread each); the k index runs fastest
+    // across threads so k-contiguous operands load coalesced
+    for (int idx = tid; idx < GBM * GBK; idx += GTHREADS) {
+      const int r = idx / GBK, c = idx % GBK;
+      const int64_t m = m0 + r, k = k0 + c;
+      As[r][c] = (m < g.M && k < g.K) ? g.A[m * g.sam + k * g.sak] : zero;
+    }
+    for (int idx = tid; idx < GBN * GBK; idx += GTHREADS) {
+      const int r = idx / GBK, c = idx % GBK;
+      const int64_t n = n0 + r, k = k0 + c;
+      Bs[r][c] = (n < g.N && k < g.K) ? g.B[n * g.sbn + k * g.sbk] : zero;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GBK; kk += 16) {
+      uint32_t af[2][4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int q = lane >> 3, rr = lane & 7;
+        ldmatrix_x4(af[i], &As[wm + i * 16 + (q & 1) * 8 + rr][kk + (q >> 1) * 8]);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        uint32_t bf[2];
+        const int q = (lane >> 3) & 1, rr = lane & 7;
+        ldmatrix_x2(bf, &Bs[wn + j * 8 + rr][kk + q * 8]);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) mma_bf16(acc[i][j], af[i], bf);
+      }
+    }
+    __syncthreads();
+  }
+  // epilogue: fragment (i, j) covers rows wm + 16i + {g, g+8}, cols wn + 8j + 2t + {0, 1}
+  const int gq = lane >> 2, tq = lane & 3;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t m = m0 + wm + i * 16 + gq + (q >> 1) * 8;
+        const int64_t n = n0 + wn + j * 8 + tq * 2 + (q & 1);
+        if (m < g.M && n < g.N) {
+          float v = acc[i][j][q] * g.alpha;
+          if (g.bias) v += g.bias[n];
+          if (g.accumulate) v += g.Cf[m * g.ldc + n];
+          if (g.Cf) g.Cf[m * g.ldc + n] = v;
+          if (g.Cb) g.Cb[m * g.ldcb + n] = __float2bfloat16(g.gelu ? gelu_f(v) : v);
+        }
+      }
+}
+
+cudaError_t launch_gemm(const GemmArgs &g, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((g.N + GBN - 1) / GBN), (unsigned)((g.M + GBM - 1) / GBM));
+  k_gemm_bf16<<<grid, GTHREADS, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+// dZ (bf16) = dH * GELU'(Z) with dH fp32 [M x N] (ld), Z fp32 (ld)
+__global__ void k_gelu_backward(int64_t M, int N, const float *__restrict__ dH, int ldh,
+                                const float *__restrict__ Z, int ldz, __nv_bfloat16 *__restrict__ dZ,
+                                int lddz) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= M * N) return;
+  const int64_t m = idx / N;
+  const int n = (int)(idx % N);
+  dZ[m * lddz + n] = __float2bfloat16(dH[m * ldh + n] * gelu_grad_f(Z[m * ldz + n]));
+}
+
+// MSE over the first `nout` columns: loss += sum (y - t)^2 / (M nout); dY = 2 (y - t) / (M nout)
+// (bf16, padded columns zero).  loss is accumulated with one atomic per block.
+__global__ void k_mse(int64_t M, int nout, int ldy, const float *__restrict__ Y,
+                      const float *__restrict__ Tg, int ldt, __nv_bfloat16 *__restrict__ dY,
+                      int lddy, float *loss) {
+  __shared__ float red[256];
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float l = 0.0f;
+  if (idx < M * lddy) {
+    const int64_t m = idx / lddy;
+    const int n = (int)(idx % lddy);
+    float d = 0.0f;
+    if (n < nout) {
+      d = Y[m * ldy + n] - Tg[m * ldt + n];
+      l = d * d;
+    }
+    dY[m * lddy + n] = __float2bfloat16(2.0f * d / (float)(M * nout));
+  }
+  red[threadIdx.x] = l;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(loss, red[0] / (float)(M * nout));
+}
+
+// db[n] = sum_m dZ[m, n] (one block per 32 columns, fp32 accumulation)
+__global__ void k_bias_grad(int64_t M, int N, const __nv_bfloat16 *__restrict__ dZ, int ld,
+                            float *__restrict__ db) {
+  __shared__ float red[8][33];
+  const int n = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int row = threadIdx.x >> 5;  // 8 row groups
+  float s = 0.0f;
+  if (n < N)
+    for (int64_t m = row; m < M; m += 8) s += __bfloat162float(dZ[m * ld + n]);
+  red[row][threadIdx.x & 31] = s;
+  __syncthreads();
+  if (threadIdx.x < 32 && n < N) {
+    float t = 0.0f;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) t += red[r][threadIdx.x];
+    db[n] = t;
+  }
+}
+
+// Adam on fp32 master weights; refreshes the bf16 shadows (both orientations for W).
+__global__ void k_adam(int64_t n, float *__restrict__ w, const float *__restrict__ g,
+                       float *__restrict__ m, float *__restrict__ v, float lr, float b1, float b2,
+                       float eps, float bc1, float bc2, __nv_bfloat16 *__restrict__ w_bf,
+                       __nv_bfloat16 *__restrict__ wT_bf, int rows, int cols) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.0f - b1) * gi;
+  const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float wi = w[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  w[i] = wi;
+  if (w_bf) w_bf[i] = __float2bfloat16(wi);
+  if (wT_bf) {  // w is [rows x cols] row-major; the transpose is [cols x rows]
+    const int64_t r = i / cols, c = i % cols;
+    wT_bf[c * rows + r] = __float2bfloat16(wi);
+  }
+}
+
+// out[r, :] = in[idx[r], :] for ncol columns (float)
+__global__ void k_gather_rows(int64_t nrows, int ncol, const int32_t *__restrict__ idx,
+                              const float *__restrict__ in, int ldin, float *__restrict__ out,
+                              int ldout) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nrows * ncol) return;
+  const int64_t r = t / ncol;
+  const int c = (int)(t % ncol);
+  out[r * ldout + c] = in[(int64_t)idx[r] * ldin + c];
+}
+
+// bf16 copy of a float matrix (for the gathered input features)
+__global__ void k_to_bf16(int64_t n, const float *__restrict__ in, __nv_bfloat16 *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = __float2bfloat16(in[i]);
+}
+
+static unsigned blocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+cudaError_t launch_gelu_backward(int64_t M, int N, const float *dH, int ldh, const float *Z, int ldz,
+                                 __nv_bfloat16 *dZ, int lddz, cudaStream_t s) {
+  k_gelu_backward<<<blocks(M * N, 256), 256, 0, s>>>(M, N, dH, ldh, Z, ldz, dZ, lddz);
+  return cudaGetLastError();
+}
+cudaError_t launch_mse(int64_t M, int nout, int ldy, const float *Y, const float *Tg, int ldt,
+                       __nv_bfloat16 *dY, int lddy, float *loss, cudaStream_t s) {
+  k_mse<<<blocks(M * lddy, 256), 256, 0, s>>>(M, nout, ldy, Y, Tg, ldt, dY, lddy, loss);
+  return cudaGetLastError();
+}
+cudaError_t launch_bias_grad(int64_t M, int N, const __nv_bfloat16 *dZ, int ld, float *db, cudaStream_t s) {
+  k_bias_grad<<<blocks(N, 32), 256, 0, s>>>(M, N, dZ, ld, db);
+  return cudaGetLastError();
+}
+cudaError_t launch_adam(int64_t n, float *w, const float *g, float *m, float *v, float lr, float b1,
+                        float b2, float eps, int step, __nv_bfloat16 *w_bf, __nv_bfloat16 *wT_bf,
+                        int rows, int cols, cudaStream_t s) {
+  const float bc1 = 1.0f - powf(b1, (float)step), bc2 = 1.0f - powf(b2, (float)step);
+  k_adam<<<blocks(n, 256), 256, 0, s>>>(n, w, g, m, v, lr, b1, b2, eps, bc1, bc2, w_bf, wT_bf, rows, cols);
+  return cudaGetLastError();
+}
+cudaError_t launch_gather_rows(int64_t nrows, int ncol, const int32_t *idx, const float *in, int ldin,
+                               float *out, int ldout, cudaStream_t s) {
+  k_gather_rows<<<blocks(nrows * ncol, 256), 256, 0, s>>>(nrows, ncol, idx, in, ldin, out, ldout);
+  return cudaGetLastError();
+}
+cudaError_t launch_to_bf16(int64_t n, const float *in, __nv_bfloat16 *out, cudaStream_t s) {
+  k_to_bf16<<<blocks(n, 256), 256, 0, s>>>(n, in, out);
+  return cudaGetLastError();
+}
+
+}  // namespace chem

@@ -1,0 +1,44 @@
+// mlp.cuh -- declarations of the surrogate's GEMM and elementwise kernels (mlp.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace chem {
+
+// C[m, n] = alpha * sum_k A(m, k) B(n, k) (+ bias[n]) (+ Cf[m, n] if accumulate);
+// A(m, k) = A[m*sam + k*sak], B(n, k) = B[n*sbn + k*sbk].  Outputs: Cf (fp32, ldc) and/or
+// Cb (bf16, ldcb) holding the value, or GELU(value) when gelu is set.
+struct GemmArgs {
+  int64_t M, N, K;
+  const __nv_bfloat16 *A;
+  int64_t sam, sak;
+  const __nv_bfloat16 *B;
+  int64_t sbn, sbk;
+  float alpha;
+  const float *bias;
+  float *Cf;
+  int64_t ldc;
+  __nv_bfloat16 *Cb;
+  int64_t ldcb;
+  int gelu;
+  int accumulate;
+};
+
+cudaError_t launch_gemm(const GemmArgs &g, cudaStream_t s);
+cudaError_t launch_gelu_backward(int64_t M, int N, const float *dH, int ldh, const float *Z, int ldz,
+                                 __nv_bfloat16 *dZ, int lddz, cudaStream_t s);
+cudaError_t launch_mse(int64_t M, int nout, int ldy, const float *Y, const float *Tg, int ldt,
+                       __nv_bfloat16 *dY, int lddy, float *loss, cudaStream_t s);
+cudaError_t launch_bias_grad(int64_t M, int N, const __nv_bfloat16 *dZ, int ld, float *db,
+                             cudaStream_t s);
+cudaError_t launch_adam(int64_t n, float *w, const float *g, float *m, float *v, float lr, float b1,
+                        float b2, float eps, int step, __nv_bfloat16 *w_bf, __nv_bfloat16 *wT_bf,
+                        int rows, int cols, cudaStream_t s);
+cudaError_t launch_gather_rows(int64_t nrows, int ncol, const int32_t *idx, const float *in,
+                               int ldin, float *out, int ldout, cudaStream_t s);
+cudaError_t launch_to_bf16(int64_t n, const float *in, __nv_bfloat16 *out, cudaStream_t s);
+
+}  // namespace chem

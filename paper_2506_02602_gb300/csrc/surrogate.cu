@@ -1,0 +1,628 @@
+// surrogate.cu -- the learned surrogate's host side: parameters and Adam state, the
+// training loop (featurise -> statistics -> per-epoch shuffled batches -> forward ->
+// MSE -> backward -> Adam), chunked inference (featurise -> four GEMM layers -> the
+// epilogue with projection, temperature solve and gate -> integrator fallback of the
+// rejected cells through an index list), save/load, and the entry points of chem.h.
+//
+// All arithmetic runs in the kernels of mlp.cu and surrogate_kernels.cu; this file
+// allocates, sequences launches on the caller's stream and keeps the host copies of
+// the normalisation constants.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+#include "mlp.cuh"
+#include "surrogate.cuh"
+
+namespace chem {
+
+struct Surrogate {
+  // parameters (fp32 master, flat), gradients, Adam moments
+  float *param = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+  // bf16 shadows per layer: W [N x K] and its transpose [K x N]
+  __nv_bfloat16 *W[kSurLayers] = {}, *WT[kSurLayers] = {};
+  int64_t off_W[kSurLayers], off_b[kSurLayers];
+  bool ready = false;
+  int64_t step = 0;
+  // normalisation (host copies; device copies in dev_norm)
+  float fmean[kSurIn], fistd[kSurIn], fmin[kSurFeat], fmax[kSurFeat];
+  float tmean[kSurOut], tistd[kSurOut];
+  float *dev_norm = nullptr;  // fmean[16], fistd[16], tmean[16], tistd[16]
+  double lam = 0.1;
+  // inference scratch
+  int64_t chunk_cap = 0;
+  float *Xraw = nullptr, *O = nullptr;
+  __nv_bfloat16 *Xbf = nullptr, *Ha = nullptr, *Hb = nullptr;
+  uint8_t *Tok = nullptr;
+  int64_t fb_cap = 0;
+  int32_t *fb_idx = nullptr;
+  unsigned int *fb_count = nullptr;
+};
+
+static void free_surrogate(Surrogate *s) {
+  if (!s) return;
+  cudaFree(s->param);
+  cudaFree(s->grad);
+  cudaFree(s->m);
+  cudaFree(s->v);
+  for (int l = 0; l < kSurLayers; ++l) {
+    cudaFree(s->W[l]);
+    cudaFree(s->WT[l]);
+  }
+  cudaFree(s->dev_norm);
+  cudaFree(s->Xraw);
+  cudaFree(s->O);
+  cudaFree(s->Xbf);
+  cudaFree(s->Ha);
+  cudaFree(s->Hb);
+  cudaFree(s->Tok);
+  cudaFree(s->fb_idx);
+  cudaFree(s->fb_count);
+  delete s;
+}
+
+void surrogate_destroy(void *p) { free_surrogate(static_cast<Surrogate *>(p)); }
+
+// splitmix64: seeded, platform-independent random numbers for init and shuffling
+struct Rng {
+  uint64_t s;
+  uint64_t next() {
+    uint64_t z = (s += 0x9e3779b97f4a7c15ull);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+  }
+  double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
+  double normal() {  // Box-Muller
+    const double u1 = uniform() + 1e-300, u2 = uniform();
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+  }
+};
+
+#define SCHK(call)                                  \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return e_;               \
+  } while (0)
+
+static cudaError_t alloc_params(Surrogate *s) {
+  int64_t o = 0;
+  for (int l = 0; l < kSurLayers; ++l) {
+    s->off_W[l] = o;
+    o += (int64_t)kSurN[l] * kSurK[l];
+    s->off_b[l] = o;
+    o += kSurN[l];
+  }
+  const size_t bytes = (size_t)kSurParams * sizeof(float);
+  SCHK(cudaMalloc(&s->param, bytes));
+  SCHK(cudaMalloc(&s->grad, bytes));
+  SCHK(cudaMalloc(&s->m, bytes));
+  SCHK(cudaMalloc(&s->v, bytes));
+  for (int l = 0; l < kSurLayers; ++l) {
+    SCHK(cudaMalloc(&s->W[l], (size_t)kSurN[l] * kSurK[l] * sizeof(__nv_bfloat16)));
+    SCHK(cudaMalloc(&s->WT[l], (size_t)kSurN[l] * kSurK[l] * sizeof(__nv_bfloat16)));
+  }
+  SCHK(cudaMalloc(&s->dev_norm, 4 * 16 * sizeof(float)));
+  SCHK(cudaMalloc(&s->fb_count, sizeof(unsigned int)));
+  return cudaSuccess;
+}
+
+// Upload host parameters, reset Adam, refresh the bf16 shadows (an Adam step with zero
+// learning rate and zero gradient writes them).
+static cudaError_t set_params(Surrogate *s, const float *h, cudaStream_t st) {
+  const size_t bytes = (size_t)kSurParams * sizeof(float);
+  SCHK(cudaMemcpyAsync(s->param, h, bytes, cudaMemcpyHostToDevice, st));
+  SCHK(cudaMemsetAsync(s->m, 0, bytes, st));
+  SCHK(cudaMemsetAsync(s->v, 0, bytes, st));
+  SCHK(cudaMemsetAsync(s->grad, 0, bytes, st));
+  for (int l = 0; l < kSurLayers; ++l)
+    SCHK(launch_adam((int64_t)kSurN[l] * kSurK[l], s->param + s->off_W[l], s->grad + s->off_W[l],
+                     s->m + s->off_W[l], s->v + s->off_W[l], 0.0f, 0.9f, 0.999f, 1e-8f, 1, s->W[l],
+                     s->WT[l], kSurN[l], kSurK[l], st));
+  s->step = 0;
+  return cudaSuccess;
+}
+
+static void init_params(Surrogate *s, uint64_t seed, std::vector<float> &h) {
+  h.assign((size_t)kSurParams, 0.0f);
+  Rng r{seed * 0x2545F4914F6CDD1Dull + 1};
+  const int fan_in[kSurLayers] = {kSurFeat, kSurHidden, kSurHidden, kSurHidden};
+  const int nout[kSurLayers] = {kSurHidden, kSurHidden, kSurHidden, NSP};
+  for (int l = 0; l < kSurLayers; ++l) {
+    const double sd = std::sqrt(2.0 / fan_in[l]);
+    for (int n = 0; n < kSurN[l]; ++n)
+      for (int k = 0; k < kSurK[l]; ++k) {
+        const bool live = n < nout[l] && k < fan_in[l];
+        h[(size_t)(s->off_W[l] + (int64_t)n * kSurK[l] + k)] = live ? (float)(sd * r.normal()) : 0.0f;
+      }
+  }
+}
+
+static cudaError_t upload_norm(Surrogate *s, cudaStream_t st) {
+  float h[64] = {0};
+  for (int c = 0; c < kSurIn; ++c) {
+    h[c] = s->fmean[c];
+    h[16 + c] = s->fistd[c];
+  }
+  for (int c = 0; c < kSurOut; ++c) {
+    h[32 + c] = s->tmean[c];
+    h[48 + c] = s->tistd[c];
+  }
+  SCHK(cudaMemcpyAsync(s->dev_norm, h, sizeof h, cudaMemcpyHostToDevice, st));
+  return cudaStreamSynchronize(st);
+}
+
+static float key_decode(int k) {
+  const int b = k >= 0 ? k : k ^ 0x7fffffff;
+  float f;
+  std::memcpy(&f, &b, sizeof f);
+  return f;
+}
+
+// One layer forward: Z (fp32, nullable) = H W^T + b; Hout (bf16) = GELU(Z) (or Z for the
+// last layer into Of fp32).
+static cudaError_t layer_forward(Surrogate *s, int l, int64_t M, const __nv_bfloat16 *H, float *Z,
+                                 __nv_bfloat16 *Hout, float *Of, cudaStream_t st) {
+  GemmArgs g{};
+  g.M = M;
+  g.N = kSurN[l];
+  g.K = kSurK[l];
+  g.A = H;
+  g.sam = kSurK[l];
+  g.sak = 1;
+  g.B = s->W[l];
+  g.sbn = kSurK[l];
+  g.sbk = 1;
+  g.alpha = 1.0f;
+  g.bias = s->param + s->off_b[l];
+  const bool last = l == kSurLayers - 1;
+  g.Cf = last ? Of : Z;
+  g.ldc = kSurN[l];
+  g.Cb = last ? nullptr : Hout;
+  g.ldcb = kSurN[l];
+  g.gelu = !last;
+  return launch_gemm(g, st);
+}
+
+// Training buffers for a batch of B rows.
+struct TrainBufs {
+  float *Xb = nullptr, *Tb = nullptr, *Y = nullptr, *loss = nullptr;
+  float *Z[3] = {}, *dH = nullptr;
+  __nv_bfloat16 *Xbf = nullptr, *H[3] = {}, *dY = nullptr, *dZ = nullptr;
+  void release() {
+    cudaFree(Xb); cudaFree(Tb); cudaFree(Y); cudaFree(loss); cudaFree(dH); cudaFree(Xbf);
+    cudaFree(dY); cudaFree(dZ);
+    for (int i = 0; i < 3; ++i) { cudaFree(Z[i]); cudaFree(H[i]); }
+  }
+  cudaError_t alloc(int64_t B) {
+    SCHK(cudaMalloc(&Xb, B * kSurIn * sizeof(float)));
+    SCHK(cudaMalloc(&Tb, B * kSurOut * sizeof(float)));
+    SCHK(cudaMalloc(&Y, B * kSurOut * sizeof(float)));
+    SCHK(cudaMalloc(&loss, sizeof(float)));
+    SCHK(cudaMalloc(&dH, B * kSurHidden * sizeof(float)));
+    SCHK(cudaMalloc(&Xbf, B * kSurIn * sizeof(__nv_bfloat16)));
+    SCHK(cudaMalloc(&dY, B * kSurOut * sizeof(__nv_bfloat16)));
+    SCHK(cudaMalloc(&dZ, B * kSurHidden * sizeof(__nv_bfloat16)));
+    for (int i = 0; i < 3; ++i) {
+      SCHK(cudaMalloc(&Z[i], B * kSurHidden * sizeof(float)));
+      SCHK(cudaMalloc(&H[i], B * kSurHidden * sizeof(__nv_bfloat16)));
+    }
+    return cudaSuccess;
+  }
+};
+
+// Forward with saved activations, MSE over the 9 outputs, backward into s->grad.
+// X: normalised features [B x 16] (fp32, also converted to bf16), T: normalised targets.
+static cudaError_t forward_backward(Surrogate *s, TrainBufs &b, int64_t B, cudaStream_t st) {
+  SCHK(launch_to_bf16(B * kSurIn, b.Xb, b.Xbf, st));
+  SCHK(layer_forward(s, 0, B, b.Xbf, b.Z[0], b.H[0], nullptr, st));
+  SCHK(layer_forward(s, 1, B, b.H[0], b.Z[1], b.H[1], nullptr, st));
+  SCHK(layer_forward(s, 2, B, b.H[1], b.Z[2], b.H[2], nullptr, st));
+  SCHK(layer_forward(s, 3, B, b.H[2], nullptr, nullptr, b.Y, st));
+  SCHK(launch_mse(B, NSP, kSurOut, b.Y, b.Tb, kSurOut, b.dY, kSurOut, b.loss, st));
+  // layer l: input Hin [B x K], output gradient G [B x N] (bf16)
+  const __nv_bfloat16 *Hin[kSurLayers] = {b.Xbf, b.H[0], b.H[1], b.H[2]};
+  const __nv_bfloat16 *G = b.dY;
+  for (int l = kSurLayers - 1; l >= 0; --l) {
+    const int N = kSurN[l], K = kSurK[l];
+    // dW[n, k] = sum_m G[m, n] Hin[m, k]
+    GemmArgs gw{};
+    gw.M = N; gw.N = K; gw.K = B;
+    gw.A = G; gw.sam = 1; gw.sak = N;
+    gw.B = Hin[l]; gw.sbn = 1; gw.sbk = K;
+    gw.alpha = 1.0f;
+    gw.Cf = s->grad + s->off_W[l]; gw.ldc = K;
+    SCHK(launch_gemm(gw, st));
+    SCHK(launch_bias_grad(B, N, G, N, s->grad + s->off_b[l], st));
+    if (l == 0) break;
+    // dHin[m, k] = sum_n G[m, n] W[n, k] (W^T stored [K x N])
+    GemmArgs gx{};
+    gx.M = B; gx.N = K; gx.K = N;
+    gx.A = G; gx.sam = N; gx.sak = 1;
+    gx.B = s->WT[l]; gx.sbn = N; gx.sbk = 1;
+    gx.alpha = 1.0f;
+    gx.Cf = b.dH; gx.ldc = K;
+    SCHK(launch_gemm(gx, st));
+    // G for layer l-1: dZ = dHin * GELU'(Z_{l-1})
+    SCHK(launch_gelu_backward(B, K, b.dH, K, b.Z[l - 1], K, b.dZ, K, st));
+    G = b.dZ;
+  }
+  return cudaSuccess;
+}
+
+static cudaError_t adam_all(Surrogate *s, float lr, cudaStream_t st) {
+  ++s->step;
+  for (int l = 0; l < kSurLayers; ++l) {
+    const int64_t nw = (int64_t)kSurN[l] * kSurK[l];
+    SCHK(launch_adam(nw, s->param + s->off_W[l], s->grad + s->off_W[l], s->m + s->off_W[l],
+                     s->v + s->off_W[l], lr, 0.9f, 0.999f, 1e-8f, (int)s->step, s->W[l], s->WT[l],
+                     kSurN[l], kSurK[l], st));
+    SCHK(launch_adam(kSurN[l], s->param + s->off_b[l], s->grad + s->off_b[l], s->m + s->off_b[l],
+                     s->v + s->off_b[l], lr, 0.9f, 0.999f, 1e-8f, (int)s->step, nullptr, nullptr,
+                     1, kSurN[l], st));
+  }
+  return cudaSuccess;
+}
+
+static SurrogateConsts make_consts(const Surrogate *s, const chem_surrogate_gate &g,
+                                   const MechTables &mt) {
+  SurrogateConsts c{};
+  for (int k = 0; k < NSP; ++k) {
+    c.tmean[k] = s->tmean[k];
+    c.tstd[k] = 1.0f / s->tistd[k];
+  }
+  for (int f = 0; f < kSurFeat; ++f) {
+    c.fmin[f] = s->fmin[f];
+    c.fmax[f] = s->fmax[f];
+  }
+  c.margin = g.ood_margin;
+  c.resid_max = g.resid_max;
+  c.neg_tol = g.neg_tol;
+  c.max_dT = g.max_dT;
+  c.lam = s->lam;
+  for (int el = 0; el < 3; ++el)
+    for (int k = 0; k < NSP; ++k) c.E[el][k] = mt.Emat[el][k];
+  return c;
+}
+
+}  // namespace chem
+
+namespace chem {
+
+static int sur_fail(chem_ctx *ctx, int code, const std::string &msg) {
+  chem_ctx_error(ctx) = msg;
+  return code;
+}
+
+static int sur_cuda(chem_ctx *ctx, cudaError_t e, const char *what) {
+  return sur_fail(ctx, e == cudaErrorMemoryAllocation ? CHEM_ERR_NOMEM : CHEM_ERR_CUDA,
+                  std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static Surrogate *ensure_surrogate(chem_ctx *ctx, cudaError_t *err) {
+  void *&slot = chem_ctx_sur(ctx);
+  *err = cudaSuccess;
+  if (!slot) {
+    Surrogate *s = new Surrogate;
+    *err = alloc_params(s);
+    if (*err != cudaSuccess) {
+      cudaGetLastError();
+      free_surrogate(s);
+      return nullptr;
+    }
+    slot = s;
+  }
+  return static_cast<Surrogate *>(slot);
+}
+
+static cudaError_t ensure_infer_buffers(Surrogate *s, int64_t chunk, int64_t n) {
+  if (chunk > s->chunk_cap) {
+    cudaFree(s->Xraw); cudaFree(s->O); cudaFree(s->Xbf); cudaFree(s->Ha); cudaFree(s->Hb); cudaFree(s->Tok);
+    s->Xraw = s->O = nullptr; s->Xbf = s->Ha = s->Hb = nullptr; s->Tok = nullptr;
+    s->chunk_cap = 0;
+    SCHK(cudaMalloc(&s->Xraw, chunk * kSurIn * sizeof(float)));
+    SCHK(cudaMalloc(&s->O, chunk * kSurOut * sizeof(float)));
+    SCHK(cudaMalloc(&s->Xbf, chunk * kSurIn * sizeof(__nv_bfloat16)));
+    SCHK(cudaMalloc(&s->Ha, chunk * kSurHidden * sizeof(__nv_bfloat16)));
+    SCHK(cudaMalloc(&s->Hb, chunk * kSurHidden * sizeof(__nv_bfloat16)));
+    SCHK(cudaMalloc(&s->Tok, chunk));
+    s->chunk_cap = chunk;
+  }
+  if (n > s->fb_cap) {
+    cudaFree(s->fb_idx);
+    s->fb_idx = nullptr;
+    s->fb_cap = 0;
+    SCHK(cudaMalloc(&s->fb_idx, n * sizeof(int32_t)));
+    s->fb_cap = n;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace chem
+
+using namespace chem;
+
+extern "C" {
+
+int64_t chem_surrogate_param_count(void) { return kSurParams; }
+
+int chem_surrogate_params(chem_ctx *ctx, float *h_out, const float *h_in, int64_t n) {
+  if (!ctx) return CHEM_ERR_INVALID;
+  if (n != kSurParams) return sur_fail(ctx, CHEM_ERR_INVALID, "parameter count mismatch");
+  cudaError_t e;
+  Surrogate *s = ensure_surrogate(ctx, &e);
+  if (!s) return sur_cuda(ctx, e, "allocating the surrogate");
+  if (h_in) {
+    e = set_params(s, h_in, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) return sur_cuda(ctx, e, "setting parameters");
+  }
+  if (h_out) {
+    e = cudaMemcpy(h_out, s->param, (size_t)kSurParams * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return sur_cuda(ctx, e, "reading parameters");
+  }
+  return CHEM_OK;
+}
+
+int chem_surrogate_grad(chem_ctx *ctx, const float *d_X, const float *d_T, int64_t B, float *d_Y,
+                        float *h_grad, float *h_loss, void *stream) {
+  if (!ctx) return CHEM_ERR_INVALID;
+  if (B <= 0 || !d_X || !d_T) return sur_fail(ctx, CHEM_ERR_INVALID, "B > 0, X and T required");
+  cudaError_t e;
+  Surrogate *s = ensure_surrogate(ctx, &e);
+  if (!s) return sur_cuda(ctx, e, "allocating the surrogate");
+  cudaStream_t st = (cudaStream_t)stream;
+  TrainBufs b;
+  e = b.alloc(B);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b.Xb, d_X, B * kSurIn * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b.Tb, d_T, B * kSurOut * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.loss, 0, sizeof(float), st);
+  if (e == cudaSuccess) e = forward_backward(s, b, B, st);
+  if (e == cudaSuccess && d_Y) e = cudaMemcpyAsync(d_Y, b.Y, B * kSurOut * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && h_grad)
+    e = cudaMemcpyAsync(h_grad, s->grad, (size_t)kSurParams * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && h_loss) e = cudaMemcpyAsync(h_loss, b.loss, sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  b.release();
+  return e == cudaSuccess ? CHEM_OK : sur_cuda(ctx, e, "surrogate forward/backward");
+}
+
+int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
+                         const chem_train_cfg *cfg_in, void *stream, float *h_epoch_loss) {
+  if (!ctx) return CHEM_ERR_INVALID;
+  chem_train_cfg cfg{};
+  if (cfg_in) cfg = *cfg_in;
+  if (cfg.epochs == 0) cfg.epochs = 20;
+  if (cfg.batch == 0) cfg.batch = 4096;
+  if (cfg.lr == 0.0f) cfg.lr = 1e-3f;
+  if (cfg.lr_final == 0.0f) cfg.lr_final = cfg.lr / 20.0f;
+  if (cfg.boxcox_lambda == 0.0f) cfg.boxcox_lambda = 0.1f;
+  if (cfg.epochs < 0 || cfg.batch < 1 || !(cfg.lr > 0.0f) || !(cfg.boxcox_lambda > 0.0f) || cfg.reserved0)
+    return sur_fail(ctx, CHEM_ERR_INVALID, "invalid training configuration");
+  if (!pairs || !pairs->d_rho || !pairs->d_e || !pairs->d_Y0 || !pairs->d_dt || !pairs->d_Y1)
+    return sur_fail(ctx, CHEM_ERR_INVALID, "pairs need rho, e, Y0, dt and Y1");
+  if (npairs < cfg.batch || npairs > INT32_MAX)
+    return sur_fail(ctx, CHEM_ERR_INVALID, "npairs must be at least one batch and below 2^31");
+  if (pairs->ldY0 < npairs || pairs->ldY1 < npairs)
+    return sur_fail(ctx, CHEM_ERR_INVALID, "ldY0 / ldY1 < npairs");
+  cudaError_t e;
+  Surrogate *s = ensure_surrogate(ctx, &e);
+  if (!s) return sur_cuda(ctx, e, "allocating the surrogate");
+  cudaStream_t st = (cudaStream_t)stream;
+  const MechTables &mt = chem_ctx_tables(ctx);
+  s->lam = cfg.boxcox_lambda;
+  s->ready = false;
+  std::vector<float> h;
+  init_params(s, cfg.seed, h);
+  e = set_params(s, h.data(), st);
+  if (e != cudaSuccess) return sur_cuda(ctx, e, "initialising parameters");
+  const int64_t n = npairs, B = cfg.batch;
+  float *X = nullptr, *Tg = nullptr;
+  double *sums = nullptr;
+  int *keys = nullptr;
+  int32_t *idx = nullptr;
+  TrainBufs b;
+  auto cleanup = [&]() {
+    cudaFree(X); cudaFree(Tg); cudaFree(sums); cudaFree(keys); cudaFree(idx);
+    b.release();
+  };
+  e = cudaMalloc(&X, n * kSurIn * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&Tg, n * kSurOut * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&sums, 4 * 32 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&keys, 4 * 32 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&idx, n * sizeof(int32_t));
+  if (e == cudaSuccess) e = b.alloc(B);
+  if (e != cudaSuccess) { cleanup(); return sur_cuda(ctx, e, "allocating training buffers"); }
+  // features and targets of every pair, then their statistics
+  e = launch_features(mt, n, pairs->d_rho, pairs->d_e, pairs->d_Y0, pairs->ldY0, pairs->d_T0,
+                      pairs->d_dt, 0.0, pairs->d_Y1, pairs->ldY1, s->lam, X, Tg, nullptr, nullptr, st);
+  int hkeys[4 * 32];
+  for (int i = 0; i < 32; ++i) {
+    hkeys[i] = INT_MAX; hkeys[32 + i] = INT_MIN; hkeys[64 + i] = INT_MAX; hkeys[96 + i] = INT_MIN;
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(sums, 0, 4 * 32 * sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(keys, hkeys, sizeof hkeys, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_colstats(n, kSurFeat, kSurIn, X, sums, sums + 32, keys, keys + 32, st);
+  if (e == cudaSuccess) e = launch_colstats(n, NSP, kSurOut, Tg, sums + 64, sums + 96, keys + 64, keys + 96, st);
+  double hs[4 * 32];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hs, sums, sizeof hs, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hkeys, keys, sizeof hkeys, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { cleanup(); return sur_cuda(ctx, e, "featurising the pairs"); }
+  for (int c = 0; c < kSurIn; ++c) {
+    if (c < kSurFeat) {
+      const double mean = hs[c] / n, var = std::fmax(hs[32 + c] / n - mean * mean, 0.0);
+      s->fmean[c] = (float)mean;
+      s->fistd[c] = (float)(1.0 / std::fmax(std::sqrt(var), 1e-6));
+      s->fmin[c] = key_decode(hkeys[c]);
+      s->fmax[c] = key_decode(hkeys[32 + c]);
+    } else {
+      s->fmean[c] = 0.0f;
+      s->fistd[c] = 0.0f;
+    }
+  }
+  for (int c = 0; c < kSurOut; ++c) {
+    if (c < NSP) {
+      const double mean = hs[64 + c] / n, var = std::fmax(hs[96 + c] / n - mean * mean, 0.0);
+      s->tmean[c] = (float)mean;
+      s->tistd[c] = (float)(1.0 / std::fmax(std::sqrt(var), 1e-6));
+    } else {
+      s->tmean[c] = 0.0f;
+      s->tistd[c] = 0.0f;
+    }
+  }
+  e = upload_norm(s, st);
+  if (e == cudaSuccess) e = launch_normalize(n, kSurFeat, kSurIn, X, s->dev_norm, s->dev_norm + 16, nullptr, st);
+  if (e == cudaSuccess) e = launch_normalize(n, NSP, kSurOut, Tg, s->dev_norm + 32, s->dev_norm + 48, nullptr, st);
+  if (e != cudaSuccess) { cleanup(); return sur_cuda(ctx, e, "normalising"); }
+  // epochs of shuffled batches
+  const int64_t nb = n / B;
+  const int64_t total = nb * cfg.epochs;
+  std::vector<int32_t> perm((size_t)n);
+  Rng r{cfg.seed ^ 0x5bd1e995ull};
+  int64_t it = 0;
+  for (int ep = 0; ep < cfg.epochs && e == cudaSuccess; ++ep) {
+    for (int64_t i = 0; i < n; ++i) perm[(size_t)i] = (int32_t)i;
+    for (int64_t i = n - 1; i > 0; --i) std::swap(perm[(size_t)i], perm[(size_t)(r.next() % (uint64_t)(i + 1))]);
+    e = cudaMemcpy(idx, perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.loss, 0, sizeof(float), st);
+    for (int64_t bi = 0; bi < nb && e == cudaSuccess; ++bi, ++it) {
+      e = launch_gather_rows(B, kSurIn, idx + bi * B, X, kSurIn, b.Xb, kSurIn, st);
+      if (e == cudaSuccess) e = launch_gather_rows(B, kSurOut, idx + bi * B, Tg, kSurOut, b.Tb, kSurOut, st);
+      if (e == cudaSuccess) e = forward_backward(s, b, B, st);
+      const double frac = total > 1 ? (double)it / (double)(total - 1) : 1.0;
+      const float lr = (float)(cfg.lr_final + 0.5 * (cfg.lr - cfg.lr_final) * (1.0 + std::cos(3.141592653589793 * frac)));
+      if (e == cudaSuccess) e = adam_all(s, lr, st);
+    }
+    float lsum = 0.0f;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&lsum, b.loss, sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && h_epoch_loss) h_epoch_loss[ep] = lsum / (float)nb;
+  }
+  cleanup();
+  if (e != cudaSuccess) return sur_cuda(ctx, e, "training");
+  s->ready = true;
+  return CHEM_OK;
+}
+
+int chem_surrogate_infer(chem_ctx *ctx, const chem_state *state, int64_t n, double dt, double rtol,
+                         double atol, const chem_surrogate_gate *gate_in, void *stream,
+                         uint8_t *d_mask, chem_stats *d_stats) {
+  if (!ctx) return CHEM_ERR_INVALID;
+  Surrogate *s = static_cast<Surrogate *>(chem_ctx_sur(ctx));
+  if (!s || !s->ready) return sur_fail(ctx, CHEM_ERR_STATE, "no trained or loaded surrogate");
+  if (!state || n < 0) return sur_fail(ctx, CHEM_ERR_INVALID, "state is NULL or ncells < 0");
+  if (!(dt > 0.0) || !std::isfinite(dt) || !(rtol > 0.0) || !(atol >= 0.0))
+    return sur_fail(ctx, CHEM_ERR_INVALID, "dt, rtol must be > 0 and atol >= 0");
+  if (n > INT32_MAX) return sur_fail(ctx, CHEM_ERR_INVALID, "at most 2^31-1 cells per call");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (d_stats) e = cudaMemsetAsync(d_stats, 0, sizeof(chem_stats), st);
+  if (e != cudaSuccess) return sur_cuda(ctx, e, "clearing stats");
+  if (n == 0) return CHEM_OK;
+  if (!state->d_rho || !state->d_e || !state->d_Y || !state->d_T || state->ldY < n)
+    return sur_fail(ctx, CHEM_ERR_INVALID, "rho, e, Y, T required and ldY >= ncells");
+  chem_surrogate_gate g{};
+  if (gate_in) g = *gate_in;
+  if (g.ood_margin == 0.0f) g.ood_margin = 0.05f;
+  if (g.resid_max == 0.0f) g.resid_max = 0.02f;
+  if (g.neg_tol == 0.0f) g.neg_tol = 1e-6f;
+  if (g.max_dT == 0.0f) g.max_dT = 25.0f;
+  const int64_t chunk = n < 524288 ? n : 524288;
+  e = ensure_infer_buffers(s, chunk, n);
+  if (e != cudaSuccess) return sur_cuda(ctx, e, "allocating inference buffers");
+  const MechTables &mt = chem_ctx_tables(ctx);
+  const SurrogateConsts sc = make_consts(s, g, mt);
+  e = cudaMemsetAsync(s->fb_count, 0, sizeof(unsigned int), st);
+  for (int64_t base = 0; base < n && e == cudaSuccess; base += chunk) {
+    const int64_t m = (n - base) < chunk ? (n - base) : chunk;
+    e = launch_features(mt, m, state->d_rho + base, state->d_e + base, state->d_Y + base, state->ldY,
+                        state->d_T + base, nullptr, dt, nullptr, 0, s->lam, s->Xraw, nullptr, nullptr,
+                        s->Tok, st);
+    if (e == cudaSuccess) e = launch_norm_bf16(m, kSurFeat, kSurIn, s->Xraw, s->dev_norm, s->dev_norm + 16, s->Xbf, st);
+    if (e == cudaSuccess) e = layer_forward(s, 0, m, s->Xbf, nullptr, s->Ha, nullptr, st);
+    if (e == cudaSuccess) e = layer_forward(s, 1, m, s->Ha, nullptr, s->Hb, nullptr, st);
+    if (e == cudaSuccess) e = layer_forward(s, 2, m, s->Hb, nullptr, s->Ha, nullptr, st);
+    if (e == cudaSuccess) e = layer_forward(s, 3, m, s->Ha, nullptr, nullptr, s->O, st);
+    if (e == cudaSuccess)
+      e = launch_surrogate_finish(mt, sc, m, s->O, s->Xraw, s->Tok, state->d_rho + base, state->d_e + base,
+                                  state->d_Y + base, state->ldY, state->d_T + base,
+                                  state->d_status ? state->d_status + base : nullptr,
+                                  state->d_nsteps ? state->d_nsteps + base : nullptr,
+                                  d_mask ? d_mask + base : nullptr, s->fb_idx, s->fb_count, base, st);
+  }
+  if (e == cudaSuccess) {
+    CellArgs a{state->d_rho, state->d_e, state->d_Y, state->ldY, state->d_T, nullptr,
+               state->d_status, state->d_nsteps, n, d_stats};
+    StepParams p{dt, rtol, atol, chem_ctx_max_steps(ctx)};
+    e = launch_lsrk_indexed(chem_ctx_variant(ctx), mt, a, p, s->fb_idx, s->fb_count, n, st);
+  }
+  if (e == cudaSuccess && d_stats) e = launch_surrogate_stats(d_stats, n, s->fb_count, st);
+  return e == cudaSuccess ? CHEM_OK : sur_cuda(ctx, e, "surrogate inference");
+}
+
+static const char kSurMagic[8] = {'C', 'H', 'E', 'M', 'S', 'U', 'R', '1'};
+
+int chem_surrogate_save(chem_ctx *ctx, const char *path) {
+  if (!ctx || !path) return CHEM_ERR_INVALID;
+  Surrogate *s = static_cast<Surrogate *>(chem_ctx_sur(ctx));
+  if (!s || !s->ready) return sur_fail(ctx, CHEM_ERR_STATE, "no trained or loaded surrogate");
+  std::vector<float> h((size_t)kSurParams);
+  cudaError_t e = cudaMemcpy(h.data(), s->param, h.size() * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return sur_cuda(ctx, e, "reading parameters");
+  FILE *f = std::fopen(path, "wb");
+  if (!f) return sur_fail(ctx, CHEM_ERR_INVALID, std::string("cannot open ") + path);
+  const int64_t np = kSurParams;
+  bool ok = std::fwrite(kSurMagic, 1, 8, f) == 8 && std::fwrite(&np, sizeof np, 1, f) == 1 &&
+            std::fwrite(&s->lam, sizeof s->lam, 1, f) == 1 &&
+            std::fwrite(s->fmean, sizeof s->fmean, 1, f) == 1 && std::fwrite(s->fistd, sizeof s->fistd, 1, f) == 1 &&
+            std::fwrite(s->fmin, sizeof s->fmin, 1, f) == 1 && std::fwrite(s->fmax, sizeof s->fmax, 1, f) == 1 &&
+            std::fwrite(s->tmean, sizeof s->tmean, 1, f) == 1 && std::fwrite(s->tistd, sizeof s->tistd, 1, f) == 1 &&
+            std::fwrite(h.data(), sizeof(float), h.size(), f) == h.size();
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? CHEM_OK : sur_fail(ctx, CHEM_ERR_INVALID, std::string("write failed: ") + path);
+}
+
+int chem_surrogate_load(chem_ctx *ctx, const char *path) {
+  if (!ctx || !path) return CHEM_ERR_INVALID;
+  FILE *f = std::fopen(path, "rb");
+  if (!f) return sur_fail(ctx, CHEM_ERR_INVALID, std::string("cannot open ") + path);
+  char magic[8];
+  int64_t np = 0;
+  double lam = 0.0;
+  float fmean[kSurIn], fistd[kSurIn], fmin[kSurFeat], fmax[kSurFeat], tmean[kSurOut], tistd[kSurOut];
+  std::vector<float> h((size_t)kSurParams);
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kSurMagic, 8) == 0 &&
+            std::fread(&np, sizeof np, 1, f) == 1 && np == kSurParams &&
+            std::fread(&lam, sizeof lam, 1, f) == 1 && std::fread(fmean, sizeof fmean, 1, f) == 1 &&
+            std::fread(fistd, sizeof fistd, 1, f) == 1 && std::fread(fmin, sizeof fmin, 1, f) == 1 &&
+            std::fread(fmax, sizeof fmax, 1, f) == 1 && std::fread(tmean, sizeof tmean, 1, f) == 1 &&
+            std::fread(tistd, sizeof tistd, 1, f) == 1 &&
+            std::fread(h.data(), sizeof(float), h.size(), f) == h.size();
+  std::fclose(f);
+  if (!ok) return sur_fail(ctx, CHEM_ERR_INVALID, std::string("not a surrogate file: ") + path);
+  cudaError_t e;
+  Surrogate *s = ensure_surrogate(ctx, &e);
+  if (!s) return sur_cuda(ctx, e, "allocating the surrogate");
+  s->lam = lam;
+  std::memcpy(s->fmean, fmean, sizeof fmean);
+  std::memcpy(s->fistd, fistd, sizeof fistd);
+  std::memcpy(s->fmin, fmin, sizeof fmin);
+  std::memcpy(s->fmax, fmax, sizeof fmax);
+  std::memcpy(s->tmean, tmean, sizeof tmean);
+  std::memcpy(s->tistd, tistd, sizeof tistd);
+  e = set_params(s, h.data(), 0);
+  if (e == cudaSuccess) e = upload_norm(s, 0);
+  if (e != cudaSuccess) return sur_cuda(ctx, e, "loading the surrogate");
+  s->ready = true;
+  return CHEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,65 @@
+// surrogate.cuh -- shapes and constants of the learned surrogate.
+//
+// Network: 12 -> 256 -> 256 -> 256 -> 9, GELU between layers, BF16 weights and
+// activations with FP32 accumulation and FP32 master weights.  Input width is padded to
+// 16 and output width to 16 (zero columns) so every GEMM tile is a whole number of
+// 16-wide MMA fragments.  Parameters are stored per layer as W [N x K] (row-major,
+// output unit n, input k contiguous) and b [N]; the flat layout concatenates
+// W0, b0, W1, b1, W2, b2, W3, b3.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.cuh"
+
+namespace chem {
+
+constexpr int kSurIn = 16;       // 12 features, padded
+constexpr int kSurFeat = 12;
+constexpr int kSurOut = 16;      // 9 outputs, padded
+constexpr int kSurHidden = 256;
+constexpr int kSurLayers = 4;
+constexpr int kSurN[kSurLayers] = {kSurHidden, kSurHidden, kSurHidden, kSurOut};
+constexpr int kSurK[kSurLayers] = {kSurIn, kSurHidden, kSurHidden, kSurHidden};
+constexpr int64_t kSurParams = (int64_t)kSurHidden * kSurIn + kSurHidden +
+                               2 * ((int64_t)kSurHidden * kSurHidden + kSurHidden) +
+                               (int64_t)kSurOut * kSurHidden + kSurOut;
+
+// Everything the inference epilogue needs besides the mechanism (passed by value).
+struct SurrogateConsts {
+  float tmean[NSP], tstd[NSP];          // target normalisation
+  float fmin[kSurFeat], fmax[kSurFeat]; // training range of the raw features
+  float margin;                         // OOD margin, fraction of the range
+  float resid_max;                      // max relative element residual before projection
+  float neg_tol;                        // most negative mass fraction allowed after projection
+  float max_dT;                         // largest accepted |T' - T0| (K)
+  double lam;                           // Box-Cox lambda
+  double E[3][NSP];                     // element mass fraction per unit species mass fraction
+};
+
+cudaError_t launch_features(const MechTables &mt, int64_t n, const double *rho, const double *e,
+                            const double *Y0, int64_t ld0, const double *T0, const double *dt_cell,
+                            double dt, const double *Y1, int64_t ld1, double lam, float *X, float *Tg,
+                            double *Tout, uint8_t *ok, cudaStream_t s);
+cudaError_t launch_colstats(int64_t n, int ncol, int ld, const float *A, double *sum, double *sumsq,
+                            int *mnkey, int *mxkey, cudaStream_t s);
+cudaError_t launch_normalize(int64_t n, int ncol, int ld, float *A, const float *mean,
+                             const float *inv_std, __nv_bfloat16 *Abf, cudaStream_t s);
+cudaError_t launch_surrogate_finish(const MechTables &mt, const SurrogateConsts &sc, int64_t n,
+                                    const float *O, const float *Xraw, const uint8_t *Tok,
+                                    const double *rho, const double *e, double *Y, int64_t ld,
+                                    double *T, int32_t *status, int32_t *nsteps, uint8_t *mask,
+                                    int32_t *fb_idx, unsigned int *fb_count, int64_t base,
+                                    cudaStream_t s);
+cudaError_t launch_norm_bf16(int64_t n, int ncol, int ld, const float *src, const float *mean,
+                             const float *inv_std, __nv_bfloat16 *dst, cudaStream_t s);
+cudaError_t launch_surrogate_stats(chem_stats *st, int64_t n, const unsigned int *fb_count,
+                                   cudaStream_t s);
+cudaError_t launch_lsrk_indexed(int variant, const MechTables &mt, const CellArgs &a,
+                                const StepParams &p, const int32_t *idx, const unsigned int *count,
+                                int64_t max_count, cudaStream_t s);
+
+}  // namespace chem

@@ -1,0 +1,361 @@
+// surrogate_kernels.cu -- device kernels of the learned surrogate around the MLP:
+// featurisation, column statistics, the inference epilogue (inverse transform,
+// element-conservation projection, temperature solve, gate, fallback compaction) and
+// the index-driven fallback integration.
+//
+// Features of a cell (12, padded to 16): T, ln p, log10 dt and the Box-Cox transforms
+// BC(Y_k) = (max(Y_k, 1e-30)^lam - 1) / lam of the 9 mass fractions; targets (9, padded
+// to 16): BC(Y_k(t + dt)) - BC(Y_k(t)).  Both are z-scored with training statistics.
+// The temperature is always solved from (e, Y) in fp64, so energy is conserved exactly
+// by construction; the projection restores the element (H, O, N) mass fractions, hence
+// sum Y too, in fp64.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "cell.cuh"
+#include "internal.cuh"
+#include "surrogate.cuh"
+
+namespace chem {
+
+__device__ __forceinline__ double boxcox_d(double y, double lam) {
+  return (pow(fmax(y, 1e-30), lam) - 1.0) / lam;
+}
+
+__device__ __forceinline__ double boxcox_inv_d(double z, double lam) {
+  return pow(fmax(1.0 + lam * z, 0.0), 1.0 / lam);
+}
+
+// Raw (un-normalised) features and, when Y1 is given, targets of n cells.
+// X[i, 0:12] = T, ln p, log10 dt, BC(Y0); Tg[i, 0:9] = BC(Y1) - BC(Y0).  Padding zero.
+// Tout (nullable) receives the solved temperature; ok (nullable) 1 where T solved.
+__global__ void k_features(const __grid_constant__ MechTables mt, int64_t n, const double *rho,
+                           const double *e, const double *Y0, int64_t ld0, const double *Tg0,
+                           const double *dt_cell, double dt_scalar, const double *Y1, int64_t ld1,
+                           double lam, float *X, float *Tg, double *Tout, uint8_t *ok) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double yw[NSP], y[NSP];
+  double inv_w = 0.0;
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) {
+    y[k] = Y0[k * ld0 + i];
+    yw[k] = y[k] * mt.invW[k];
+    inv_w += yw[k];
+  }
+  double T = Tg0 ? Tg0[i] : CUDART_NAN;
+  const bool good = isfinite(rho[i]) && rho[i] > 0.0 && isfinite(e[i]) && solve_T(mt, yw, e[i] / R_U, T);
+  if (!good) T = 1500.0;
+  const double p = rho[i] * R_U * T * inv_w;
+  const double dt = dt_cell ? dt_cell[i] : dt_scalar;
+  float *x = X + i * kSurIn;
+  x[0] = (float)T;
+  x[1] = (float)log(fmax(p, 1e-30));
+  x[2] = (float)log10(dt);
+  double bc0[NSP];
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) {
+    bc0[k] = boxcox_d(y[k], lam);
+    x[3 + k] = (float)bc0[k];
+  }
+#pragma unroll
+  for (int c = 12; c < kSurIn; ++c) x[c] = 0.0f;
+  if (Y1) {
+    float *t = Tg + i * kSurOut;
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) t[k] = (float)(boxcox_d(Y1[k * ld1 + i], lam) - bc0[k]);
+#pragma unroll
+    for (int c = NSP; c < kSurOut; ++c) t[c] = 0.0f;
+  }
+  if (Tout) Tout[i] = T;
+  if (ok) ok[i] = good;
+}
+
+// Column sums, sums of squares, minima and maxima of the first ncol columns of a
+// row-major [n x ld] float matrix (double sums; minima and maxima as order-preserving
+// integer keys of the float bits, which the host initialises to INT_MAX / INT_MIN and
+// decodes with float_key_decode).
+__device__ __forceinline__ int float_key(float f) {
+  const int b = __float_as_int(f);
+  return b >= 0 ? b : b ^ 0x7fffffff;
+}
+
+__global__ void k_colstats(int64_t n, int ncol, int ld, const float *__restrict__ A, double *sum,
+                           double *sumsq, int *mnkey, int *mxkey) {
+  __shared__ double s1[32][9], s2[32][9];
+  __shared__ float smin[32][9], smax[32][9];
+  const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;  // blockDim 256: 8 row groups
+  double a = 0.0, b = 0.0;
+  float lo = 3.0e38f, hi = -3.0e38f;
+  if (lane < ncol) {
+    for (int64_t i = (int64_t)blockIdx.x * 8 + row; i < n; i += (int64_t)gridDim.x * 8) {
+      const float v = A[i * ld + lane];
+      a += v;
+      b += (double)v * v;
+      lo = fminf(lo, v);
+      hi = fmaxf(hi, v);
+    }
+  }
+  s1[lane][row] = a;
+  s2[lane][row] = b;
+  smin[lane][row] = lo;
+  smax[lane][row] = hi;
+  __syncthreads();
+  if (threadIdx.x < ncol) {
+    double ta = 0.0, tb = 0.0;
+    float tl = 3.0e38f, th = -3.0e38f;
+    for (int r = 0; r < 8; ++r) {
+      ta += s1[threadIdx.x][r];
+      tb += s2[threadIdx.x][r];
+      tl = fminf(tl, smin[threadIdx.x][r]);
+      th = fmaxf(th, smax[threadIdx.x][r]);
+    }
+    atomicAdd(&sum[threadIdx.x], ta);
+    atomicAdd(&sumsq[threadIdx.x], tb);
+    atomicMin(&mnkey[threadIdx.x], float_key(tl));
+    atomicMax(&mxkey[threadIdx.x], float_key(th));
+  }
+}
+
+// In place: A[i, c] = (A[i, c] - mean[c]) * inv_std[c] for c < ncol, and a bf16 copy.
+__global__ void k_normalize(int64_t n, int ncol, int ld, float *A, const float *mean,
+                            const float *inv_std, __nv_bfloat16 *Abf) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ld) return;
+  const int c = (int)(t % ld);
+  float v = A[t];
+  if (c < ncol) v = (v - mean[c]) * inv_std[c];
+  else v = 0.0f;
+  A[t] = v;
+  if (Abf) Abf[t] = __float2bfloat16(v);
+}
+
+// The inference epilogue, one thread per cell.  Takes the network output O [n x 16]
+// (z-scored BC increments), the raw features X (un-normalised: T, ln p, log10 dt,
+// BC(Y0)) and the state; writes accepted cells (Y'', T'', status OK, nsteps 0) and
+// appends rejected ones to the fallback list.
+__global__ void k_surrogate_finish(const __grid_constant__ MechTables mt, SurrogateConsts sc,
+                                   int64_t n, const float *__restrict__ O,
+                                   const float *__restrict__ Xraw, const uint8_t *__restrict__ Tok,
+                                   const double *__restrict__ rho, const double *__restrict__ e,
+                                   double *Y, int64_t ld, double *T, int32_t *status,
+                                   int32_t *nsteps, uint8_t *mask, int32_t *fb_idx,
+                                   unsigned int *fb_count, int64_t base) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float *x = Xraw + i * kSurIn;
+  const float *o = O + i * kSurOut;
+  bool accept = Tok[i] != 0;
+  // out-of-distribution: every feature within the training box widened by the margin
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    const float w = sc.margin * (sc.fmax[c] - sc.fmin[c]);
+    accept &= x[c] >= sc.fmin[c] - w && x[c] <= sc.fmax[c] + w;
+  }
+  double y0[NSP], y1[NSP];
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) {
+    y0[k] = Y[k * ld + i];
+    const double d = (double)o[k] * sc.tstd[k] + sc.tmean[k];
+    y1[k] = boxcox_inv_d((double)x[3 + k] + d, sc.lam);
+  }
+  // element mass fractions before projection and the residual
+  double z0[3] = {0.0, 0.0, 0.0}, r[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int el = 0; el < 3; ++el)
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+      z0[el] += sc.E[el][k] * y0[k];
+      r[el] += sc.E[el][k] * (y1[k] - y0[k]);
+    }
+  double rn = 0.0, zn = 0.0;
+#pragma unroll
+  for (int el = 0; el < 3; ++el) {
+    rn += r[el] * r[el];
+    zn += z0[el] * z0[el];
+  }
+  accept &= rn <= (double)sc.resid_max * sc.resid_max * zn;
+  // weighted least-squares projection onto E Y = E Y0: Y'' = Y' - W E^T (E W E^T)^-1 r
+  double w[NSP], M[3][3];
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) w[k] = fmax(y1[k], 1e-12);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < NSP; ++k) s += sc.E[a][k] * w[k] * sc.E[b][k];
+      M[a][b] = s;
+    }
+  // 3x3 solve by Cramer's rule (M is symmetric positive definite for the H, O, N rows)
+  const double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                     M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                     M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+  double lamv[3] = {0.0, 0.0, 0.0};
+  if (det != 0.0 && isfinite(det)) {
+    const double id = 1.0 / det;
+    lamv[0] = (r[0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (r[1] * M[2][2] - M[1][2] * r[2]) +
+               M[0][2] * (r[1] * M[2][1] - M[1][1] * r[2])) * id;
+    lamv[1] = (M[0][0] * (r[1] * M[2][2] - M[1][2] * r[2]) - r[0] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+               M[0][2] * (M[1][0] * r[2] - r[1] * M[2][0])) * id;
+    lamv[2] = (M[0][0] * (M[1][1] * r[2] - r[1] * M[2][1]) - M[0][1] * (M[1][0] * r[2] - r[1] * M[2][0]) +
+               r[0] * (M[1][0] * M[2][1] - M[1][1] * M[2][0])) * id;
+  } else {
+    accept = false;
+  }
+  double ymin = 1.0;
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) {
+    double corr = 0.0;
+#pragma unroll
+    for (int el = 0; el < 3; ++el) corr += sc.E[el][k] * lamv[el];
+    y1[k] -= w[k] * corr;
+    ymin = fmin(ymin, y1[k]);
+  }
+  accept &= ymin >= -(double)sc.neg_tol;
+  // temperature of the projected state (fp64 Newton from the input temperature)
+  double yw[NSP];
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) yw[k] = y1[k] * mt.invW[k];
+  double T1 = (double)x[0];
+  const bool tok = solve_T(mt, yw, e[i] / R_U, T1);
+  accept &= tok && fabs(T1 - (double)x[0]) <= (double)sc.max_dT;
+  if (accept) {
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) Y[k * ld + i] = y1[k];
+    T[i] = T1;
+    if (status) status[i] = CHEM_CELL_OK;
+    if (nsteps) nsteps[i] = 0;
+    if (mask) mask[i] = 0;
+  } else {
+    if (mask) mask[i] = 1;
+    const unsigned slot = atomicAdd(fb_count, 1u);
+    fb_idx[slot] = (int32_t)(base + i);
+  }
+}
+
+// Integrate the cells listed in idx[0 .. *count) in place (the surrogate's fallback);
+// threads past the count return at once, so no host synchronisation sizes the launch.
+// The per-cell arithmetic is cell.cuh's; status reports CHEM_CELL_SURROGATE for a
+// successful fallback (the cell was integrated instead), else the integrator's code.
+template <int V>
+__global__ void __launch_bounds__(128) k_lsrk_indexed(const __grid_constant__ MechTables mt,
+                                                      const CellArgs a, const StepParams p,
+                                                      const int32_t *__restrict__ idx,
+                                                      const unsigned int *count) {
+  load_math_tables();
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = t < (int64_t)*count;
+  CellState c;
+  c.nacc = c.nrej = c.nrhs = 0;
+  c.status = CHEM_CELL_OK;
+  int64_t i = -1;
+  if (live) {
+    i = idx[t];
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) c.X[k] = a.Y[k * a.ld + i];
+    c.T = a.T[i];
+    c.h = CUDART_NAN;
+    cell_begin(c, a.rho[i], a.e[i], p.dt);
+    while (!c.done) cell_attempt<V>(mt, c, p);
+    cell_finish(mt, c);
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) a.Y[k * a.ld + i] = c.X[k];
+    a.T[i] = c.T;
+    if (a.status) a.status[i] = c.status == CHEM_CELL_OK ? CHEM_CELL_SURROGATE : c.status;
+    if (a.nsteps) a.nsteps[i] = c.nacc + c.nrej;
+  }
+  if (a.stats) {
+    int hist[6];
+#pragma unroll
+    for (int s = 0; s < 6; ++s) hist[s] = live && (c.status == CHEM_CELL_OK ? s == CHEM_CELL_SURROGATE : c.status == s);
+    accumulate_stats(a.stats, live ? 1 : 0, c.nacc, c.nrej, c.nrhs, c.nacc + c.nrej, hist);
+  }
+}
+
+// dst (bf16) = (src - mean) * inv_std for the first ncol columns, zero elsewhere; src kept.
+__global__ void k_norm_bf16(int64_t n, int ncol, int ld, const float *__restrict__ src,
+                            const float *__restrict__ mean, const float *__restrict__ inv_std,
+                            __nv_bfloat16 *__restrict__ dst) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ld) return;
+  const int c = (int)(t % ld);
+  dst[t] = __float2bfloat16(c < ncol ? (src[t] - mean[c]) * inv_std[c] : 0.0f);
+}
+
+// Surrogate-call totals, launched after the fallback kernel on the same stream: every
+// cell counted once (cells = n overrides the fallback kernel's count of its own cells),
+// accepted cells as CHEM_CELL_OK (the fallback kernel counted the rejected ones by status).
+__global__ void k_surrogate_stats(chem_stats *st, int64_t n, const unsigned int *fb_count) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    st->cells = n;
+    st->status_count[CHEM_CELL_OK] += n - (int64_t)*fb_count;
+  }
+}
+
+static unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+cudaError_t launch_norm_bf16(int64_t n, int ncol, int ld, const float *src, const float *mean,
+                             const float *inv_std, __nv_bfloat16 *dst, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_norm_bf16<<<nblk(n * ld, 256), 256, 0, s>>>(n, ncol, ld, src, mean, inv_std, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_surrogate_stats(chem_stats *st, int64_t n, const unsigned int *fb_count,
+                                   cudaStream_t s) {
+  k_surrogate_stats<<<1, 32, 0, s>>>(st, n, fb_count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_features(const MechTables &mt, int64_t n, const double *rho, const double *e,
+                            const double *Y0, int64_t ld0, const double *T0, const double *dt_cell,
+                            double dt, const double *Y1, int64_t ld1, double lam, float *X, float *Tg,
+                            double *Tout, uint8_t *ok, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_features<<<nblk(n, 128), 128, 0, s>>>(mt, n, rho, e, Y0, ld0, T0, dt_cell, dt, Y1, ld1, lam, X, Tg,
+                                          Tout, ok);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colstats(int64_t n, int ncol, int ld, const float *A, double *sum, double *sumsq,
+                            int *mnkey, int *mxkey, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t want = (n + 7) / 8;
+  const unsigned grid = (unsigned)(want < 1024 ? want : 1024);
+  k_colstats<<<grid, 256, 0, s>>>(n, ncol, ld, A, sum, sumsq, mnkey, mxkey);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normalize(int64_t n, int ncol, int ld, float *A, const float *mean,
+                             const float *inv_std, __nv_bfloat16 *Abf, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_normalize<<<nblk(n * ld, 256), 256, 0, s>>>(n, ncol, ld, A, mean, inv_std, Abf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_surrogate_finish(const MechTables &mt, const SurrogateConsts &sc, int64_t n,
+                                    const float *O, const float *Xraw, const uint8_t *Tok,
+                                    const double *rho, const double *e, double *Y, int64_t ld,
+                                    double *T, int32_t *status, int32_t *nsteps, uint8_t *mask,
+                                    int32_t *fb_idx, unsigned int *fb_count, int64_t base,
+                                    cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_surrogate_finish<<<nblk(n, 128), 128, 0, s>>>(mt, sc, n, O, Xraw, Tok, rho, e, Y, ld, T, status,
+                                                  nsteps, mask, fb_idx, fb_count, base);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lsrk_indexed(int variant, const MechTables &mt, const CellArgs &a,
+                                const StepParams &p, const int32_t *idx, const unsigned int *count,
+                                int64_t max_count, cudaStream_t s) {
+  if (max_count <= 0) return cudaSuccess;
+  if (variant == CHEM_VARIANT_MIXED)
+    k_lsrk_indexed<CHEM_VARIANT_MIXED><<<nblk(max_count, 128), 128, 0, s>>>(mt, a, p, idx, count);
+  else
+    k_lsrk_indexed<CHEM_VARIANT_FP64><<<nblk(max_count, 128), 128, 0, s>>>(mt, a, p, idx, count);
+  return cudaGetLastError();
+}
+
+}  // namespace chem

@@ -60,17 +60,21 @@ int main(void) {
          offsetof(chem_state, d_nsteps), offsetof(chem_stats, status_count));
   printf("%zu %zu %zu %zu\n", sizeof(chem_batch), sizeof(chem_batch_options),
          offsetof(chem_batch, d_box_nsub), offsetof(chem_batch_options, d_cost_hint));
+  printf("%zu %zu %zu %zu\n", sizeof(chem_pairs), sizeof(chem_train_cfg), sizeof(chem_surrogate_gate),
+         offsetof(chem_train_cfg, seed));
   return 0;
 }''')
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)
-    a, b, c = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:3]
+    a, b, c, d = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:4]
     assert [int(x) for x in a.split()] == [C.sizeof(chem.Mechanism), C.sizeof(chem.Options),
                                           C.sizeof(chem.State), C.sizeof(chem.Stats)]
     assert [int(x) for x in b.split()] == [chem.Mechanism.eff.offset, chem.Mechanism.reversible.offset,
                                           chem.State.d_nsteps.offset, chem.Stats.status_count.offset]
     assert [int(x) for x in c.split()] == [C.sizeof(chem.Batch), C.sizeof(chem.BatchOptions),
                                           chem.Batch.d_box_nsub.offset, chem.BatchOptions.d_cost_hint.offset]
+    assert [int(x) for x in d.split()] == [C.sizeof(chem.Pairs), C.sizeof(chem.TrainCfg), C.sizeof(chem.Gate),
+                                          chem.TrainCfg.seed.offset]
 
 
 def _setup_rc(lib, mech, variant=0):
