@@ -297,7 +297,11 @@ typedef struct {
   float ood_margin;  /* [0.05] accepted feature range: training range widened by this fraction */
   float resid_max;   /* [0.02] largest relative element-mass residual before projection */
   float neg_tol;     /* [1e-6] most negative mass fraction allowed after projection */
-  float max_dT;      /* [25] largest accepted |T(t + dt) - T(t)|, K */
+  float max_dT;      /* [200] largest accepted |T(t + dt) - T(t)|, K */
+  float judge_tol;   /* [5e-4] largest accepted error estimate relative to T (the trapezoid
+                        judge of chem_surrogate_infer); negative: no judge */
+  float judge_rate;  /* [1] largest dt * max_k |dY_k/dt| / (|Y_k| + 1e-6) at either end of
+                        the step for the judge to accept; negative: no bound */
 } chem_surrogate_gate;
 
 /* Number of float parameters of the network (flat layout W0 [256x16], b0 [256], W1
@@ -319,7 +323,12 @@ int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
 /*
  * Advance the state over dt with the surrogate (chem_state as in chem_integrate).  Per
  * cell: features -> network -> inverse transform -> fp64 projection -> fp64 temperature
- * -> gate (feature range, element residual, negativity, temperature solve, |dT|).
+ * -> gate (feature range, element residual, negativity, temperature solve, |dT|) ->
+ * judge: with the integrator's right-hand side F0 = f(Y0), F1 = f(Y1), the trapezoidal
+ * corrector Yc = Y0 + dt/2 (F0 + F1) gives the error estimate |T(e, Yc) - T(e, Y1)|,
+ * which must not exceed judge_tol * T(e, Y1); and the step must be slow for the cell
+ * (judge_rate), since along a growing mode with dt * lambda = 2 the defect does not
+ * see an error.
  * Accepted cells get the projected Y, its T, status CHEM_CELL_OK and nsteps 0; rejected
  * cells are integrated with rtol, atol (one thread per cell, the context's variant) and
  * get status CHEM_CELL_SURROGATE, or the integrator's failure code, and their attempted
@@ -351,6 +360,15 @@ int chem_surrogate_params(chem_ctx *ctx, float *h_out, const float *h_in, int64_
  */
 int chem_surrogate_grad(chem_ctx *ctx, const float *d_X, const float *d_T, int64_t B, float *d_Y,
                         float *h_grad, float *h_loss, void *stream);
+
+/*
+ * The network alone on B rows, as inference runs it (one fused kernel, activations kept
+ * on chip): d_X [B x 16] normalised features (fp32 device), d_Y [B x 16] outputs (fp32
+ * device, out; columns 9..15 zero).  Gives the same numbers as the forward pass of
+ * chem_surrogate_grad.  Asynchronous on stream.  Errors: B < 0 or NULL arrays with
+ * B > 0 -> CHEM_ERR_INVALID.  (Not a call of the paper's method: a check of the kernel.)
+ */
+int chem_surrogate_forward(chem_ctx *ctx, const float *d_X, int64_t B, float *d_Y, void *stream);
 
 /*
  * chem_integrate_batched for callers that cannot allocate device memory during the call.

@@ -95,7 +95,8 @@ class TrainCfg(C.Structure):
 
 class Gate(C.Structure):
     _fields_ = [("ood_margin", C.c_float), ("resid_max", C.c_float), ("neg_tol", C.c_float),
-                ("max_dT", C.c_float)]
+                ("max_dT", C.c_float), ("judge_tol", C.c_float),
+                ("judge_rate", C.c_float)]
 
 
 ORDER_STIFFNESS, ORDER_NATURAL = 0, 1
@@ -132,6 +133,7 @@ def load() -> C.CDLL:
         "chem_surrogate_load": (C.c_int, [vp, C.c_char_p]),
         "chem_surrogate_params": (C.c_int, [vp, vp, vp, i64]),
         "chem_surrogate_grad": (C.c_int, [vp, vp, vp, i64, vp, vp, vp, vp]),
+        "chem_surrogate_forward": (C.c_int, [vp, vp, i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -330,7 +332,8 @@ class Context:
     def surrogate_infer(self, rho, e, Y, T, dt, rtol=1e-6, atol=1e-10, status=None, nsteps=None,
                         mask=None, stats=None, gate=None, stream=None):
         """chem_surrogate_infer: advance Y, T in place over dt; gate is a dict of
-        ood_margin / resid_max / neg_tol / max_dT (0 or missing = default)."""
+        ood_margin / resid_max / neg_tol / max_dT / judge_tol / judge_rate (0 or missing =
+        default)."""
         n = rho.numel()
         st = State(_ptr(rho).value, _ptr(e).value, _ptr(Y).value, Y.stride(0), _ptr(T).value, None,
                    None if status is None else status.data_ptr(),
@@ -370,6 +373,15 @@ class Context:
                                                g.ctypes.data_as(C.c_void_p), loss.ctypes.data_as(C.c_void_p),
                                                _stream(stream)))
         return Y, g, float(loss[0])
+
+    def surrogate_forward(self, X, stream=None):
+        """chem_surrogate_forward (the fused inference network) on an fp32 CUDA tensor
+        X [B, 16] of normalised features: returns Y [B, 16]."""
+        import torch
+        B = X.shape[0]
+        Y = torch.empty((B, 16), dtype=torch.float32, device=X.device)
+        self._raise(self.L.chem_surrogate_forward(self.h, _ptr(X), B, _ptr(Y), _stream(stream)))
+        return Y
 
     def integrate_host(self, rho, e, Y, T, dt, rtol=1e-6, atol=1e-10, h=None, status=None,
                        nsteps=None, stream=None):

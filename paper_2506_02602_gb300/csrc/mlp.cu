@@ -17,39 +17,12 @@
 
 #include "internal.cuh"
 #include "mlp.cuh"
+#include "mma.cuh"
 
 namespace chem {
 
 constexpr int GBM = 128, GBN = 128, GBK = 32, GPAD = 8;
 constexpr int GTHREADS = 256;
-
-__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
-
-__device__ __forceinline__ float gelu_grad_f(float x) {
-  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
-}
-
-__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const void *smem) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
-}
-
-__device__ __forceinline__ void ldmatrix_x2(uint32_t (&r)[2], const void *smem) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
-               : "=r"(r[0]), "=r"(r[1])
-               : "r"(a));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
 
 __global__ void __launch_bounds__(GTHREADS) k_gemm_bf16(GemmArgs g) {
   __shared__ __align__(16) __nv_bfloat16 As[GBM][GBK + GPAD];
@@ -60,6 +33,13 @@ __global__ void __launch_bounds__(GTHREADS) k_gemm_bf16(GemmArgs g) {
   const int wn = (warp >> 2) * 64;  // warp column offset
   const int64_t m0 = (int64_t)blockIdx.y * GBM;
   const int64_t n0 = (int64_t)blockIdx.x * GBN;
+  // this CTA's K slice (the whole K without split-K)
+  int64_t kbeg = 0, kend = g.K;
+  if (g.split > 1) {
+    const int64_t steps = (g.K + GBK - 1) / GBK, per = (steps + g.split - 1) / g.split;
+    kbeg = (int64_t)blockIdx.z * per * GBK;
+    kend = kbeg + per * GBK < g.K ? kbeg + per * GBK : g.K;
+  }
   float acc[2][8][4];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
@@ -68,18 +48,20 @@ __global__ void __launch_bounds__(GTHREADS) k_gemm_bf16(GemmArgs g) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
   const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-  for (int64_t k0 = 0; k0 < g.K; k0 += GBK) {
-    // stage the A and B tiles (16 elements per thread each); the k index runs fastest
-    // across threads so k-contiguous operands load coalesced
+  for (int64_t k0 = kbeg; k0 < kend; k0 += GBK) {
+    // stage the A and B tiles (16 elements per thread each); across threads the index
+    // along the operand's unit-stride dimension runs fastest, so loads coalesce for
+    // k-contiguous operands (forward, input gradient) and row-contiguous ones (weight
+    // gradient) alike
     for (int idx = tid; idx < GBM * GBK; idx += GTHREADS) {
-      const int r = idx / GBK, c = idx % GBK;
+      const int r = g.sak == 1 ? idx / GBK : idx % GBM, c = g.sak == 1 ? idx % GBK : idx / GBM;
       const int64_t m = m0 + r, k = k0 + c;
-      As[r][c] = (m < g.M && k < g.K) ? g.A[m * g.sam + k * g.sak] : zero;
+      As[r][c] = (m < g.M && k < kend) ? g.A[m * g.sam + k * g.sak] : zero;
     }
     for (int idx = tid; idx < GBN * GBK; idx += GTHREADS) {
-      const int r = idx / GBK, c = idx % GBK;
+      const int r = g.sbk == 1 ? idx / GBK : idx % GBN, c = g.sbk == 1 ? idx % GBK : idx / GBN;
       const int64_t n = n0 + r, k = k0 + c;
-      Bs[r][c] = (n < g.N && k < g.K) ? g.B[n * g.sbn + k * g.sbk] : zero;
+      Bs[r][c] = (n < g.N && k < kend) ? g.B[n * g.sbn + k * g.sbk] : zero;
     }
     __syncthreads();
 #pragma unroll
@@ -111,7 +93,9 @@ __global__ void __launch_bounds__(GTHREADS) k_gemm_bf16(GemmArgs g) {
       for (int q = 0; q < 4; ++q) {
         const int64_t m = m0 + wm + i * 16 + gq + (q >> 1) * 8;
         const int64_t n = n0 + wn + j * 8 + tq * 2 + (q & 1);
-        if (m < g.M && n < g.N) {
+        if (m < g.M && n < g.N && g.split > 1) {
+          g.Cf[(int64_t)blockIdx.z * g.split_ld + m * g.ldc + n] = acc[i][j][q] * g.alpha;
+        } else if (m < g.M && n < g.N) {
           float v = acc[i][j][q] * g.alpha;
           if (g.bias) v += g.bias[n];
           if (g.accumulate) v += g.Cf[m * g.ldc + n];
@@ -123,7 +107,9 @@ __global__ void __launch_bounds__(GTHREADS) k_gemm_bf16(GemmArgs g) {
 
 cudaError_t launch_gemm(const GemmArgs &g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
-  dim3 grid((unsigned)((g.N + GBN - 1) / GBN), (unsigned)((g.M + GBM - 1) / GBM));
+  if (g.split > 1 && (!g.Cf || g.Cb || g.bias || g.accumulate)) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)((g.N + GBN - 1) / GBN), (unsigned)((g.M + GBM - 1) / GBM),
+            (unsigned)(g.split > 1 ? g.split : 1));
   k_gemm_bf16<<<grid, GTHREADS, 0, s>>>(g);
   return cudaGetLastError();
 }
@@ -167,22 +153,35 @@ __global__ void k_mse(int64_t M, int nout, int ldy, const float *__restrict__ Y,
 }
 
 // db[n] = sum_m dZ[m, n] (one block per 32 columns, fp32 accumulation)
+// Partial column sums: CTA (x, y) sums rows y, y + nsplit, ... of columns 32x .. 32x+31
+// into part[y * N + n] (8 row groups per CTA, combined in a fixed order).
 __global__ void k_bias_grad(int64_t M, int N, const __nv_bfloat16 *__restrict__ dZ, int ld,
-                            float *__restrict__ db) {
+                            float *__restrict__ part) {
   __shared__ float red[8][33];
   const int n = blockIdx.x * 32 + (threadIdx.x & 31);
   const int row = threadIdx.x >> 5;  // 8 row groups
+  const int64_t stride = 8 * (int64_t)gridDim.y;
   float s = 0.0f;
   if (n < N)
-    for (int64_t m = row; m < M; m += 8) s += __bfloat162float(dZ[m * ld + n]);
+    for (int64_t m = (int64_t)blockIdx.y * 8 + row; m < M; m += stride) s += __bfloat162float(dZ[m * ld + n]);
   red[row][threadIdx.x & 31] = s;
   __syncthreads();
   if (threadIdx.x < 32 && n < N) {
     float t = 0.0f;
 #pragma unroll
     for (int r = 0; r < 8; ++r) t += red[r][threadIdx.x];
-    db[n] = t;
+    part[(int64_t)blockIdx.y * N + n] = t;
   }
+}
+
+// out[i] = sum_{s < nsplit} part[s * split_ld + i], in order of s
+__global__ void k_reduce_splits(int64_t n, int nsplit, const float *__restrict__ part, int64_t split_ld,
+                                float *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float t = 0.0f;
+  for (int z = 0; z < nsplit; ++z) t += part[z * split_ld + i];
+  out[i] = t;
 }
 
 // Adam on fp32 master weights; refreshes the bf16 shadows (both orientations for W).
@@ -235,9 +234,17 @@ cudaError_t launch_mse(int64_t M, int nout, int ldy, const float *Y, const float
   k_mse<<<blocks(M * lddy, 256), 256, 0, s>>>(M, nout, ldy, Y, Tg, ldt, dY, lddy, loss);
   return cudaGetLastError();
 }
-cudaError_t launch_bias_grad(int64_t M, int N, const __nv_bfloat16 *dZ, int ld, float *db, cudaStream_t s) {
-  k_bias_grad<<<blocks(N, 32), 256, 0, s>>>(M, N, dZ, ld, db);
+cudaError_t launch_reduce_splits(int64_t n, int nsplit, const float *part, int64_t split_ld, float *out,
+                                 cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_reduce_splits<<<blocks(n, 256), 256, 0, s>>>(n, nsplit, part, split_ld, out);
   return cudaGetLastError();
+}
+cudaError_t launch_bias_grad(int64_t M, int N, const __nv_bfloat16 *dZ, int ld, float *part, int nsplit,
+                             float *db, cudaStream_t s) {
+  k_bias_grad<<<dim3(blocks(N, 32), (unsigned)nsplit), 256, 0, s>>>(M, N, dZ, ld, part);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? launch_reduce_splits(N, nsplit, part, N, db, s) : e;
 }
 cudaError_t launch_adam(int64_t n, float *w, const float *g, float *m, float *v, float lr, float b1,
                         float b2, float eps, int step, __nv_bfloat16 *w_bf, __nv_bfloat16 *wT_bf,

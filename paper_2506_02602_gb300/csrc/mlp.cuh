@@ -11,6 +11,9 @@ namespace chem {
 // C[m, n] = alpha * sum_k A(m, k) B(n, k) (+ bias[n]) (+ Cf[m, n] if accumulate);
 // A(m, k) = A[m*sam + k*sak], B(n, k) = B[n*sbn + k*sbk].  Outputs: Cf (fp32, ldc) and/or
 // Cb (bf16, ldcb) holding the value, or GELU(value) when gelu is set.
+// Split-K (split > 1): the K range is cut into `split` slices of whole 32-wide steps and
+// slice z writes its partial sum (alpha applied, no bias, no bf16 output) to
+// Cf + z * split_ld; launch_reduce_splits adds the slices in a fixed order.
 struct GemmArgs {
   int64_t M, N, K;
   const __nv_bfloat16 *A;
@@ -25,6 +28,8 @@ struct GemmArgs {
   int64_t ldcb;
   int gelu;
   int accumulate;
+  int split;
+  int64_t split_ld;
 };
 
 cudaError_t launch_gemm(const GemmArgs &g, cudaStream_t s);
@@ -32,8 +37,12 @@ cudaError_t launch_gelu_backward(int64_t M, int N, const float *dH, int ldh, con
                                  __nv_bfloat16 *dZ, int lddz, cudaStream_t s);
 cudaError_t launch_mse(int64_t M, int nout, int ldy, const float *Y, const float *Tg, int ldt,
                        __nv_bfloat16 *dY, int lddy, float *loss, cudaStream_t s);
-cudaError_t launch_bias_grad(int64_t M, int N, const __nv_bfloat16 *dZ, int ld, float *db,
-                             cudaStream_t s);
+cudaError_t launch_reduce_splits(int64_t n, int nsplit, const float *part, int64_t split_ld,
+                                 float *out, cudaStream_t s);
+// db[n] = sum_m dZ[m, n], through nsplit row slices written to part [nsplit x N], then
+// reduced in a fixed order (deterministic).
+cudaError_t launch_bias_grad(int64_t M, int N, const __nv_bfloat16 *dZ, int ld, float *part,
+                             int nsplit, float *db, cudaStream_t s);
 cudaError_t launch_adam(int64_t n, float *w, const float *g, float *m, float *v, float lr, float b1,
                         float b2, float eps, int step, __nv_bfloat16 *w_bf, __nv_bfloat16 *wT_bf,
                         int rows, int cols, cudaStream_t s);

@@ -39,7 +39,6 @@ struct Surrogate {
   // inference scratch
   int64_t chunk_cap = 0;
   float *Xraw = nullptr, *O = nullptr;
-  __nv_bfloat16 *Xbf = nullptr, *Ha = nullptr, *Hb = nullptr;
   uint8_t *Tok = nullptr;
   int64_t fb_cap = 0;
   int32_t *fb_idx = nullptr;
@@ -59,9 +58,6 @@ static void free_surrogate(Surrogate *s) {
   cudaFree(s->dev_norm);
   cudaFree(s->Xraw);
   cudaFree(s->O);
-  cudaFree(s->Xbf);
-  cudaFree(s->Ha);
-  cudaFree(s->Hb);
   cudaFree(s->Tok);
   cudaFree(s->fb_idx);
   cudaFree(s->fb_count);
@@ -192,12 +188,16 @@ static cudaError_t layer_forward(Surrogate *s, int l, int64_t M, const __nv_bflo
 }
 
 // Training buffers for a batch of B rows.
+// Split-K factor of the weight-gradient GEMMs (the batch is their reduction dimension)
+// and the row slices of the bias-gradient sums.
+constexpr int kGradSplit = 16;
+
 struct TrainBufs {
-  float *Xb = nullptr, *Tb = nullptr, *Y = nullptr, *loss = nullptr;
+  float *Xb = nullptr, *Tb = nullptr, *Y = nullptr, *loss = nullptr, *part = nullptr;
   float *Z[3] = {}, *dH = nullptr;
   __nv_bfloat16 *Xbf = nullptr, *H[3] = {}, *dY = nullptr, *dZ = nullptr;
   void release() {
-    cudaFree(Xb); cudaFree(Tb); cudaFree(Y); cudaFree(loss); cudaFree(dH); cudaFree(Xbf);
+    cudaFree(Xb); cudaFree(Tb); cudaFree(Y); cudaFree(loss); cudaFree(part); cudaFree(dH); cudaFree(Xbf);
     cudaFree(dY); cudaFree(dZ);
     for (int i = 0; i < 3; ++i) { cudaFree(Z[i]); cudaFree(H[i]); }
   }
@@ -206,6 +206,7 @@ struct TrainBufs {
     SCHK(cudaMalloc(&Tb, B * kSurOut * sizeof(float)));
     SCHK(cudaMalloc(&Y, B * kSurOut * sizeof(float)));
     SCHK(cudaMalloc(&loss, sizeof(float)));
+    SCHK(cudaMalloc(&part, (size_t)kGradSplit * kSurHidden * kSurHidden * sizeof(float)));
     SCHK(cudaMalloc(&dH, B * kSurHidden * sizeof(float)));
     SCHK(cudaMalloc(&Xbf, B * kSurIn * sizeof(__nv_bfloat16)));
     SCHK(cudaMalloc(&dY, B * kSurOut * sizeof(__nv_bfloat16)));
@@ -233,14 +234,18 @@ static cudaError_t forward_backward(Surrogate *s, TrainBufs &b, int64_t B, cudaS
   for (int l = kSurLayers - 1; l >= 0; --l) {
     const int N = kSurN[l], K = kSurK[l];
     // dW[n, k] = sum_m G[m, n] Hin[m, k]
+    // (split-K over the batch into b.part, then a fixed-order reduction)
     GemmArgs gw{};
     gw.M = N; gw.N = K; gw.K = B;
     gw.A = G; gw.sam = 1; gw.sak = N;
     gw.B = Hin[l]; gw.sbn = 1; gw.sbk = K;
     gw.alpha = 1.0f;
-    gw.Cf = s->grad + s->off_W[l]; gw.ldc = K;
+    gw.Cf = b.part; gw.ldc = K;
+    gw.split = kGradSplit;
+    gw.split_ld = (int64_t)N * K;
     SCHK(launch_gemm(gw, st));
-    SCHK(launch_bias_grad(B, N, G, N, s->grad + s->off_b[l], st));
+    SCHK(launch_reduce_splits((int64_t)N * K, kGradSplit, b.part, (int64_t)N * K, s->grad + s->off_W[l], st));
+    SCHK(launch_bias_grad(B, N, G, N, b.part, kGradSplit, s->grad + s->off_b[l], st));
     if (l == 0) break;
     // dHin[m, k] = sum_n G[m, n] W[n, k] (W^T stored [K x N])
     GemmArgs gx{};
@@ -286,6 +291,8 @@ static SurrogateConsts make_consts(const Surrogate *s, const chem_surrogate_gate
   c.resid_max = g.resid_max;
   c.neg_tol = g.neg_tol;
   c.max_dT = g.max_dT;
+  c.judge_tol = g.judge_tol;
+  c.judge_rate = g.judge_rate;
   c.lam = s->lam;
   for (int el = 0; el < 3; ++el)
     for (int k = 0; k < NSP; ++k) c.E[el][k] = mt.Emat[el][k];
@@ -322,16 +329,28 @@ static Surrogate *ensure_surrogate(chem_ctx *ctx, cudaError_t *err) {
   return static_cast<Surrogate *>(slot);
 }
 
+// Cells per inference chunk (features and outputs, 132 B a cell, are staged per chunk).
+constexpr int64_t kInferChunk = 1 << 22;
+
+// The fused network over n rows of features X (raw with norm, else normalised).
+static cudaError_t mlp_forward(const Surrogate *s, int64_t n, const float *X, const float *norm, float *O,
+                               cudaStream_t st) {
+  const __nv_bfloat16 *W[kSurLayers];
+  const float *b[kSurLayers];
+  for (int l = 0; l < kSurLayers; ++l) {
+    W[l] = s->W[l];
+    b[l] = s->param + s->off_b[l];
+  }
+  return launch_mlp_fused(n, X, norm, W, b, O, st);
+}
+
 static cudaError_t ensure_infer_buffers(Surrogate *s, int64_t chunk, int64_t n) {
   if (chunk > s->chunk_cap) {
-    cudaFree(s->Xraw); cudaFree(s->O); cudaFree(s->Xbf); cudaFree(s->Ha); cudaFree(s->Hb); cudaFree(s->Tok);
-    s->Xraw = s->O = nullptr; s->Xbf = s->Ha = s->Hb = nullptr; s->Tok = nullptr;
+    cudaFree(s->Xraw); cudaFree(s->O); cudaFree(s->Tok);
+    s->Xraw = s->O = nullptr; s->Tok = nullptr;
     s->chunk_cap = 0;
     SCHK(cudaMalloc(&s->Xraw, chunk * kSurIn * sizeof(float)));
     SCHK(cudaMalloc(&s->O, chunk * kSurOut * sizeof(float)));
-    SCHK(cudaMalloc(&s->Xbf, chunk * kSurIn * sizeof(__nv_bfloat16)));
-    SCHK(cudaMalloc(&s->Ha, chunk * kSurHidden * sizeof(__nv_bfloat16)));
-    SCHK(cudaMalloc(&s->Hb, chunk * kSurHidden * sizeof(__nv_bfloat16)));
     SCHK(cudaMalloc(&s->Tok, chunk));
     s->chunk_cap = chunk;
   }
@@ -392,6 +411,16 @@ int chem_surrogate_grad(chem_ctx *ctx, const float *d_X, const float *d_T, int64
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   b.release();
   return e == cudaSuccess ? CHEM_OK : sur_cuda(ctx, e, "surrogate forward/backward");
+}
+
+int chem_surrogate_forward(chem_ctx *ctx, const float *d_X, int64_t B, float *d_Y, void *stream) {
+  if (!ctx) return CHEM_ERR_INVALID;
+  if (B < 0 || (B > 0 && (!d_X || !d_Y))) return sur_fail(ctx, CHEM_ERR_INVALID, "B >= 0, X and Y required");
+  cudaError_t e;
+  Surrogate *s = ensure_surrogate(ctx, &e);
+  if (!s) return sur_cuda(ctx, e, "allocating the surrogate");
+  e = mlp_forward(s, B, d_X, nullptr, d_Y, (cudaStream_t)stream);
+  return e == cudaSuccess ? CHEM_OK : sur_cuda(ctx, e, "surrogate forward");
 }
 
 int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
@@ -534,8 +563,10 @@ int chem_surrogate_infer(chem_ctx *ctx, const chem_state *state, int64_t n, doub
   if (g.ood_margin == 0.0f) g.ood_margin = 0.05f;
   if (g.resid_max == 0.0f) g.resid_max = 0.02f;
   if (g.neg_tol == 0.0f) g.neg_tol = 1e-6f;
-  if (g.max_dT == 0.0f) g.max_dT = 25.0f;
-  const int64_t chunk = n < 524288 ? n : 524288;
+  if (g.max_dT == 0.0f) g.max_dT = 200.0f;
+  if (g.judge_tol == 0.0f) g.judge_tol = 5e-4f;
+  if (g.judge_rate == 0.0f) g.judge_rate = 1.0f;
+  const int64_t chunk = n < kInferChunk ? n : kInferChunk;
   e = ensure_infer_buffers(s, chunk, n);
   if (e != cudaSuccess) return sur_cuda(ctx, e, "allocating inference buffers");
   const MechTables &mt = chem_ctx_tables(ctx);
@@ -546,13 +577,10 @@ int chem_surrogate_infer(chem_ctx *ctx, const chem_state *state, int64_t n, doub
     e = launch_features(mt, m, state->d_rho + base, state->d_e + base, state->d_Y + base, state->ldY,
                         state->d_T + base, nullptr, dt, nullptr, 0, s->lam, s->Xraw, nullptr, nullptr,
                         s->Tok, st);
-    if (e == cudaSuccess) e = launch_norm_bf16(m, kSurFeat, kSurIn, s->Xraw, s->dev_norm, s->dev_norm + 16, s->Xbf, st);
-    if (e == cudaSuccess) e = layer_forward(s, 0, m, s->Xbf, nullptr, s->Ha, nullptr, st);
-    if (e == cudaSuccess) e = layer_forward(s, 1, m, s->Ha, nullptr, s->Hb, nullptr, st);
-    if (e == cudaSuccess) e = layer_forward(s, 2, m, s->Hb, nullptr, s->Ha, nullptr, st);
-    if (e == cudaSuccess) e = layer_forward(s, 3, m, s->Ha, nullptr, nullptr, s->O, st);
+    if (e == cudaSuccess) e = mlp_forward(s, m, s->Xraw, s->dev_norm, s->O, st);
     if (e == cudaSuccess)
-      e = launch_surrogate_finish(mt, sc, m, s->O, s->Xraw, s->Tok, state->d_rho + base, state->d_e + base,
+      e = launch_surrogate_finish(chem_ctx_variant(ctx), mt, sc, m, dt, s->O, s->Xraw, s->Tok,
+                                  state->d_rho + base, state->d_e + base,
                                   state->d_Y + base, state->ldY, state->d_T + base,
                                   state->d_status ? state->d_status + base : nullptr,
                                   state->d_nsteps ? state->d_nsteps + base : nullptr,

@@ -36,6 +36,8 @@ struct SurrogateConsts {
   float resid_max;                      // max relative element residual before projection
   float neg_tol;                        // most negative mass fraction allowed after projection
   float max_dT;                         // largest accepted |T' - T0| (K)
+  float judge_tol;                      // largest estimated relative T error (<= 0: no judge)
+  float judge_rate;                     // largest dt * relative rate of change (< 0: no bound)
   double lam;                           // Box-Cox lambda
   double E[3][NSP];                     // element mass fraction per unit species mass fraction
 };
@@ -48,16 +50,22 @@ cudaError_t launch_colstats(int64_t n, int ncol, int ld, const float *A, double 
                             int *mnkey, int *mxkey, cudaStream_t s);
 cudaError_t launch_normalize(int64_t n, int ncol, int ld, float *A, const float *mean,
                              const float *inv_std, __nv_bfloat16 *Abf, cudaStream_t s);
-cudaError_t launch_surrogate_finish(const MechTables &mt, const SurrogateConsts &sc, int64_t n,
-                                    const float *O, const float *Xraw, const uint8_t *Tok,
-                                    const double *rho, const double *e, double *Y, int64_t ld,
-                                    double *T, int32_t *status, int32_t *nsteps, uint8_t *mask,
-                                    int32_t *fb_idx, unsigned int *fb_count, int64_t base,
-                                    cudaStream_t s);
+cudaError_t launch_surrogate_finish(int variant, const MechTables &mt, const SurrogateConsts &sc,
+                                    int64_t n, double dt, const float *O, const float *Xraw,
+                                    const uint8_t *Tok, const double *rho, const double *e, double *Y,
+                                    int64_t ld, double *T, int32_t *status, int32_t *nsteps,
+                                    uint8_t *mask, int32_t *fb_idx, unsigned int *fb_count,
+                                    int64_t base, cudaStream_t s);
 cudaError_t launch_norm_bf16(int64_t n, int ncol, int ld, const float *src, const float *mean,
                              const float *inv_std, __nv_bfloat16 *dst, cudaStream_t s);
 cudaError_t launch_surrogate_stats(chem_stats *st, int64_t n, const unsigned int *fb_count,
                                    cudaStream_t s);
+// The whole network on n rows in one kernel (mlp_fused.cu): X [n x 16] raw features
+// normalised with norm = {fmean[16], fistd[16]} (or already normalised when norm is
+// NULL), W / b the BF16 weights and FP32 biases per layer, O [n x 16] the outputs.
+cudaError_t launch_mlp_fused(int64_t n, const float *X, const float *norm,
+                             const __nv_bfloat16 *const (&W)[kSurLayers],
+                             const float *const (&b)[kSurLayers], float *O, cudaStream_t s);
 cudaError_t launch_lsrk_indexed(int variant, const MechTables &mt, const CellArgs &a,
                                 const StepParams &p, const int32_t *idx, const unsigned int *count,
                                 int64_t max_count, cudaStream_t s);

@@ -9,6 +9,19 @@
 // The temperature is always solved from (e, Y) in fp64, so energy is conserved exactly
 // by construction; the projection restores the element (H, O, N) mass fractions, hence
 // sum Y too, in fp64.
+//
+// Error judge: the integrator's own right-hand side checks each candidate result.  With
+// F0 = f(Y0) and F1 = f(Y1) the trapezoidal corrector Yc = Y0 + dt/2 (F0 + F1) differs
+// from the exact solution by O(dt^3 |d3Y/dt3|) where the cell is smooth over dt, so
+// |T(e, Yc) - T(e, Y1)| estimates the temperature error of Y1; a cell whose estimate
+// exceeds judge_tol * T is sent to the integrator.  Stiff cells (dt beyond the fast
+// time scales), where the trapezoidal rule itself is not accurate, fail the check too.
+// Linearised, an error d of Y1 shows in the defect as (I - dt/2 J) d, which vanishes
+// along a growing mode with dt * lambda = 2 (chain branching before ignition), so the
+// judge also bounds the cell's reactivity over the step,
+//   dt * max_k max(|F0_k| / (|Y0_k| + 1e-6), |F1_k| / (|Y1_k| + 1e-6)) <= judge_rate,
+// which keeps the factor at or above 1 - judge_rate / 2 (1e-6: the mass fraction below
+// which a species' share of the mixture energy is under ~1 K).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -130,17 +143,63 @@ __global__ void k_normalize(int64_t n, int ncol, int ld, float *A, const float *
   if (Abf) Abf[t] = __float2bfloat16(v);
 }
 
+// Temperature-error estimate of a surrogate result y1 (see the file comment): returns
+// false if a right-hand side or temperature solve fails, else sets dT = |T(Yc) - T1|
+// and rate = dt * the largest relative rate of change at either end.
+// The right-hand sides use the context's variant (fp32 rates in the mixed one).
+template <int V>
+__device__ __noinline__ bool judge_defect(const MechTables &mt, const double (&y0)[NSP],
+                                          const double (&y1)[NSP], double rho, double eR,
+                                          double T0, double T1, double dt, double &dT,
+                                          double &rate) {
+  double F0[NSP], F1[NSP];
+  double Ta = T0, Tb = T1;
+  const double invRho = 1.0 / rho;
+  bool ok;
+  if constexpr (V == CHEM_VARIANT_MIXED) {
+    float u0[NSP], u1[NSP], f0[NSP], f1[NSP];
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+      u0[k] = (float)y0[k];
+      u1[k] = (float)y1[k];
+    }
+    ok = cell_rhs_mixed(mt, u0, (float)rho, (float)invRho, eR, Ta, f0) &&
+         cell_rhs_mixed(mt, u1, (float)rho, (float)invRho, eR, Tb, f1);
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+      F0[k] = f0[k];
+      F1[k] = f1[k];
+    }
+  } else {
+    ok = cell_rhs(mt, y0, rho, invRho, eR, Ta, F0) && cell_rhs(mt, y1, rho, invRho, eR, Tb, F1);
+  }
+  if (!ok) return false;
+  double yw[NSP], r = 0.0;
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) {
+    yw[k] = (y0[k] + 0.5 * dt * (F0[k] + F1[k])) * mt.invW[k];
+    r = fmax(r, fmax(fabs(F0[k]) / (fabs(y0[k]) + 1e-6), fabs(F1[k]) / (fabs(y1[k]) + 1e-6)));
+  }
+  rate = dt * r;
+  double Tc = T1;
+  if (!solve_T(mt, yw, eR, Tc)) return false;
+  dT = fabs(Tc - T1);
+  return isfinite(dT);
+}
+
 // The inference epilogue, one thread per cell.  Takes the network output O [n x 16]
 // (z-scored BC increments), the raw features X (un-normalised: T, ln p, log10 dt,
 // BC(Y0)) and the state; writes accepted cells (Y'', T'', status OK, nsteps 0) and
 // appends rejected ones to the fallback list.
-__global__ void k_surrogate_finish(const __grid_constant__ MechTables mt, SurrogateConsts sc,
-                                   int64_t n, const float *__restrict__ O,
-                                   const float *__restrict__ Xraw, const uint8_t *__restrict__ Tok,
-                                   const double *__restrict__ rho, const double *__restrict__ e,
-                                   double *Y, int64_t ld, double *T, int32_t *status,
-                                   int32_t *nsteps, uint8_t *mask, int32_t *fb_idx,
-                                   unsigned int *fb_count, int64_t base) {
+template <int V>
+__global__ void __launch_bounds__(128)
+    k_surrogate_finish(const __grid_constant__ MechTables mt, const __grid_constant__ SurrogateConsts sc,
+                       int64_t n, double dt, const float *__restrict__ O,
+                       const float *__restrict__ Xraw, const uint8_t *__restrict__ Tok,
+                       const double *__restrict__ rho, const double *__restrict__ e, double *Y,
+                       int64_t ld, double *T, int32_t *status, int32_t *nsteps, uint8_t *mask,
+                       int32_t *fb_idx, unsigned int *fb_count, int64_t base) {
+  load_math_tables();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float *x = Xraw + i * kSurIn;
@@ -221,6 +280,11 @@ __global__ void k_surrogate_finish(const __grid_constant__ MechTables mt, Surrog
   double T1 = (double)x[0];
   const bool tok = solve_T(mt, yw, e[i] / R_U, T1);
   accept &= tok && fabs(T1 - (double)x[0]) <= (double)sc.max_dT;
+  if (accept && sc.judge_tol > 0.0f) {
+    double dT = 0.0, rate = 0.0;
+    const bool jok = judge_defect<V>(mt, y0, y1, rho[i], e[i] / R_U, (double)x[0], T1, dt, dT, rate);
+    accept = jok && dT <= (double)sc.judge_tol * T1 && (sc.judge_rate < 0.0f || rate <= (double)sc.judge_rate);
+  }
   if (accept) {
 #pragma unroll
     for (int k = 0; k < NSP; ++k) Y[k * ld + i] = y1[k];
@@ -335,15 +399,19 @@ cudaError_t launch_normalize(int64_t n, int ncol, int ld, float *A, const float 
   return cudaGetLastError();
 }
 
-cudaError_t launch_surrogate_finish(const MechTables &mt, const SurrogateConsts &sc, int64_t n,
-                                    const float *O, const float *Xraw, const uint8_t *Tok,
-                                    const double *rho, const double *e, double *Y, int64_t ld,
-                                    double *T, int32_t *status, int32_t *nsteps, uint8_t *mask,
-                                    int32_t *fb_idx, unsigned int *fb_count, int64_t base,
-                                    cudaStream_t s) {
+cudaError_t launch_surrogate_finish(int variant, const MechTables &mt, const SurrogateConsts &sc,
+                                    int64_t n, double dt, const float *O, const float *Xraw,
+                                    const uint8_t *Tok, const double *rho, const double *e, double *Y,
+                                    int64_t ld, double *T, int32_t *status, int32_t *nsteps,
+                                    uint8_t *mask, int32_t *fb_idx, unsigned int *fb_count,
+                                    int64_t base, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_surrogate_finish<<<nblk(n, 128), 128, 0, s>>>(mt, sc, n, O, Xraw, Tok, rho, e, Y, ld, T, status,
-                                                  nsteps, mask, fb_idx, fb_count, base);
+  if (variant == CHEM_VARIANT_MIXED)
+    k_surrogate_finish<CHEM_VARIANT_MIXED><<<nblk(n, 128), 128, 0, s>>>(
+        mt, sc, n, dt, O, Xraw, Tok, rho, e, Y, ld, T, status, nsteps, mask, fb_idx, fb_count, base);
+  else
+    k_surrogate_finish<CHEM_VARIANT_FP64><<<nblk(n, 128), 128, 0, s>>>(
+        mt, sc, n, dt, O, Xraw, Tok, rho, e, Y, ld, T, status, nsteps, mask, fb_idx, fb_count, base);
   return cudaGetLastError();
 }
 

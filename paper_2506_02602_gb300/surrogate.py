@@ -90,9 +90,10 @@ def trajectory_states(ctx, ntraj, seed=3, nstage=48, t0=1e-9, t_end=3e-3, nfine=
     return {k: (torch.cat(v, dim=1) if k == "Y" else torch.cat(v)) for k, v in out.items()}
 
 
-def make_pairs(ctx, states, seed=3, dt_lo=1e-9, dt_hi=1e-7, max_pairs=None):
+def make_pairs(ctx, states, seed=3, dt_lo=1e-9, dt_hi=1e-7, max_pairs=None, max_dT=None):
     """(state, dt) -> state pairs: each state advanced over its own log-uniform dt
-    (pairs whose integration did not end with status 0 are dropped)."""
+    (pairs whose integration did not end with status 0 are dropped, and with max_dT
+    those whose temperature changes by more than max_dT K)."""
     import torch
     n = states["T"].numel()
     rng = np.random.default_rng(seed + 7)
@@ -111,9 +112,32 @@ def make_pairs(ctx, states, seed=3, dt_lo=1e-9, dt_hi=1e-7, max_pairs=None):
     ctx.integrate_batched(rho, e, Y1, T1, torch.arange(m + 1, dtype=torch.int64, device=dev), dt,
                           torch.ones(m, dtype=torch.int32, device=dev), status=st)
     good = st == 0   # a pair whose integration failed is not a sample of the map
+    if max_dT is not None:   # keep the mildly reactive pairs only
+        good &= (T1 - T0).abs() <= max_dT
     return {"rho": rho[good].contiguous(), "e": e[good].contiguous(), "Y0": Y0[:, good].contiguous(),
             "T0": T0[good].contiguous(), "dt": dt[good].contiguous(), "Y1": Y1[:, good].contiguous(),
             "T1": T1[good].contiguous()}
+
+
+def split_by_trajectory(states, heldout=0.1, seed=3):
+    """(train, held-out) state sets; a seeded fraction of whole trajectories is held out."""
+    import torch
+    traj = states["traj"]
+    ntraj = int(traj.max().item()) + 1 if traj.numel() else 0
+    rng = np.random.default_rng(seed + 11)
+    held = torch.tensor(rng.random(ntraj) < heldout, device=traj.device)[traj]
+
+    def take(m):
+        return {k: (v[:, m].contiguous() if k == "Y" else v[m].contiguous()) for k, v in states.items()}
+    return take(~held), take(held)
+
+
+def draw_cells(states, n, seed=3):
+    """n cells drawn with replacement (seeded) from a state set, as contiguous planes."""
+    import torch
+    m = states["T"].numel()
+    idx = torch.tensor(np.random.default_rng(seed + 13).integers(0, m, n), device=states["T"].device)
+    return {k: (v[:, idx].contiguous() if k == "Y" else v[idx].contiguous()) for k, v in states.items()}
 
 
 def evaluate(ctx_sur, ctx_ref, states, dt, rtol=1e-6, atol=1e-10, gate=None, reps=3):

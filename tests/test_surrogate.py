@@ -79,6 +79,11 @@ def test_forward_backward_matches_fp64_oracle(lib):
     lo, dy = mlp.mse(Yo, Tt[:, :9])
     go = mlp.backward(params, pre, dy)
     Yg = Y.cpu().numpy()
+    # the fused inference kernel: same fragments, K order and epilogue -> same numbers
+    Yf = ctx.surrogate_forward(Xb.cuda()).cpu().numpy()
+    np.testing.assert_array_equal(Yf, Yg)
+    Yf2 = ctx.surrogate_forward(Xb[:333].contiguous().cuda()).cpu().numpy()  # ragged last tile
+    np.testing.assert_array_equal(Yf2, Yg[:333])
     assert np.linalg.norm(Yg[:, :9] - Yo) <= 2e-2 * np.linalg.norm(Yo)
     assert np.all(Yg[:, 9:] == 0.0)
     assert loss == pytest.approx(lo, rel=2e-2)
