@@ -8,13 +8,22 @@ stages, step control), from the same pristine state each time; the restore copy 
 an L2 flush (a 256 MB write, the inputs are 96 MB < 129 MB L2) are inside the timed
 region, so the reported rate slightly understates the kernel.
 
-Variants: plain fp64 and mixed precision (fp32 rates and stages, fp64 temperature solve,
-Gibbs terms, registers and control), each timed over K steps; the headline is the
-fastest variant whose error against the FP64 result meets its stated bound
-(mixed: 1e-5 relative on T).  Every variant's rate, error and roofline fraction is in
-"variants".
+Variants: plain fp64, mixed precision (fp32 rates and stages, fp64 temperature solve,
+Gibbs terms, registers and control) and the hybrid (the learned surrogate with its
+error judge, mixed-precision integration of the cells it rejects), each timed over K
+steps; the headline is the fastest variant whose error against the FP64 result meets
+its stated bound (mixed: 1e-5, hybrid: 1e-3 relative on T).  Every variant's rate,
+error and roofline fraction is in "variants".
+
+The surrogate leg ("surrogate") is the learned part's own workload: 48,000 seeded 0D
+ignition trajectories (phi U[0.5, 2], T0 U[900, 2200] K, p U[1, 30] atm) recorded by the
+GPU integrator, 2M (state, dt ~ logU[1e-9, 1e-7] s) -> state training pairs from 90 % of
+them, training on the GPU (batch 4096), and inference on 16,777,216 cells drawn from the
+held-out 10 %, against plain fp64 and mixed integration of the same cells.
 
 Legs of one run (rank 0 prints one JSON line):
+  surrogate data generation, training and inference (above; skipped by --no-surrogate,
+            which also drops the hybrid variant);
   value     device-resident throughput (cells/s) of the headline variant;
   e2e       the same through chem_integrate_host: host buffers (pinned), H2D + D2H
             copies inside the timed region;
@@ -53,6 +62,10 @@ def parse():
     ap.add_argument("--ny", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-amr", action="store_true", help="skip the AMR-batch comparison leg")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned surrogate (leg and variant)")
+    ap.add_argument("--sur-traj", type=int, default=48000)
+    ap.add_argument("--sur-epochs", type=int, default=100)
+    ap.add_argument("--sur-cells", type=int, default=1 << 24)
     ap.add_argument("--cpu-sample", type=int, default=131072)
     ap.add_argument("--ref-sample", type=int, default=32768)
     return ap.parse_args()
@@ -175,7 +188,122 @@ def run_reference(args, rank, world):
 
 
 # ----------------------------------------------------------------- GPU leg
-VARIANTS = (("fp64", 0.0), ("mixed", 1e-5))  # (variant, stated error bound on T vs FP64)
+VARIANTS = (("fp64", 0.0), ("mixed", 1e-5), ("hybrid", 1e-3))  # (variant, stated error bound on T vs FP64)
+MLP_FLOPS_PER_ROW = 2 * (16 * 256 + 256 * 256 * 2 + 256 * 16)  # padded 16-256-256-256-16 network
+
+
+def _bf16_peak():
+    """Measured dense BF16 peak (TFLOP/s, cuBLAS burst) of this GPU model."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
+
+
+BF16_PEAK_TFLOPS, BF16_PEAK_KIND = _bf16_peak()
+
+
+def timed(fn, reps, stream):
+    """Best CUDA-event time (ms) of fn() over reps calls, after one untimed call."""
+    import torch
+    fn()
+    best = float("inf")
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return best
+
+
+def surrogate_leg(args, mech, dev, stream):
+    """Data generation, training and inference of the learned surrogate (module docstring).
+    Returns the leg's summary and a mixed-precision context holding the trained network."""
+    import tempfile
+
+    import torch
+    from paper_2506_02602_gb300 import chem, surrogate
+    out = {}
+    gen = chem.Context(mech, "fp64", max_steps=4000)
+    plain = chem.Context(mech, "fp64")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = surrogate.trajectory_states(gen, args.sur_traj, seed=3)
+    tr, held = surrogate.split_by_trajectory(st, 0.1, seed=3)
+    pairs = surrogate.make_pairs(plain, tr, seed=3, max_pairs=2_000_000)
+    torch.cuda.synchronize()
+    out["data"] = {"trajectories": args.sur_traj, "states": int(st["T"].numel()),
+                   "train_pairs": int(pairs["T0"].numel()), "heldout_states": int(held["T"].numel()),
+                   "seconds": time.perf_counter() - t0}
+    gen.close()
+    hyb = chem.Context(mech, "mixed")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = hyb.surrogate_train(pairs["rho"], pairs["e"], pairs["Y0"], pairs["dt"], pairs["Y1"], T0=pairs["T0"],
+                               epochs=args.sur_epochs, batch=4096, lr=1e-3, seed=1, dt_power=1.0)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    steps = (pairs["T0"].numel() // 4096) * args.sur_epochs
+    out["train"] = {"epochs": args.sur_epochs, "batch": 4096, "adam_steps": int(steps), "seconds": t_train,
+                    "loss_first_last": [float(loss[0]), float(loss[-1])],
+                    "samples_per_s": steps * 4096 / t_train,
+                    "tflops": 3 * MLP_FLOPS_PER_ROW * steps * 4096 / t_train / 1e12}
+    del pairs, tr
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "net.bin")
+        hyb.surrogate_save(path)
+        hyb64 = chem.Context(mech, "fp64")
+        hyb64.surrogate_load(path)
+    mixed = chem.Context(mech, "mixed")
+    cells = surrogate.draw_cells(held, args.sur_cells, seed=3)
+    n = cells["T"].numel()
+    Y, T = cells["Y"].clone(), cells["T"].clone()
+    mask = torch.empty(n, dtype=torch.uint8, device=dev)
+
+    def reset():
+        Y.copy_(cells["Y"])
+        T.copy_(cells["T"])
+
+    # the fused network alone on n rows (the MLP kernel's tensor-pipe roofline)
+    Xf = torch.zeros(min(n, 1 << 22), 16, dtype=torch.float32, device=dev)
+    Xf[:, :12].normal_()
+    t_mlp = timed(lambda: hyb.surrogate_forward(Xf, stream=stream), 3, stream)
+    out["mlp_kernel"] = {"rows": int(Xf.shape[0]), "ms": t_mlp,
+                         "tflops": Xf.shape[0] * MLP_FLOPS_PER_ROW / (t_mlp * 1e-3) / 1e12}
+    del Xf
+    out["inference"] = {}
+    for dt in (1e-9, 1e-8):
+        r = {}
+        t = timed(lambda: (reset(), plain.integrate(cells["rho"], cells["e"], Y, T, dt, RTOL, ATOL, stream=stream)),
+                  2, stream)
+        Yr, Tr = Y.clone(), T.clone()
+        r["plain_fp64"] = {"cells_per_s": n / (t * 1e-3)}
+        t = timed(lambda: (reset(), mixed.integrate(cells["rho"], cells["e"], Y, T, dt, RTOL, ATOL, stream=stream)),
+                  2, stream)
+        r["mixed"] = {"cells_per_s": n / (t * 1e-3),
+                      "max_rel_T": float(((T - Tr).abs() / Tr).max())}
+        for name, ctx in (("surrogate_fp64_fallback", hyb64), ("surrogate_mixed_fallback", hyb)):
+            t = timed(lambda: (reset(), ctx.surrogate_infer(cells["rho"], cells["e"], Y, T, dt, RTOL, ATOL,
+                                                            mask=mask, stream=stream)), 2, stream)
+            rel = (T - Tr).abs() / Tr
+            fb = mask.bool()
+            r[name] = {"cells_per_s": n / (t * 1e-3), "fallback_frac": float(fb.float().mean()),
+                       "max_rel_T": float(rel.max()),
+                       "max_rel_T_accepted": float(rel[~fb].max()) if bool((~fb).any()) else 0.0,
+                       "max_abs_Y": float((Y - Yr).abs().max()),
+                       "speedup_vs_plain_fp64": r["plain_fp64"]["cells_per_s"] and
+                       (n / (t * 1e-3)) / r["plain_fp64"]["cells_per_s"]}
+        out["inference"][f"dt={dt:g}"] = r
+        del Yr, Tr
+    out["cells"] = n
+    out["stated_error_T"] = 1e-3
+    out["fallback_target"] = 5e-3
+    for c in (plain, hyb64, mixed):
+        c.close()
+    return out, hyb
 
 
 def amr_leg(ctx, steps, dev):
@@ -250,10 +378,15 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     mech = mechanism.build(0)
+    stream = torch.cuda.current_stream(dev)
+    sur, ctxs = None, {}
+    variants = [(v, b) for v, b in VARIANTS if v != "hybrid" or not args.no_surrogate]
+    if not args.no_surrogate:
+        sur, ctxs["hybrid"] = surrogate_leg(args, mech, dev, stream)
     d = workloads.detonation_slice(args.nx, args.ny, seed=1)
     n = d["T"].size
     S = d["Y"].shape[0]
-    ctxs = {v: chem.Context(mech, v) for v, _ in VARIANTS}
+    ctxs.update({v: chem.Context(mech, v) for v, _ in variants if v != "hybrid"})
     T0 = torch.tensor(d["T"], dtype=torch.float64, device=dev)
     p0 = torch.tensor(d["p"], dtype=torch.float64, device=dev)
     Y0 = torch.tensor(d["Y"], dtype=torch.float64, device=dev)
@@ -262,7 +395,7 @@ def run_ours(args, rank, world, local):
     status = torch.empty(n, dtype=torch.int32, device=dev)
     nsteps = torch.empty(n, dtype=torch.int32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    fbmask = torch.empty(n, dtype=torch.uint8, device=dev)
 
     def step(ctx, ev0=None, ev1=None):
         Y.copy_(Y0)
@@ -270,14 +403,18 @@ def run_ours(args, rank, world, local):
         flush.fill_(1.0)
         if ev0 is not None:
             ev0.record(stream)
-        ctx.integrate(rho, e, Y, T, DT, RTOL, ATOL, status=status, nsteps=nsteps, stream=stream)
+        if ctx is ctxs.get("hybrid"):
+            ctx.surrogate_infer(rho, e, Y, T, DT, RTOL, ATOL, status=status, nsteps=nsteps, mask=fbmask,
+                                stream=stream)
+        else:
+            ctx.integrate(rho, e, Y, T, DT, RTOL, ATOL, status=status, nsteps=nsteps, stream=stream)
         if ev1 is not None:
             ev1.record(stream)
 
     clocks = Clocks(local)
     clocks.start()
     res = {}
-    for v, _ in VARIANTS:
+    for v, _ in variants:
         ctx = ctxs[v]
         for _ in range(args.warmup):
             step(ctx)
@@ -302,21 +439,34 @@ def run_ours(args, rank, world, local):
         ns = nsteps.cpu().numpy()
         res[v] = {"elapsed": elapsed, "kernel_ms": kernel_ms, "nsteps": ns,
                   "status": status.cpu().numpy(), "Y": Y.cpu().numpy(), "T": T.cpu().numpy()}
+        if v == "hybrid":
+            res[v]["fallback_frac"] = float(fbmask.float().mean())
     clk = clocks.stop()
 
     ref = res["fp64"]
     summary = {}
-    for v, bound in VARIANTS:
+    for v, bound in variants:
         r = res[v]
         relT = float(np.max(np.abs(r["T"] - ref["T"]) / ref["T"]))
         absY = float(np.max(np.abs(r["Y"] - ref["Y"])))
         if v == "fp64":
             flops = roofline.launch_flops(int(r["nsteps"].sum()), n, mech)
             note = "fp64 pipe; credited flops (exp/log = 20) / CUDA-event launch time"
-        else:
+        elif v == "mixed":
             flops = roofline.launch_flops_mixed_fp64(int(r["nsteps"].sum()), n, mech)
             note = "fp64 pipe; credited fp64 part only (temperature solve, Gibbs, ln Kc, fp64 registers, control)"
-        achieved = flops / (r["kernel_ms"] * 1e-3) / 1e9
+        if v == "hybrid":
+            # the fused network kernel, timed alone on the surrogate leg's rows
+            mk = sur["mlp_kernel"]
+            rl = {"bound": "tensor", "achieved": mk["tflops"], "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+                  "frac": mk["tflops"] / BF16_PEAK_TFLOPS, "traffic": None,
+                  "note": "fused BF16 MLP kernel (mma.sync), timed alone on "
+                          f"{mk['rows']} rows; peak = measured cuBLAS bf16 burst"}
+        else:
+            achieved = flops / (r["kernel_ms"] * 1e-3) / 1e9
+            rl = {"bound": "alu", "achieved": achieved, "peak": roofline.FP64_PEAK_GFLOPS,
+                  "unit": "GFLOP/s", "frac": achieved / roofline.FP64_PEAK_GFLOPS,
+                  "traffic": None, "note": note}
         summary[v] = {
             "value": world * n * args.steps / r["elapsed"], "ms_per_step": 1e3 * r["elapsed"] / args.steps,
             "kernel_ms": r["kernel_ms"], "stated_error_T": bound,
@@ -324,11 +474,11 @@ def run_ours(args, rank, world, local):
             "meets_stated_error": relT <= bound if v != "fp64" else True,
             "attempted_steps": int(r["nsteps"].sum()), "max_steps": int(r["nsteps"].max()),
             "status_ok": int((r["status"] == 0).sum()),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": roofline.FP64_PEAK_GFLOPS,
-                         "unit": "GFLOP/s", "frac": achieved / roofline.FP64_PEAK_GFLOPS,
-                         "traffic": None, "note": note},
+            "roofline": rl,
         }
-    ok = [v for v, _ in VARIANTS if summary[v]["meets_stated_error"]]
+        if v == "hybrid":
+            summary[v]["fallback_frac"] = r["fallback_frac"]
+    ok = [v for v, _ in variants if summary[v]["meets_stated_error"]]
     head = max(ok, key=lambda v: summary[v]["value"])
     H = summary[head]
 
@@ -342,11 +492,27 @@ def run_ours(args, rank, world, local):
     h_ns = torch.empty(n, dtype=torch.int32).pin_memory()
     hY, hT = h_Y.numpy(), h_T.numpy()
 
+    d_rho, d_e = torch.empty_like(rho), torch.empty_like(e)
+    d_Y, d_T = torch.empty_like(Y), torch.empty_like(T)
+
     def e2e_step():
         hY[...] = h_Y0
         hT[...] = h_T0
-        ctx.integrate_host(h_rho.numpy(), h_e.numpy(), hY, hT, DT, RTOL, ATOL,
-                           status=h_st.numpy(), nsteps=h_ns.numpy(), stream=stream)
+        if head == "hybrid":  # no host entry point for the surrogate: copies in the timed region
+            d_rho.copy_(h_rho, non_blocking=True)
+            d_e.copy_(h_e, non_blocking=True)
+            d_Y.copy_(h_Y, non_blocking=True)
+            d_T.copy_(h_T, non_blocking=True)
+            ctx.surrogate_infer(d_rho, d_e, d_Y, d_T, DT, RTOL, ATOL, status=status, nsteps=nsteps,
+                                stream=stream)
+            h_Y.copy_(d_Y, non_blocking=True)
+            h_T.copy_(d_T, non_blocking=True)
+            h_st.copy_(status, non_blocking=True)
+            h_ns.copy_(nsteps, non_blocking=True)
+            torch.cuda.synchronize()
+        else:
+            ctx.integrate_host(h_rho.numpy(), h_e.numpy(), hY, hT, DT, RTOL, ATOL,
+                               status=h_st.numpy(), nsteps=h_ns.numpy(), stream=stream)
 
     e2e_step()
     if world > 1:
@@ -363,7 +529,7 @@ def run_ours(args, rank, world, local):
 
     amr = None
     if not args.no_amr:
-        amr = amr_leg(ctxs[head], max(2, min(args.steps, 3)), dev)
+        amr = amr_leg(ctxs["mixed" if head == "hybrid" else head], max(2, min(args.steps, 3)), dev)
 
     line = None
     if rank == 0:
@@ -376,7 +542,7 @@ def run_ours(args, rank, world, local):
             "metric": METRIC, "value": H["value"], "unit": "cells/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": H["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if head == "fp64" else "f32+f64",
+            "dtype": {"fp64": "f64", "mixed": "f32+f64", "hybrid": "bf16+f32+f64"}[head],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "variant": head, "cells": n,
                        "l2": "flushed between steps (256 MB write)",
@@ -389,8 +555,9 @@ def run_ours(args, rank, world, local):
                     "h2d_bytes_per_step": n * (3 + S) * 8,
                     "d2h_bytes_per_step": n * (1 + S) * 8 + 2 * n * 4,
                     "matches_device_path": e2e_match},
-            "gpu_launches": args.steps * len(VARIANTS),
+            "gpu_launches": args.steps * sum(1 if v != "hybrid" else 4 for v, _ in variants),
             "amr_batch": amr,
+            "surrogate": sur,
             "clocks": clk,
             "cpu_baseline": cpu,
             "parity_vs_oracle_sample": parity,

@@ -262,7 +262,8 @@ int chem_integrate_batched(chem_ctx *ctx, const chem_state *state, int64_t ncell
  * to the change of its Box-Cox-transformed mass fractions over the step.  The paper
  * names learning the chemical source term as future work (Sec. 7).  Inputs (z-scored
  * with training statistics): T, ln p, log10 dt, BC(Y_k) = (max(Y_k, 1e-30)^lam - 1) / lam;
- * outputs: BC(Y_k(t + dt)) - BC(Y_k(t)).  After inference the predicted mass fractions
+ * outputs: BC(Y_k(t + dt)) - BC(Y_k(t)), times (1e-8 s / dt)^dt_power (training option,
+ * stored with the network).  After inference the predicted mass fractions
  * are projected in fp64 onto the element (H, O, N) mass fractions of the input (weighted
  * least squares), the temperature is solved from (e, Y) in fp64, and a gate decides per
  * cell whether the answer stands; rejected cells are integrated by the cell's precision
@@ -288,7 +289,8 @@ typedef struct {
   float lr;             /* [1e-3] Adam learning rate, cosine-decayed to lr_final */
   float lr_final;       /* [lr / 20] */
   float boxcox_lambda;  /* [0.1] */
-  int32_t reserved0;    /* must be zero */
+  float dt_power;       /* [0] targets are the BC increments times (1e-8 s / dt)^dt_power,
+                           so a target is near a rate of change where dt_power = 1 */
   uint64_t seed;        /* weight initialisation and shuffling [0] */
 } chem_train_cfg;
 
@@ -325,8 +327,9 @@ int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
  * cell: features -> network -> inverse transform -> fp64 projection -> fp64 temperature
  * -> gate (feature range, element residual, negativity, temperature solve, |dT|) ->
  * judge: with the integrator's right-hand side F0 = f(Y0), F1 = f(Y1), the trapezoidal
- * corrector Yc = Y0 + dt/2 (F0 + F1) gives the error estimate |T(e, Yc) - T(e, Y1)|,
- * which must not exceed judge_tol * T(e, Y1); and the step must be slow for the cell
+ * defect D = Y1 - Y0 - dt/2 (F0 + F1) gives the temperature-error estimate
+ * sum_k |u_k(T1) - e| |D_k| / c_v(T1), which must not exceed judge_tol * T1 (u_k the
+ * species internal energies per mass); and the step must be slow for the cell
  * (judge_rate), since along a growing mode with dt * lambda = 2 the defect does not
  * see an error.
  * Accepted cells get the projected Y, its T, status CHEM_CELL_OK and nsteps 0; rejected

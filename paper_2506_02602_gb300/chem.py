@@ -90,7 +90,7 @@ class Pairs(C.Structure):
 
 class TrainCfg(C.Structure):
     _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("lr_final", C.c_float),
-                ("boxcox_lambda", C.c_float), ("reserved0", C.c_int32), ("seed", C.c_uint64)]
+                ("boxcox_lambda", C.c_float), ("dt_power", C.c_float), ("seed", C.c_uint64)]
 
 
 class Gate(C.Structure):
@@ -315,7 +315,7 @@ class Context:
 
     # learned surrogate ------------------------------------------------------------
     def surrogate_train(self, rho, e, Y0, dt, Y1, T0=None, epochs=20, batch=4096, lr=1e-3,
-                        lr_final=0.0, boxcox_lambda=0.1, seed=0, stream=None):
+                        lr_final=0.0, boxcox_lambda=0.1, seed=0, dt_power=0.0, stream=None):
         """chem_surrogate_train on CUDA tensors (Y0, Y1: [S, n] planes; dt: [n]).
         Returns the mean loss of every epoch (numpy)."""
         n = rho.numel()
@@ -323,7 +323,7 @@ class Context:
             _check_f64_cuda(nm, t, n)
         pr = Pairs(rho.data_ptr(), e.data_ptr(), Y0.data_ptr(), Y0.stride(0),
                    None if T0 is None else T0.data_ptr(), dt.data_ptr(), Y1.data_ptr(), Y1.stride(0))
-        cfg = TrainCfg(epochs, batch, lr, lr_final, boxcox_lambda, 0, seed)
+        cfg = TrainCfg(epochs, batch, lr, lr_final, boxcox_lambda, dt_power, seed)
         loss = np.zeros(max(epochs, 1), dtype=np.float32)
         self._raise(self.L.chem_surrogate_train(self.h, C.byref(pr), n, C.byref(cfg), _stream(stream),
                                                 loss.ctypes.data_as(C.c_void_p)))

@@ -36,6 +36,7 @@ struct Surrogate {
   float tmean[kSurOut], tistd[kSurOut];
   float *dev_norm = nullptr;  // fmean[16], fistd[16], tmean[16], tistd[16]
   double lam = 0.1;
+  double dt_power = 0.0;
   // inference scratch
   int64_t chunk_cap = 0;
   float *Xraw = nullptr, *O = nullptr;
@@ -294,6 +295,7 @@ static SurrogateConsts make_consts(const Surrogate *s, const chem_surrogate_gate
   c.judge_tol = g.judge_tol;
   c.judge_rate = g.judge_rate;
   c.lam = s->lam;
+  c.dt_power = s->dt_power;
   for (int el = 0; el < 3; ++el)
     for (int k = 0; k < NSP; ++k) c.E[el][k] = mt.Emat[el][k];
   return c;
@@ -433,7 +435,8 @@ int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
   if (cfg.lr == 0.0f) cfg.lr = 1e-3f;
   if (cfg.lr_final == 0.0f) cfg.lr_final = cfg.lr / 20.0f;
   if (cfg.boxcox_lambda == 0.0f) cfg.boxcox_lambda = 0.1f;
-  if (cfg.epochs < 0 || cfg.batch < 1 || !(cfg.lr > 0.0f) || !(cfg.boxcox_lambda > 0.0f) || cfg.reserved0)
+  if (cfg.epochs < 0 || cfg.batch < 1 || !(cfg.lr > 0.0f) || !(cfg.boxcox_lambda > 0.0f) ||
+      !std::isfinite(cfg.dt_power))
     return sur_fail(ctx, CHEM_ERR_INVALID, "invalid training configuration");
   if (!pairs || !pairs->d_rho || !pairs->d_e || !pairs->d_Y0 || !pairs->d_dt || !pairs->d_Y1)
     return sur_fail(ctx, CHEM_ERR_INVALID, "pairs need rho, e, Y0, dt and Y1");
@@ -447,6 +450,7 @@ int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
   cudaStream_t st = (cudaStream_t)stream;
   const MechTables &mt = chem_ctx_tables(ctx);
   s->lam = cfg.boxcox_lambda;
+  s->dt_power = cfg.dt_power;
   s->ready = false;
   std::vector<float> h;
   init_params(s, cfg.seed, h);
@@ -471,7 +475,7 @@ int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
   if (e != cudaSuccess) { cleanup(); return sur_cuda(ctx, e, "allocating training buffers"); }
   // features and targets of every pair, then their statistics
   e = launch_features(mt, n, pairs->d_rho, pairs->d_e, pairs->d_Y0, pairs->ldY0, pairs->d_T0,
-                      pairs->d_dt, 0.0, pairs->d_Y1, pairs->ldY1, s->lam, X, Tg, nullptr, nullptr, st);
+                      pairs->d_dt, 0.0, pairs->d_Y1, pairs->ldY1, s->lam, s->dt_power, X, Tg, nullptr, nullptr, st);
   int hkeys[4 * 32];
   for (int i = 0; i < 32; ++i) {
     hkeys[i] = INT_MAX; hkeys[32 + i] = INT_MIN; hkeys[64 + i] = INT_MAX; hkeys[96 + i] = INT_MIN;
@@ -575,7 +579,7 @@ int chem_surrogate_infer(chem_ctx *ctx, const chem_state *state, int64_t n, doub
   for (int64_t base = 0; base < n && e == cudaSuccess; base += chunk) {
     const int64_t m = (n - base) < chunk ? (n - base) : chunk;
     e = launch_features(mt, m, state->d_rho + base, state->d_e + base, state->d_Y + base, state->ldY,
-                        state->d_T + base, nullptr, dt, nullptr, 0, s->lam, s->Xraw, nullptr, nullptr,
+                        state->d_T + base, nullptr, dt, nullptr, 0, s->lam, s->dt_power, s->Xraw, nullptr, nullptr,
                         s->Tok, st);
     if (e == cudaSuccess) e = mlp_forward(s, m, s->Xraw, s->dev_norm, s->O, st);
     if (e == cudaSuccess)
@@ -596,7 +600,7 @@ int chem_surrogate_infer(chem_ctx *ctx, const chem_state *state, int64_t n, doub
   return e == cudaSuccess ? CHEM_OK : sur_cuda(ctx, e, "surrogate inference");
 }
 
-static const char kSurMagic[8] = {'C', 'H', 'E', 'M', 'S', 'U', 'R', '1'};
+static const char kSurMagic[8] = {'C', 'H', 'E', 'M', 'S', 'U', 'R', '2'};
 
 int chem_surrogate_save(chem_ctx *ctx, const char *path) {
   if (!ctx || !path) return CHEM_ERR_INVALID;
@@ -610,6 +614,7 @@ int chem_surrogate_save(chem_ctx *ctx, const char *path) {
   const int64_t np = kSurParams;
   bool ok = std::fwrite(kSurMagic, 1, 8, f) == 8 && std::fwrite(&np, sizeof np, 1, f) == 1 &&
             std::fwrite(&s->lam, sizeof s->lam, 1, f) == 1 &&
+            std::fwrite(&s->dt_power, sizeof s->dt_power, 1, f) == 1 &&
             std::fwrite(s->fmean, sizeof s->fmean, 1, f) == 1 && std::fwrite(s->fistd, sizeof s->fistd, 1, f) == 1 &&
             std::fwrite(s->fmin, sizeof s->fmin, 1, f) == 1 && std::fwrite(s->fmax, sizeof s->fmax, 1, f) == 1 &&
             std::fwrite(s->tmean, sizeof s->tmean, 1, f) == 1 && std::fwrite(s->tistd, sizeof s->tistd, 1, f) == 1 &&
@@ -624,12 +629,13 @@ int chem_surrogate_load(chem_ctx *ctx, const char *path) {
   if (!f) return sur_fail(ctx, CHEM_ERR_INVALID, std::string("cannot open ") + path);
   char magic[8];
   int64_t np = 0;
-  double lam = 0.0;
+  double lam = 0.0, dt_power = 0.0;
   float fmean[kSurIn], fistd[kSurIn], fmin[kSurFeat], fmax[kSurFeat], tmean[kSurOut], tistd[kSurOut];
   std::vector<float> h((size_t)kSurParams);
   bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kSurMagic, 8) == 0 &&
             std::fread(&np, sizeof np, 1, f) == 1 && np == kSurParams &&
-            std::fread(&lam, sizeof lam, 1, f) == 1 && std::fread(fmean, sizeof fmean, 1, f) == 1 &&
+            std::fread(&lam, sizeof lam, 1, f) == 1 && std::fread(&dt_power, sizeof dt_power, 1, f) == 1 &&
+            std::fread(fmean, sizeof fmean, 1, f) == 1 &&
             std::fread(fistd, sizeof fistd, 1, f) == 1 && std::fread(fmin, sizeof fmin, 1, f) == 1 &&
             std::fread(fmax, sizeof fmax, 1, f) == 1 && std::fread(tmean, sizeof tmean, 1, f) == 1 &&
             std::fread(tistd, sizeof tistd, 1, f) == 1 &&
@@ -640,6 +646,7 @@ int chem_surrogate_load(chem_ctx *ctx, const char *path) {
   Surrogate *s = ensure_surrogate(ctx, &e);
   if (!s) return sur_cuda(ctx, e, "allocating the surrogate");
   s->lam = lam;
+  s->dt_power = dt_power;
   std::memcpy(s->fmean, fmean, sizeof fmean);
   std::memcpy(s->fistd, fistd, sizeof fistd);
   std::memcpy(s->fmin, fmin, sizeof fmin);

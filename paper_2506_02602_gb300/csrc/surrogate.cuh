@@ -22,6 +22,7 @@ constexpr int kSurFeat = 12;
 constexpr int kSurOut = 16;      // 9 outputs, padded
 constexpr int kSurHidden = 256;
 constexpr int kSurLayers = 4;
+constexpr double kSurDtRef = 1e-8;  // s, reference step of the target scaling
 constexpr int kSurN[kSurLayers] = {kSurHidden, kSurHidden, kSurHidden, kSurOut};
 constexpr int kSurK[kSurLayers] = {kSurIn, kSurHidden, kSurHidden, kSurHidden};
 constexpr int64_t kSurParams = (int64_t)kSurHidden * kSurIn + kSurHidden +
@@ -39,12 +40,14 @@ struct SurrogateConsts {
   float judge_tol;                      // largest estimated relative T error (<= 0: no judge)
   float judge_rate;                     // largest dt * relative rate of change (< 0: no bound)
   double lam;                           // Box-Cox lambda
+  double dt_power;                      // targets scaled by (kSurDtRef / dt)^dt_power
   double E[3][NSP];                     // element mass fraction per unit species mass fraction
 };
 
 cudaError_t launch_features(const MechTables &mt, int64_t n, const double *rho, const double *e,
                             const double *Y0, int64_t ld0, const double *T0, const double *dt_cell,
-                            double dt, const double *Y1, int64_t ld1, double lam, float *X, float *Tg,
+                            double dt, const double *Y1, int64_t ld1, double lam, double dt_power,
+                            float *X, float *Tg,
                             double *Tout, uint8_t *ok, cudaStream_t s);
 cudaError_t launch_colstats(int64_t n, int ncol, int ld, const float *A, double *sum, double *sumsq,
                             int *mnkey, int *mxkey, cudaStream_t s);

@@ -5,20 +5,24 @@
 //
 // Features of a cell (12, padded to 16): T, ln p, log10 dt and the Box-Cox transforms
 // BC(Y_k) = (max(Y_k, 1e-30)^lam - 1) / lam of the 9 mass fractions; targets (9, padded
-// to 16): BC(Y_k(t + dt)) - BC(Y_k(t)).  Both are z-scored with training statistics.
+// to 16): (BC(Y_k(t + dt)) - BC(Y_k(t))) (1e-8 s / dt)^dt_power.  Both are z-scored with
+// training statistics.
 // The temperature is always solved from (e, Y) in fp64, so energy is conserved exactly
 // by construction; the projection restores the element (H, O, N) mass fractions, hence
 // sum Y too, in fp64.
 //
 // Error judge: the integrator's own right-hand side checks each candidate result.  With
 // F0 = f(Y0) and F1 = f(Y1) the trapezoidal corrector Yc = Y0 + dt/2 (F0 + F1) differs
-// from the exact solution by O(dt^3 |d3Y/dt3|) where the cell is smooth over dt, so
-// |T(e, Yc) - T(e, Y1)| estimates the temperature error of Y1; a cell whose estimate
-// exceeds judge_tol * T is sent to the integrator.  Stiff cells (dt beyond the fast
-// time scales), where the trapezoidal rule itself is not accurate, fail the check too.
-// Linearised, an error d of Y1 shows in the defect as (I - dt/2 J) d, which vanishes
-// along a growing mode with dt * lambda = 2 (chain branching before ignition), so the
-// judge also bounds the cell's reactivity over the step,
+// from the exact solution by O(dt^3 |d3Y/dt3|) where the cell is smooth over dt, so the
+// defect D = Y1 - Yc estimates the error of Y1.  At constant e the temperature moves by
+// -sum_k (u_k - e) dY_k / c_v for a change dY with sum_k dY_k = 0, so the judge takes
+//   est = sum_k |u_k(T1) - e| |D_k| / c_v(T1)
+// (no cancellation between species counted) and sends a cell with est > judge_tol * T1
+// to the integrator.  Stiff cells (dt beyond the fast time scales), where the
+// trapezoidal rule itself is not accurate, fail the check too.  Linearised, an error d
+// of Y1 shows in the defect as (I - dt/2 J) d, which vanishes along a growing mode with
+// dt * lambda = 2 (chain branching before ignition), so the judge also bounds the
+// cell's reactivity over the step,
 //   dt * max_k max(|F0_k| / (|Y0_k| + 1e-6), |F1_k| / (|Y1_k| + 1e-6)) <= judge_rate,
 // which keeps the factor at or above 1 - judge_rate / 2 (1e-6: the mass fraction below
 // which a species' share of the mixture energy is under ~1 K).
@@ -45,7 +49,8 @@ __device__ __forceinline__ double boxcox_inv_d(double z, double lam) {
 __global__ void k_features(const __grid_constant__ MechTables mt, int64_t n, const double *rho,
                            const double *e, const double *Y0, int64_t ld0, const double *Tg0,
                            const double *dt_cell, double dt_scalar, const double *Y1, int64_t ld1,
-                           double lam, float *X, float *Tg, double *Tout, uint8_t *ok) {
+                           double lam, double dt_power, float *X, float *Tg, double *Tout,
+                           uint8_t *ok) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double yw[NSP], y[NSP];
@@ -76,7 +81,9 @@ __global__ void k_features(const __grid_constant__ MechTables mt, int64_t n, con
   if (Y1) {
     float *t = Tg + i * kSurOut;
 #pragma unroll
-    for (int k = 0; k < NSP; ++k) t[k] = (float)(boxcox_d(Y1[k * ld1 + i], lam) - bc0[k]);
+    const double sc = dt_power == 0.0 ? 1.0 : pow(kSurDtRef / dt, dt_power);
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) t[k] = (float)((boxcox_d(Y1[k * ld1 + i], lam) - bc0[k]) * sc);
 #pragma unroll
     for (int c = NSP; c < kSurOut; ++c) t[c] = 0.0f;
   }
@@ -144,8 +151,8 @@ __global__ void k_normalize(int64_t n, int ncol, int ld, float *A, const float *
 }
 
 // Temperature-error estimate of a surrogate result y1 (see the file comment): returns
-// false if a right-hand side or temperature solve fails, else sets dT = |T(Yc) - T1|
-// and rate = dt * the largest relative rate of change at either end.
+// false if a right-hand side fails, else sets dT = est (K) and rate = dt * the largest
+// relative rate of change at either end.
 // The right-hand sides use the context's variant (fp32 rates in the mixed one).
 template <int V>
 __device__ __noinline__ bool judge_defect(const MechTables &mt, const double (&y0)[NSP],
@@ -174,17 +181,24 @@ __device__ __noinline__ bool judge_defect(const MechTables &mt, const double (&y
     ok = cell_rhs(mt, y0, rho, invRho, eR, Ta, F0) && cell_rhs(mt, y1, rho, invRho, eR, Tb, F1);
   }
   if (!ok) return false;
-  double yw[NSP], r = 0.0;
+  const int range = T1 >= mt.T_mid;
+  double yw[NSP], m[6], d[5], r = 0.0, s = 0.0;
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) yw[k] = y1[k] * mt.invW[k];
+  mix_ecoef(mt, range, yw, m);
+  cv_coef(m, d);
+  const double cvR = cv_over_R(d, T1);
 #pragma unroll
   for (int k = 0; k < NSP; ++k) {
-    yw[k] = (y0[k] + 0.5 * dt * (F0[k] + F1[k])) * mt.invW[k];
+    const double *c = mt.ec[range][k];
+    const double ukR = fma(T1, fma(T1, fma(T1, fma(T1, fma(T1, c[4], c[3]), c[2]), c[1]), c[0]), c[5]) * mt.invW[k];
+    const double defect = y1[k] - (y0[k] + 0.5 * dt * (F0[k] + F1[k]));
+    s = fma(fabs(ukR - eR), fabs(defect), s);
     r = fmax(r, fmax(fabs(F0[k]) / (fabs(y0[k]) + 1e-6), fabs(F1[k]) / (fabs(y1[k]) + 1e-6)));
   }
   rate = dt * r;
-  double Tc = T1;
-  if (!solve_T(mt, yw, eR, Tc)) return false;
-  dT = fabs(Tc - T1);
-  return isfinite(dT);
+  dT = s / cvR;
+  return isfinite(dT) && cvR > 0.0;
 }
 
 // The inference epilogue, one thread per cell.  Takes the network output O [n x 16]
@@ -212,10 +226,11 @@ __global__ void __launch_bounds__(128)
     accept &= x[c] >= sc.fmin[c] - w && x[c] <= sc.fmax[c] + w;
   }
   double y0[NSP], y1[NSP];
+  const double unscale = sc.dt_power == 0.0 ? 1.0 : pow(dt / kSurDtRef, sc.dt_power);
 #pragma unroll
   for (int k = 0; k < NSP; ++k) {
     y0[k] = Y[k * ld + i];
-    const double d = (double)o[k] * sc.tstd[k] + sc.tmean[k];
+    const double d = ((double)o[k] * sc.tstd[k] + sc.tmean[k]) * unscale;
     y1[k] = boxcox_inv_d((double)x[3 + k] + d, sc.lam);
   }
   // element mass fractions before projection and the residual
@@ -375,10 +390,11 @@ cudaError_t launch_surrogate_stats(chem_stats *st, int64_t n, const unsigned int
 
 cudaError_t launch_features(const MechTables &mt, int64_t n, const double *rho, const double *e,
                             const double *Y0, int64_t ld0, const double *T0, const double *dt_cell,
-                            double dt, const double *Y1, int64_t ld1, double lam, float *X, float *Tg,
+                            double dt, const double *Y1, int64_t ld1, double lam, double dt_power,
+                            float *X, float *Tg,
                             double *Tout, uint8_t *ok, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_features<<<nblk(n, 128), 128, 0, s>>>(mt, n, rho, e, Y0, ld0, T0, dt_cell, dt, Y1, ld1, lam, X, Tg,
+  k_features<<<nblk(n, 128), 128, 0, s>>>(mt, n, rho, e, Y0, ld0, T0, dt_cell, dt, Y1, ld1, lam, dt_power, X, Tg,
                                           Tout, ok);
   return cudaGetLastError();
 }

@@ -2,11 +2,12 @@
 
 Data recipe (0D ignition trajectories): initial states phi ~ U[0.5, 2], T0 ~ U[900, 2200] K,
 p ~ U[1, 30] atm (chem_inputs.workloads.trajectory_starts).  Every trajectory is integrated
-on the GPU with the FP64 integrator over a logarithmic time grid, recording the state at
-each grid point, up to its ignition (first time T exceeds T0 + 400 K); the grid interval
-holding the ignition is then re-recorded at a fine per-trajectory spacing, followed by a
-short post-ignition window (trajectory_states).  Each recorded state then gets a step dt ~ log-uniform [1e-9, 1e-7] s and is integrated over
-it (the batched integrator, one box per cell), giving a (state, dt) -> state pair.
+on the GPU with the FP64 integrator over a logarithmic time grid, recording the initial
+state and the state at each grid point up to its ignition (first time T exceeds
+T0 + 400 K); the grid interval holding the ignition is then re-recorded at a fine
+per-trajectory spacing, followed by a short post-ignition window (trajectory_states).
+Each recorded state then gets a step dt ~ log-uniform [1e-9, 1e-7] s and is integrated
+over it (the batched integrator, one box per cell), giving a (state, dt) -> state pair.
 
 Everything that computes runs in libchem's kernels; torch gathers and stores arrays.
 """
@@ -22,8 +23,9 @@ def trajectory_states(ctx, ntraj, seed=3, nstage=48, t0=1e-9, t_end=3e-3, nfine=
     """States along ntraj ignition trajectories (dict of CUDA tensors rho, e, Y [S, m], T,
     plus the trajectory id and time of each state).
 
-    Pass 1 integrates every trajectory over a logarithmic time grid (one dt for all) and
-    records the states until the grid interval [t_lo, t_hi] in which T first exceeds
+    Pass 1 records the initial state, integrates every trajectory over a logarithmic time
+    grid (one dt for all) and records the states until the grid interval [t_lo, t_hi] in
+    which T first exceeds
     T0 + 400 K, or the integration stops at ctx's step limit (the interval is stiff).
     Pass 2 restarts each such trajectory at t_lo and records nfine equal sub-intervals of
     its own [t_lo, t_hi] (the ignition transient), then npost intervals of post / npost
@@ -46,6 +48,8 @@ def trajectory_states(ctx, ntraj, seed=3, nstage=48, t0=1e-9, t_end=3e-3, nfine=
         out["rho"].append(r); out["e"].append(en); out["Y"].append(Ya); out["T"].append(Ta)
         out["traj"].append(idx); out["t"].append(t)
 
+    # the initial states (radical free) are states of the trajectories too
+    record(active.clone(), rho, e, Y.clone(), T.clone(), torch.zeros_like(T))
     ign_idx, ign_lo, ign_hi = [], [], []
     for j in range(nstage):
         if active.numel() == 0:
