@@ -190,6 +190,10 @@ def run_reference(args, rank, world):
 # ----------------------------------------------------------------- GPU leg
 VARIANTS = (("fp64", 0.0), ("mixed", 1e-5), ("hybrid", 1e-3))  # (variant, stated error bound on T vs FP64)
 MLP_FLOPS_PER_ROW = 2 * (16 * 256 + 256 * 256 * 2 + 256 * 16)  # padded 16-256-256-256-16 network
+# DRAM bytes (read + write) per cell of one k_lsrk launch, from an ncu capture of the
+# 131,072-cell slice (profiles/k_lsrk_detonation_slice.md), scaled by the cell count;
+# to be set to None whenever the kernel changes until it is captured again.
+TRAFFIC_PER_CELL = {"fp64": 12.742144e6 / 131072, "mixed": 12.701952e6 / 131072}
 
 
 def _bf16_peak():
@@ -464,9 +468,11 @@ def run_ours(args, rank, world, local):
                           f"{mk['rows']} rows; peak = measured cuBLAS bf16 burst"}
         else:
             achieved = flops / (r["kernel_ms"] * 1e-3) / 1e9
+            tpc = TRAFFIC_PER_CELL.get(v)
             rl = {"bound": "alu", "achieved": achieved, "peak": roofline.FP64_PEAK_GFLOPS,
                   "unit": "GFLOP/s", "frac": achieved / roofline.FP64_PEAK_GFLOPS,
-                  "traffic": None, "note": note}
+                  "traffic": None if tpc is None else tpc * n, "note": note +
+                  "; traffic = ncu DRAM bytes per cell on a 131,072-cell slice x cells"}
         summary[v] = {
             "value": world * n * args.steps / r["elapsed"], "ms_per_step": 1e3 * r["elapsed"] / args.steps,
             "kernel_ms": r["kernel_ms"], "stated_error_T": bound,
