@@ -78,6 +78,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(vals, world, device):
+    """Element-wise maximum of a list of floats over all ranks (the slowest rank's
+    timings); the identity for one rank."""
+    if world <= 1:
+        return [float(v) for v in vals]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def job_rate(world, cells_per_rank, steps, elapsed):
+    """Whole-job throughput: every rank integrates its own cells_per_rank each step
+    (weak scaling), timed by the slowest rank."""
+    return world * cells_per_rank * steps / elapsed
+
+
 # ----------------------------------------------------------------- clocks sampler
 class Clocks:
     """nvidia-smi sampling during the timed region (every 200 ms)."""
@@ -436,10 +454,7 @@ def run_ours(args, rank, world, local):
             torch.distributed.barrier()
         elapsed = time.perf_counter() - t0
         kernel_ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
-        if world > 1:
-            t = torch.tensor([elapsed, kernel_ms], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            elapsed, kernel_ms = float(t[0]), float(t[1])
+        elapsed, kernel_ms = max_over_ranks([elapsed, kernel_ms], world, dev)
         ns = nsteps.cpu().numpy()
         res[v] = {"elapsed": elapsed, "kernel_ms": kernel_ms, "nsteps": ns,
                   "status": status.cpu().numpy(), "Y": Y.cpu().numpy(), "T": T.cpu().numpy()}
@@ -474,7 +489,7 @@ def run_ours(args, rank, world, local):
                   "traffic": None if tpc is None else tpc * n, "note": note +
                   "; traffic = ncu DRAM bytes per cell on a 131,072-cell slice x cells"}
         summary[v] = {
-            "value": world * n * args.steps / r["elapsed"], "ms_per_step": 1e3 * r["elapsed"] / args.steps,
+            "value": job_rate(world, n, args.steps, r["elapsed"]), "ms_per_step": 1e3 * r["elapsed"] / args.steps,
             "kernel_ms": r["kernel_ms"], "stated_error_T": bound,
             "error_vs_fp64_gpu": {"max_rel_T": relT, "max_abs_Y": absY},
             "meets_stated_error": relT <= bound if v != "fp64" else True,
@@ -527,10 +542,7 @@ def run_ours(args, rank, world, local):
     for _ in range(args.steps):
         e2e_step()
     e2e_el = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_el], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_el = float(t[0])
+    e2e_el, = max_over_ranks([e2e_el], world, dev)
     e2e_match = bool(np.array_equal(hY, res[head]["Y"]) and np.array_equal(hT, res[head]["T"]))
 
     amr = None
@@ -557,7 +569,7 @@ def run_ours(args, rank, world, local):
             "roofline": H["roofline"],
             "variants": {v: {k: x for k, x in summary[v].items() if k != "roofline"} |
                          {"roofline_frac": summary[v]["roofline"]["frac"]} for v in summary},
-            "e2e": {"value": world * n * args.steps / e2e_el, "unit": "cells/s",
+            "e2e": {"value": job_rate(world, n, args.steps, e2e_el), "unit": "cells/s",
                     "h2d_bytes_per_step": n * (3 + S) * 8,
                     "d2h_bytes_per_step": n * (1 + S) * 8 + 2 * n * 4,
                     "matches_device_path": e2e_match},
