@@ -313,9 +313,13 @@ typedef struct {
 
 /* Adaptive integration of y' = f(y) over [0, dt] with the Eq. 22 controller.
  * Optional logs (h, err, accepted) of every attempted step. */
+/* on_event (nullable) is told when an attempt begins (0) and when one is rejected (1),
+ * so that a right-hand side with state of its own (the temperature warm start of a
+ * chemistry cell) can return it to the accepted state together with X. */
 static void integrate_adaptive(int n, rhs_fn f, void *ctx, double dt, double rtol, double atol,
                                double h0, int32_t max_steps, double *X, adapt_out *out,
-                               double *log_h, double *log_err, int32_t *log_acc, int32_t max_log) {
+                               double *log_h, double *log_err, int32_t *log_acc, int32_t max_log,
+                               void (*on_event)(void *ctx, int ev)) {
   double t = 0.0, h = (h0 > 0.0) ? h0 : dt;
   double Xs[OR_MAXN], E[OR_MAXN];
   out->status = 0; out->nacc = 0; out->nrej = 0; out->margin = INFINITY; out->h_next = h;
@@ -325,6 +329,7 @@ static void integrate_adaptive(int n, rhs_fn f, void *ctx, double dt, double rto
     if (h > dt - t) h = dt - t;
     for (int i = 0; i < n; ++i) Xs[i] = X[i];
     int k = out->nacc + out->nrej;
+    if (on_event) on_event(ctx, 0);
     /* A trial stage (2..5) whose RHS fails (no temperature root) or an error estimate
      * that is not finite rejects the attempt with the smallest factor 1/5; a failure
      * at stage 1, the accepted state itself, ends the cell with status 3. */
@@ -337,6 +342,7 @@ static void integrate_adaptive(int n, rhs_fn f, void *ctx, double dt, double rto
     double err = failed ? NAN : wrms(n, E, Xs, X, rtol, atol);
     if (!isfinite(err)) {
       for (int i = 0; i < n; ++i) X[i] = Xs[i];
+      if (on_event) on_event(ctx, 1);
       if (k < max_log) { log_h[k] = h; log_err[k] = err; log_acc[k] = 0; }
       out->nrej++;
       h = h * 0.2;
@@ -350,6 +356,7 @@ static void integrate_adaptive(int n, rhs_fn f, void *ctx, double dt, double rto
       out->nacc++;
     } else {
       for (int i = 0; i < n; ++i) X[i] = Xs[i];
+      if (on_event) on_event(ctx, 1);
       out->nrej++;
     }
     h = h * fac;
@@ -386,7 +393,7 @@ int32_t oracle_linear_integrate(int32_t n, const double *M, double *y, double dt
   linear_ctx c = {n, M};
   adapt_out o;
   integrate_adaptive(n, linear_rhs, &c, dt, rtol, atol, h0, max_steps, y, &o, log_h, log_err,
-                     log_acc, max_log);
+                     log_acc, max_log, NULL);
   out3[0] = o.status; out3[1] = o.nacc; out3[2] = o.nrej;
   return o.nacc + o.nrej;
 }
@@ -413,7 +420,18 @@ double oracle_quadratic_fixed(double y0, double h, int32_t nsteps, int32_t embed
 typedef struct {
   const omech *m;
   double rho, e, T;  /* T: last Newton result, the next warm start */
+  double T_acc;      /* temperature of the accepted state (stage 1 of the attempt) */
+  int first;         /* the next evaluation is stage 1 of an attempt */
 } chem_cell;
+
+/* A rejected attempt returns the cell to its accepted state: X (restored by the
+ * integrator) and the temperature warm start with it, so the next Newton solve starts
+ * from that state's own temperature, not from a trial stage's. */
+static void chem_event(void *vctx, int ev) {
+  chem_cell *cc = (chem_cell *)vctx;
+  if (ev == 0) cc->first = 1;
+  else cc->T = cc->T_acc;
+}
 
 /* dY_k/dt = W_k wdot_k / rho at fixed (rho, e); T from Newton on (e, Y). */
 static int chem_rhs(void *vctx, const double *Y, double *F) {
@@ -421,6 +439,7 @@ static int chem_rhs(void *vctx, const double *Y, double *F) {
   double T, w[OR_MAXSP];
   if (oracle_T_from_e(cc->m, Y, cc->e, cc->T, &T, NULL)) return 1;
   cc->T = T;
+  if (cc->first) { cc->T_acc = T; cc->first = 0; }
   oracle_wdot(cc->m, cc->rho, T, Y, w);
   for (int k = 0; k < cc->m->nsp; ++k) F[k] = cc->m->W[k] * w[k] / cc->rho;
   return 0;
@@ -429,7 +448,7 @@ static int chem_rhs(void *vctx, const double *Y, double *F) {
 /* dY/dt of one cell at (rho, e, Y), T solved from Tguess; the solved T is returned. */
 double oracle_chem_rhs(const omech *m, double rho, double e, const double *Y, double Tguess,
                        double *F) {
-  chem_cell cc = {m, rho, e, Tguess};
+  chem_cell cc = {m, rho, e, Tguess, Tguess, 0};
   if (chem_rhs(&cc, Y, F)) return NAN;
   return cc.T;
 }
@@ -452,7 +471,7 @@ int32_t oracle_integrate(const omech *m, int64_t n, const double *rho, const dou
   for (int64_t i = 0; i < n; ++i) {
     double X[OR_MAXN];
     for (int k = 0; k < m->nsp; ++k) X[k] = Y[k * ldY + i];
-    chem_cell cc = {m, rho[i], e[i], T[i]};
+    chem_cell cc = {m, rho[i], e[i], T[i], T[i], 0};
     adapt_out o;
     int bad_input = !(isfinite(rho[i]) && rho[i] > 0.0 && isfinite(e[i]));
     for (int k = 0; k < m->nsp; ++k) bad_input |= !isfinite(X[k]);
@@ -462,7 +481,7 @@ int32_t oracle_integrate(const omech *m, int64_t n, const double *rho, const dou
     } else {
       double hi = (h0 && isfinite(h0[i]) && h0[i] > 0.0) ? h0[i] : 0.0;
       integrate_adaptive(m->nsp, chem_rhs, &cc, dt, rtol, atol, hi, max_steps, X,
-                         &o, NULL, NULL, NULL, 0);
+                         &o, NULL, NULL, NULL, 0, chem_event);
     }
     double Tout = NAN;
     if (o.status != 4 && oracle_T_from_e(m, X, e[i], cc.T, &Tout, NULL) != 0) {
@@ -484,7 +503,7 @@ int32_t oracle_integrate(const omech *m, int64_t n, const double *rho, const dou
  * T after every step in T_trace[nsteps]; used for the step-halving ignition-delay check. */
 int32_t oracle_chem_fixed(const omech *m, double rho, double e, double *Y, double Tguess, double h,
                           int32_t nsteps, double *T_trace) {
-  chem_cell cc = {m, rho, e, Tguess};
+  chem_cell cc = {m, rho, e, Tguess, Tguess, 0};
   double E[OR_MAXN];
   for (int s = 0; s < nsteps; ++s) {
     if (lsrk_step(m->nsp, chem_rhs, &cc, h, Y, E)) return 3;

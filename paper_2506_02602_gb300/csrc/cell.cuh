@@ -97,6 +97,7 @@ __device__ __forceinline__ void cell_attempt(const MechTables &mt, CellState &c,
 #pragma unroll
   for (int k = 0; k < NSP; ++k) { Xs[k] = c.X[k]; U[k] = (SReal)c.X[k]; E[k] = 0.0; }
   int failed = 0;
+  double Tacc = c.T;  // temperature of the accepted state, set by stage 1
 #pragma unroll 1
   for (int s = 0; s < 5; ++s) {
     SReal F[NSP];
@@ -105,6 +106,7 @@ __device__ __forceinline__ void cell_attempt(const MechTables &mt, CellState &c,
     if constexpr (kMixed) ok = cell_rhs_mixed(mt, U, c.rho_f, c.invRho_f, c.eR, c.T, F);
     else ok = cell_rhs(mt, U, c.rho, c.invRho, c.eR, c.T, F);
     if (!ok) { failed = s + 1; break; }
+    if (s == 0) Tacc = c.T;
     const double ha = h * c_ls_a[s], hb = h * c_ls_b[s], he = h * c_ls_e[s];
     if constexpr (kMixed) {
       const float ha_f = (float)ha;
@@ -141,9 +143,13 @@ __device__ __forceinline__ void cell_attempt(const MechTables &mt, CellState &c,
     }
     err = sqrt(sum * (1.0 / NSP));
   }
+  // a rejected attempt returns the cell to its accepted state, the temperature warm
+  // start included (a trial stage's temperature can sit near another root of e(T) of the
+  // extrapolated polynomials)
   if (!isfinite(err)) {
 #pragma unroll
     for (int k = 0; k < NSP; ++k) c.X[k] = Xs[k];
+    c.T = Tacc;
     ++c.nrej;
     c.h = h * 0.2;
     return;
@@ -155,6 +161,7 @@ __device__ __forceinline__ void cell_attempt(const MechTables &mt, CellState &c,
   } else {
 #pragma unroll
     for (int k = 0; k < NSP; ++k) c.X[k] = Xs[k];
+    c.T = Tacc;
     ++c.nrej;
   }
   c.h = h * fac;

@@ -128,3 +128,26 @@ def test_initial_step_option():
     b = O.integrate(rho, e, r["Y"], r["T"], 1e-7, h0=np.full(64, 1e-9))
     np.testing.assert_allclose(a["T"], b["T"], rtol=1e-8)
     assert np.all(b["nsteps"] >= 1)
+
+
+def test_rejected_attempts_restore_the_temperature_start():
+    """A long first step on hot burnt gas (2870-2910 K, 7-9 atm) is rejected several
+    times; the trial stages of those attempts reach temperatures where the extrapolated
+    NASA-7 e(T) has another root (~14,500 K).  A rejection returns the cell to its
+    accepted state, the Newton starting temperature included, so one call over 2e-7 s
+    must land where 40 calls over 5e-9 s land (without the restore the cell ran to
+    20,600 K and stopped with h underflow)."""
+    b = W.amr_batch(nboxes=40, seed=22, edges=(2, 3, 4))
+    idx = np.array([87, 104, 163, 367])
+    T0, p, Y0 = b["T"][idx], b["p"][idx], b["Y"][:, idx]
+    rho, e = O.state_from_TPY(T0, p, Y0)
+    one = O.integrate(rho, e, Y0, T0, 2e-7)
+    Y, T = Y0.copy(), T0.copy()
+    for _ in range(40):
+        r = O.integrate(rho, e, Y, T, 5e-9)
+        Y, T = r["Y"], r["T"]
+        assert np.all(r["status"] == 0)
+    assert np.all(one["status"] == 0)
+    assert np.all(one["T"] < 3100.0)
+    np.testing.assert_allclose(one["T"], T, rtol=1e-6)
+    np.testing.assert_allclose(one["Y"], Y, atol=1e-6)
