@@ -211,7 +211,7 @@ MLP_FLOPS_PER_ROW = 2 * (16 * 256 + 256 * 256 * 2 + 256 * 16)  # padded 16-256-2
 # DRAM bytes (read + write) per cell of one k_lsrk launch, from an ncu capture of the
 # 131,072-cell slice (profiles/k_lsrk_detonation_slice.md), scaled by the cell count;
 # to be set to None whenever the kernel changes until it is captured again.
-TRAFFIC_PER_CELL = {"fp64": 12.742144e6 / 131072, "mixed": 12.701952e6 / 131072}
+TRAFFIC_PER_CELL = {"fp64": None, "mixed": None}
 
 
 def _bf16_peak():
@@ -330,10 +330,11 @@ def surrogate_leg(args, mech, dev, stream):
 
 def amr_leg(ctx, steps, dev):
     """Ragged AMR-like batch (256 boxes, edges {8,16,24,32}^3, 3 levels with 2^l substeps
-    of 1e-7/2^l s, heavy-tailed stiffness): the persistent work-stealing launch against
-    the plain path of one chem_integrate launch per box and substep on 8 streams (one
-    stream per box, round robin).  Both run the same per-cell arithmetic, so their
-    results must be bit-identical."""
+    of 1e-7/2^l s, heavy-tailed stiffness): the persistent work-stealing launch, with the
+    options chem_autotune_batched picks on this batch, against the plain path of one
+    chem_integrate launch per box and substep on 8 streams (one stream per box, round
+    robin).  Both run the same per-cell arithmetic, so their results must be
+    bit-identical."""
     import torch
     from chem_inputs import workloads
     b = workloads.amr_batch()
@@ -351,13 +352,22 @@ def amr_leg(ctx, steps, dev):
     ns = torch.empty(n, dtype=torch.int32, device=dev)
     streams = [torch.cuda.Stream(dev) for _ in range(8)]
 
-    def persistent():
+    def persistent(**opts):
         Y.copy_(Y0); T.copy_(T0); h.fill_(float("nan"))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.integrate_batched(rho, e, Y, T, off, dts, nsub, RTOL, ATOL, h=h, nsteps=ns)
+        ctx.integrate_batched(rho, e, Y, T, off, dts, nsub, RTOL, ATOL, h=h, nsteps=ns, **opts)
         torch.cuda.synchronize()
         return time.perf_counter() - t0
+
+    # the autotuner on this batch (its own copies of the state; no cache file)
+    h.fill_(float("nan"))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tuned, table = ctx.autotune_batched(rho, e, Y0, T0, off, dts, nsub, RTOL, ATOL, h=h)
+    t_tune = time.perf_counter() - t0
+    persistent()
+    t_default = min(persistent() for _ in range(steps))
 
     def per_box():
         Y.copy_(Y0); T.copy_(T0); h.fill_(float("nan"))
@@ -372,8 +382,8 @@ def amr_leg(ctx, steps, dev):
         torch.cuda.synchronize()
         return time.perf_counter() - t0
 
-    persistent()
-    tp = min(persistent() for _ in range(steps))
+    persistent(**tuned)
+    tp = min(persistent(**tuned) for _ in range(steps))
     Yp, Tp, steps_p = Y.cpu().numpy(), T.cpu().numpy(), ns.cpu().numpy()
     per_box()
     tb = min(per_box() for _ in range(steps))
@@ -382,6 +392,10 @@ def amr_leg(ctx, steps, dev):
     return {"workload": f"AMR-like batch: 256 boxes, {n} cells, {subs} cell-substeps, 3 levels",
             "variant": ctx.variant,
             "persistent_cells_per_s": n / tp, "persistent_ms": 1e3 * tp,
+            "autotuned": {"options": tuned, "default_options_ms": 1e3 * t_default, "tuned_ms": 1e3 * tp,
+                          "tuning_s": t_tune,
+                          "candidates": [{k: r[k] for k in ("shape", "block", "regs", "ctas_per_sm", "order",
+                                                            "use_graph", "ms")} for r in table]},
             "per_box_cells_per_s": n / tb, "per_box_ms": 1e3 * tb,
             "speedup": tb / tp, "cell_substeps_per_s": subs / tp,
             "attempted_steps": int(steps_p.sum()), "max_steps": int(steps_p.max()),

@@ -224,13 +224,22 @@ typedef struct {
   const int32_t *d_box_nsub;
 } chem_batch;
 
+/* Compiled shapes of the persistent kernel: (threads per CTA, minimum resident CTAs
+ * per SM, hence a register cap of min(255, 65536 / (threads * CTAs))):
+ * 0 = (128, 2) [default, no cap in effect], 1 = (128, 3), 2 = (128, 4), 3 = (64, 6),
+ * 4 = (64, 8), 5 = (256, 2).  All run the same algorithm; the compiler contracts
+ * multiply-adds per compiled kernel, so results of different shapes agree to rounding
+ * (to the integration tolerance in ill-conditioned cells), not bit for bit.  Shape 0
+ * gives the results of chem_integrate. */
+#define CHEM_BATCH_SHAPES 6
+
 /* Options of chem_integrate_batched.  Zero-initialised = the defaults. */
 typedef struct {
   int32_t order;               /* chem_queue_order [CHEM_ORDER_STIFFNESS] */
   int32_t ctas_per_sm;         /* persistent CTAs per SM; 0 = all that fit [0] */
   int32_t use_graph;           /* 1: capture the call's launches in a CUDA graph and
                                   replay it while the arguments are unchanged [0] */
-  int32_t reserved;            /* must be zero */
+  int32_t shape;               /* persistent-kernel shape, 0 .. CHEM_BATCH_SHAPES-1 [0] */
   const int32_t *d_cost_hint;  /* nullable device [ncells]: per-cell cost used as the
                                   stiffness key instead of the probe (e.g. d_nsteps of
                                   the previous call) */
@@ -248,12 +257,50 @@ typedef struct {
  * depend on the queue order.  The context owns the queue scratch (5 bytes per cell plus
  * 520 bytes), allocated on the first call that needs more: make one uncaptured call of
  * the largest size before capturing calls in a CUDA graph.  opt may be NULL.
- * Errors: as chem_integrate, plus nboxes < 1, NULL box arrays, unknown order, nonzero
- * reserved -> CHEM_ERR_INVALID; allocation failure -> CHEM_ERR_NOMEM.  Asynchronous.
+ * Errors: as chem_integrate, plus nboxes < 1, NULL box arrays, unknown order, shape out
+ * of range, ctas_per_sm < 0 -> CHEM_ERR_INVALID; allocation failure -> CHEM_ERR_NOMEM.
+ * Asynchronous.
  */
 int chem_integrate_batched(chem_ctx *ctx, const chem_state *state, int64_t ncells,
                            const chem_batch *batch, double rtol, double atol,
                            const chem_batch_options *opt, void *stream, chem_stats *d_stats);
+
+/* Threads per CTA, registers per thread and resident CTAs per SM of a persistent-kernel
+ * shape in the context's variant (outputs nullable).  Errors: shape out of range ->
+ * CHEM_ERR_INVALID; CUDA -> CHEM_ERR_CUDA. */
+int chem_batch_shape_info(chem_ctx *ctx, int32_t shape, int32_t *block, int32_t *regs,
+                          int32_t *ctas_per_sm);
+
+/* One timed candidate of chem_autotune_batched. */
+typedef struct {
+  chem_batch_options opt;  /* the candidate */
+  float ms;                /* best of two timed launches (after one untimed), ms */
+  int32_t block;           /* threads per CTA of its shape */
+  int32_t regs;            /* registers per thread of its shape */
+  int32_t ctas_per_sm;     /* resident CTAs per SM it ran with */
+} chem_tune_result;
+
+/*
+ * Autotuner of chem_integrate_batched (no counterpart in the paper, which sizes boxes
+ * and streams by hand, Sec. 4.1.2).  Times candidate options on the caller's own batch,
+ * integrating private copies of Y, T (and h): the caller's state is not modified.
+ * Coordinate descent: every shape (stiffness order, all resident CTAs), then the
+ * natural order, then fewer CTAs per SM, then graph replay, each step keeping the
+ * fastest.  *best receives the fastest options (base's d_cost_hint kept; base may be
+ * NULL).  h_results (nullable, host [max_results]) receives the timed candidates and
+ * *n_results their count.
+ * cache_path (nullable): a text file of earlier results, one line per key (device name,
+ * SM count, variant, max_steps, rtol, atol, floor(log2 ncells), floor(log2 nboxes));
+ * on a hit *best comes from the file, nothing is launched and *n_results = 0; on a miss
+ * the result is appended.  Synchronous; allocates the copies for the duration of the
+ * call.  Errors: as chem_integrate_batched; unreadable cache lines are skipped; a cache
+ * file that cannot be written -> CHEM_ERR_INVALID after *best is set.
+ */
+int chem_autotune_batched(chem_ctx *ctx, const chem_state *state, int64_t ncells,
+                          const chem_batch *batch, double rtol, double atol,
+                          const chem_batch_options *base, const char *cache_path, void *stream,
+                          chem_batch_options *best, chem_tune_result *h_results,
+                          int32_t max_results, int32_t *n_results);
 
 /* ---------------------------------------------------------------- learned surrogate
  *
@@ -393,7 +440,8 @@ int chem_surrogate_forward(chem_ctx *ctx, const float *d_X, int64_t B, float *d_
  * Limits and rules:
  *   - At most 1,048,576 cells per call. Larger ncells returns CHEM_ERR_INVALID with a
  *     message, before anything is launched.
- *   - opt->use_graph is ignored: the launches go straight to the stream.
+ *   - opt->use_graph is ignored: the launches go straight to the stream; opt->shape is
+ *     honoured.
  *   - Set-up: the first call on each device looks up the array's device address, with
  *     that device current. Make that first call outside any stream capture.
  *   - Every call on a device shares the one array. Each call clears the parts that must

@@ -80,7 +80,15 @@ class Batch(C.Structure):
 
 class BatchOptions(C.Structure):
     _fields_ = [("order", C.c_int32), ("ctas_per_sm", C.c_int32), ("use_graph", C.c_int32),
-                ("reserved", C.c_int32), ("d_cost_hint", C.c_void_p)]
+                ("shape", C.c_int32), ("d_cost_hint", C.c_void_p)]
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("opt", BatchOptions), ("ms", C.c_float), ("block", C.c_int32), ("regs", C.c_int32),
+                ("ctas_per_sm", C.c_int32)]
+
+
+BATCH_SHAPES = 6
 
 
 class Pairs(C.Structure):
@@ -125,6 +133,10 @@ def load() -> C.CDLL:
         "chem_diag_math": (C.c_int, [C.c_int, i64, vp, vp, vp]),
         "chem_integrate_batched": (C.c_int, [vp, C.POINTER(State), i64, C.POINTER(Batch), dbl, dbl,
                                              C.POINTER(BatchOptions), vp, vp]),
+        "chem_batch_shape_info": (C.c_int, [vp, C.c_int32, vp, vp, vp]),
+        "chem_autotune_batched": (C.c_int, [vp, C.POINTER(State), i64, C.POINTER(Batch), dbl, dbl,
+                                            C.POINTER(BatchOptions), C.c_char_p, vp, C.POINTER(BatchOptions),
+                                            vp, C.c_int32, vp]),
         "chem_surrogate_param_count": (C.c_int64, []),
         "chem_surrogate_train": (C.c_int, [vp, C.POINTER(Pairs), i64, C.POINTER(TrainCfg), vp, vp]),
         "chem_surrogate_infer": (C.c_int, [vp, C.POINTER(State), i64, dbl, dbl, dbl, C.POINTER(Gate),
@@ -268,7 +280,7 @@ class Context:
 
     def integrate_batched(self, rho, e, Y, T, box_offset, box_dt, box_nsub, rtol=1e-6, atol=1e-10,
                           h=None, status=None, nsteps=None, stats=None, order=ORDER_STIFFNESS,
-                          ctas_per_sm=0, use_graph=False, cost_hint=None, stream=None):
+                          ctas_per_sm=0, use_graph=False, cost_hint=None, stream=None, shape=0):
         """chem_integrate_batched: box_offset (int64 [nb+1]), box_dt (float64 [nb]) and
         box_nsub (int32 [nb]) are CUDA tensors; the state tensors are as in integrate."""
         import torch
@@ -282,15 +294,44 @@ class Context:
                    None if status is None else status.data_ptr(),
                    None if nsteps is None else nsteps.data_ptr())
         b = Batch(box_dt.numel(), box_offset.data_ptr(), box_dt.data_ptr(), box_nsub.data_ptr())
-        o = BatchOptions(order, ctas_per_sm, int(bool(use_graph)), 0,
+        o = BatchOptions(order, ctas_per_sm, int(bool(use_graph)), shape,
                          None if cost_hint is None else cost_hint.data_ptr())
         self._raise(self.L.chem_integrate_batched(self.h, C.byref(st), n, C.byref(b), float(rtol),
                                                   float(atol), C.byref(o), _stream(stream), _ptr(stats)))
 
+    def batch_shape_info(self, shape):
+        """chem_batch_shape_info: (threads per CTA, registers per thread, CTAs per SM)."""
+        blk, regs, per = C.c_int32(), C.c_int32(), C.c_int32()
+        self._raise(self.L.chem_batch_shape_info(self.h, shape, C.byref(blk), C.byref(regs), C.byref(per)))
+        return blk.value, regs.value, per.value
+
+    def autotune_batched(self, rho, e, Y, T, box_offset, box_dt, box_nsub, rtol=1e-6, atol=1e-10,
+                         h=None, cache_path=None, cost_hint=None, stream=None, max_results=64):
+        """chem_autotune_batched on the caller's batch (state untouched).  Returns (best
+        options as a dict usable as integrate_batched keywords, list of timed candidates)."""
+        n = rho.numel()
+        st = State(_ptr(rho).value, _ptr(e).value, _ptr(Y).value, Y.stride(0), _ptr(T).value,
+                   None if h is None else h.data_ptr(), None, None)
+        b = Batch(box_dt.numel(), box_offset.data_ptr(), box_dt.data_ptr(), box_nsub.data_ptr())
+        base = BatchOptions(0, 0, 0, 0, None if cost_hint is None else cost_hint.data_ptr())
+        best = BatchOptions()
+        res = (TuneResult * max_results)()
+        nres = C.c_int32()
+        self._raise(self.L.chem_autotune_batched(
+            self.h, C.byref(st), n, C.byref(b), float(rtol), float(atol), C.byref(base),
+            None if cache_path is None else os.fsencode(cache_path), _stream(stream), C.byref(best),
+            res, max_results, C.byref(nres)))
+        opts = {"order": best.order, "ctas_per_sm": best.ctas_per_sm, "use_graph": bool(best.use_graph),
+                "shape": best.shape}
+        table = [{"order": r.opt.order, "ctas_per_sm": r.ctas_per_sm, "use_graph": bool(r.opt.use_graph),
+                  "shape": r.opt.shape, "block": r.block, "regs": r.regs, "ms": r.ms}
+                 for r in res[: min(nres.value, max_results)]]
+        return opts, table
+
     def integrate_batched_noalloc(self, rho, e, Y, T, box_offset, box_dt, box_nsub, rtol=1e-6,
                                   atol=1e-10, h=None, status=None, nsteps=None, stats=None,
                                   order=ORDER_STIFFNESS, ctas_per_sm=0, cost_hint=None,
-                                  stream=None, ncells=None):
+                                  stream=None, ncells=None, shape=0):
         """chem_integrate_batched_noalloc: the batched integration for callers that cannot
         allocate device memory during the call (inside a graph capture, under a memory
         arena that owns the GPU, in latency-bound loops).  The scratch is a fixed array in
@@ -309,7 +350,7 @@ class Context:
                    None if status is None else status.data_ptr(),
                    None if nsteps is None else nsteps.data_ptr())
         b = Batch(box_dt.numel(), box_offset.data_ptr(), box_dt.data_ptr(), box_nsub.data_ptr())
-        o = BatchOptions(order, ctas_per_sm, 0, 0, None if cost_hint is None else cost_hint.data_ptr())
+        o = BatchOptions(order, ctas_per_sm, 0, shape, None if cost_hint is None else cost_hint.data_ptr())
         self._raise(fn(self.h, C.byref(st), n, C.byref(b), float(rtol), float(atol), C.byref(o),
                        _stream(stream), _ptr(stats)))
 

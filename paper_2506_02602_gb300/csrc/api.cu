@@ -356,8 +356,8 @@ int chem_integrate_batched(chem_ctx *ctx, const chem_state *state, int64_t ncell
   if (opt) o = *opt;
   if (o.order != CHEM_ORDER_STIFFNESS && o.order != CHEM_ORDER_NATURAL)
     return fail(ctx, CHEM_ERR_INVALID, "unknown queue order %d", o.order);
-  if (o.reserved || o.ctas_per_sm < 0)
-    return fail(ctx, CHEM_ERR_INVALID, "invalid batch options");
+  if (o.shape < 0 || o.shape >= CHEM_BATCH_SHAPES || o.ctas_per_sm < 0)
+    return fail(ctx, CHEM_ERR_INVALID, "invalid batch options (shape %d, ctas_per_sm %d)", o.shape, o.ctas_per_sm);
   if (!batch || batch->nboxes < 1 || !batch->d_box_offset || !batch->d_box_dt || !batch->d_box_nsub)
     return fail(ctx, CHEM_ERR_INVALID, "batch needs nboxes >= 1 and its three device arrays");
   cudaStream_t s = (cudaStream_t)stream;
@@ -380,7 +380,7 @@ int chem_integrate_batched(chem_ctx *ctx, const chem_state *state, int64_t ncell
       cudaError_t e = cudaMemsetAsync(d_stats, 0, sizeof(chem_stats), st);
       if (e != cudaSuccess) return e;
     }
-    return launch_batched(ctx->opt.variant, ctx->tables, a, p, sc, o.order, o.ctas_per_sm, st);
+    return launch_batched(ctx->opt.variant, ctx->tables, a, p, sc, o.order, o.ctas_per_sm, o.shape, st);
   };
   if (!o.use_graph) {
     cudaError_t e = issue(s);

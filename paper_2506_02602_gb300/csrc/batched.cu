@@ -121,11 +121,17 @@ __global__ void k_scatter(int64_t n, const uint8_t *__restrict__ bucket, int32_t
   order[base + __popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
 }
 
-template <int V>
-__global__ void __launch_bounds__(128) k_lsrk_persistent(const __grid_constant__ MechTables mt,
-                                                         const BatchArgs a, const StepParams p,
-                                                         const int32_t *__restrict__ order,
-                                                         unsigned long long *cursor) {
+// The persistent kernel is compiled in several shapes (threads per CTA, minimum
+// resident CTAs per SM); the second number caps the registers per thread at
+// 65536 / (block * minb), trading registers (and spills) against resident warps.  The
+// autotuner picks among them.  Every shape runs the same algorithm, but the compiler
+// contracts multiply-adds per compiled kernel, so shapes agree to rounding, not bit for
+// bit; shape 0 (no register cap) compiles like the one-pass kernel.
+template <int V, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_lsrk_persistent(const __grid_constant__ MechTables mt,
+                                                                 const BatchArgs a, const StepParams p,
+                                                                 const int32_t *__restrict__ order,
+                                                                 unsigned long long *cursor) {
   load_math_tables();
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -193,29 +199,90 @@ __global__ void __launch_bounds__(128) k_lsrk_persistent(const __grid_constant__
   if (a.stats) accumulate_stats(a.stats, done_cells, tot_acc, tot_rej, tot_rhs, max_steps, hist);
 }
 
-static int g_persist_ctas[2] = {0, 0};  // resident CTAs per SM of each variant (cached)
+// (block, minb) of each shape; shape 0 is the default.
+static constexpr int kShapeBlock[CHEM_BATCH_SHAPES] = {128, 128, 128, 64, 64, 256};
+static constexpr int kShapeMinB[CHEM_BATCH_SHAPES] = {2, 3, 4, 6, 8, 2};
 
-int persistent_capacity(int variant, int *num_sms) {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(num_sms, cudaDevAttrMultiProcessorCount, dev);
-  const int v = variant == CHEM_VARIANT_MIXED ? 1 : 0;
-  if (g_persist_ctas[v] == 0) {
-    int per = 0;
-    if (v)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lsrk_persistent<CHEM_VARIANT_MIXED>, 128, 0);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lsrk_persistent<CHEM_VARIANT_FP64>, 128, 0);
-    g_persist_ctas[v] = per > 0 ? per : 1;
+template <int V>
+static const void *persistent_fn(int shape) {
+  switch (shape) {
+    case 1: return reinterpret_cast<const void *>(k_lsrk_persistent<V, 128, 3>);
+    case 2: return reinterpret_cast<const void *>(k_lsrk_persistent<V, 128, 4>);
+    case 3: return reinterpret_cast<const void *>(k_lsrk_persistent<V, 64, 6>);
+    case 4: return reinterpret_cast<const void *>(k_lsrk_persistent<V, 64, 8>);
+    case 5: return reinterpret_cast<const void *>(k_lsrk_persistent<V, 256, 2>);
+    default: return reinterpret_cast<const void *>(k_lsrk_persistent<V, 128, 2>);
   }
-  return g_persist_ctas[v];
+}
+static_assert(CHEM_BATCH_SHAPES == 6, "persistent_fn lists every shape");
+
+static const void *persistent_kernel(int variant, int shape) {
+  return variant == CHEM_VARIANT_MIXED ? persistent_fn<CHEM_VARIANT_MIXED>(shape)
+                                       : persistent_fn<CHEM_VARIANT_FP64>(shape);
+}
+
+// Resident CTAs per SM and registers per thread of every (variant, shape), per device
+// ordinal (looked up once; 0 = not yet).
+static int g_persist_ctas[16][2][CHEM_BATCH_SHAPES];
+static int g_persist_regs[16][2][CHEM_BATCH_SHAPES];
+
+cudaError_t persistent_shape(int variant, int shape, int *block, int *ctas_per_sm, int *regs, int *num_sms) {
+  if (shape < 0 || shape >= CHEM_BATCH_SHAPES) return cudaErrorInvalidValue;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int v = variant == CHEM_VARIANT_MIXED ? 1 : 0;
+  const int d = dev >= 0 && dev < 16 ? dev : -1;
+  if (d < 0 || g_persist_ctas[d][v][shape] == 0) {
+    const void *fn = persistent_kernel(variant, shape);
+    int per = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kShapeBlock[shape], 0);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa{};
+    e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    if (d < 0) {
+      *ctas_per_sm = per > 0 ? per : 1;
+      *regs = fa.numRegs;
+      *block = kShapeBlock[shape];
+      return cudaSuccess;
+    }
+    g_persist_regs[d][v][shape] = fa.numRegs;
+    g_persist_ctas[d][v][shape] = per > 0 ? per : 1;
+  }
+  *ctas_per_sm = g_persist_ctas[d][v][shape];
+  *regs = g_persist_regs[d][v][shape];
+  *block = kShapeBlock[shape];
+  return cudaSuccess;
+}
+
+template <int V, int B, int M>
+static void launch_persistent_t(unsigned grid, cudaStream_t st, const MechTables &mt, const BatchArgs &a,
+                                const StepParams &p, const int32_t *order, unsigned long long *cursor) {
+  k_lsrk_persistent<V, B, M><<<grid, B, 0, st>>>(mt, a, p, order, cursor);
+}
+
+template <int V>
+static void launch_persistent(int shape, unsigned grid, cudaStream_t st, const MechTables &mt,
+                              const BatchArgs &a, const StepParams &p, const int32_t *order,
+                              unsigned long long *cursor) {
+  switch (shape) {
+    case 1: launch_persistent_t<V, 128, 3>(grid, st, mt, a, p, order, cursor); break;
+    case 2: launch_persistent_t<V, 128, 4>(grid, st, mt, a, p, order, cursor); break;
+    case 3: launch_persistent_t<V, 64, 6>(grid, st, mt, a, p, order, cursor); break;
+    case 4: launch_persistent_t<V, 64, 8>(grid, st, mt, a, p, order, cursor); break;
+    case 5: launch_persistent_t<V, 256, 2>(grid, st, mt, a, p, order, cursor); break;
+    default: launch_persistent_t<V, 128, 2>(grid, st, mt, a, p, order, cursor); break;
+  }
 }
 
 cudaError_t launch_batched(int variant, const MechTables &mt, const BatchArgs &a,
                            const StepParams &p, const BatchScratch &s, int order_mode,
-                           int ctas_per_sm, cudaStream_t st) {
+                           int ctas_per_sm, int shape, cudaStream_t st) {
   if (a.n <= 0) return cudaSuccess;
-  const int block = 128;
+  const int block = 128;  // of the probe and scatter kernels
   const unsigned grid_cells = (unsigned)((a.n + block - 1) / block);
   cudaError_t e;
   const int32_t *order = nullptr;
@@ -230,15 +297,17 @@ cudaError_t launch_batched(int variant, const MechTables &mt, const BatchArgs &a
     e = cudaMemsetAsync(s.cursor, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
   }
-  int sms = 0;
-  const int cap = persistent_capacity(variant, &sms);
+  int sms = 0, pblock = 0, cap = 0, regs = 0;
+  e = persistent_shape(variant, shape, &pblock, &cap, &regs, &sms);
+  if (e != cudaSuccess) return e;
   const int per = (ctas_per_sm > 0 && ctas_per_sm < cap) ? ctas_per_sm : cap;
   const int64_t cap_ctas = (int64_t)sms * per;
-  const unsigned grid = (unsigned)(cap_ctas < (int64_t)grid_cells ? cap_ctas : (int64_t)grid_cells);
+  const int64_t need = (a.n + pblock - 1) / pblock;
+  const unsigned grid = (unsigned)(cap_ctas < need ? cap_ctas : need);
   if (variant == CHEM_VARIANT_MIXED)
-    k_lsrk_persistent<CHEM_VARIANT_MIXED><<<grid, block, 0, st>>>(mt, a, p, order, s.cursor);
+    launch_persistent<CHEM_VARIANT_MIXED>(shape, grid, st, mt, a, p, order, s.cursor);
   else
-    k_lsrk_persistent<CHEM_VARIANT_FP64><<<grid, block, 0, st>>>(mt, a, p, order, s.cursor);
+    launch_persistent<CHEM_VARIANT_FP64>(shape, grid, st, mt, a, p, order, s.cursor);
   return cudaGetLastError();
 }
 
@@ -306,7 +375,7 @@ extern "C" int chem_integrate_batched_noalloc(chem_ctx *ctx, const chem_state *s
   chem_batch_options o{};
   if (opt) o = *opt;
   if (o.order != CHEM_ORDER_STIFFNESS && o.order != CHEM_ORDER_NATURAL) return bad("unknown queue order");
-  if (o.reserved || o.ctas_per_sm < 0) return bad("invalid batch options");
+  if (o.shape < 0 || o.shape >= CHEM_BATCH_SHAPES || o.ctas_per_sm < 0) return bad("invalid batch options");
   if (!batch || batch->nboxes < 1 || !batch->d_box_offset || !batch->d_box_dt || !batch->d_box_nsub)
     return bad("batch needs nboxes >= 1 and its three device arrays");
   if (ncells > 0) {
@@ -346,7 +415,7 @@ extern "C" int chem_integrate_batched_noalloc(chem_ctx *ctx, const chem_state *s
   // launch_batched clears the bucket counts (cudaMemsetAsync) and resets the cursor
   // (k_scan, or cudaMemsetAsync in natural order) before the kernels read them
   e = launch_batched(chem_ctx_variant(ctx), chem_ctx_tables(ctx), a, p, sc, o.order,
-                     o.ctas_per_sm, s);
+                     o.ctas_per_sm, o.shape, s);
   if (e != cudaSuccess) {
     err = std::string("batched launch: ") + cudaGetErrorString(e);
     return CHEM_ERR_CUDA;

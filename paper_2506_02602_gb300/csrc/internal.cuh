@@ -73,7 +73,10 @@ void surrogate_destroy(void *sur);
 
 cudaError_t launch_batched(int variant, const MechTables &mt, const BatchArgs &a,
                            const StepParams &p, const BatchScratch &s, int order_mode,
-                           int ctas_per_sm, cudaStream_t st);
+                           int ctas_per_sm, int shape, cudaStream_t st);
+// Threads per CTA, resident CTAs per SM, registers per thread of a persistent-kernel
+// shape, and the device's SM count.
+cudaError_t persistent_shape(int variant, int shape, int *block, int *ctas_per_sm, int *regs, int *num_sms);
 cudaError_t launch_state_from_TPY(const MechTables &mt, int64_t n, const double *T,
                                   const double *p, const double *Y, int64_t ld, double *rho,
                                   double *e, cudaStream_t s);

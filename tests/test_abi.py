@@ -62,11 +62,13 @@ int main(void) {
          offsetof(chem_batch, d_box_nsub), offsetof(chem_batch_options, d_cost_hint));
   printf("%zu %zu %zu %zu\n", sizeof(chem_pairs), sizeof(chem_train_cfg), sizeof(chem_surrogate_gate),
          offsetof(chem_train_cfg, seed));
+  printf("%zu %zu %zu\n", sizeof(chem_tune_result), offsetof(chem_tune_result, ms),
+         offsetof(chem_tune_result, ctas_per_sm));
   return 0;
 }''')
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)
-    a, b, c, d = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:4]
+    a, b, c, d, t = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:5]
     assert [int(x) for x in a.split()] == [C.sizeof(chem.Mechanism), C.sizeof(chem.Options),
                                           C.sizeof(chem.State), C.sizeof(chem.Stats)]
     assert [int(x) for x in b.split()] == [chem.Mechanism.eff.offset, chem.Mechanism.reversible.offset,
@@ -75,6 +77,8 @@ int main(void) {
                                           chem.Batch.d_box_nsub.offset, chem.BatchOptions.d_cost_hint.offset]
     assert [int(x) for x in d.split()] == [C.sizeof(chem.Pairs), C.sizeof(chem.TrainCfg), C.sizeof(chem.Gate),
                                           chem.TrainCfg.seed.offset]
+    assert [int(x) for x in t.split()] == [C.sizeof(chem.TuneResult), chem.TuneResult.ms.offset,
+                                          chem.TuneResult.ctas_per_sm.offset]
 
 
 def _setup_rc(lib, mech, variant=0):

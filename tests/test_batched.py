@@ -6,8 +6,11 @@
   kernel);
 * the persistent kernel's per-cell arithmetic is the one-pass kernel's: with one
   substep per box the results are bit-identical to chem_integrate, whatever the queue
-  order (stiffness-sorted, natural, cost hint) and with or without graph replay;
-* statistics, argument errors, and a full-size AMR batch checked on sampled cells.
+  order (stiffness-sorted, natural, cost hint) and with or without graph replay; the
+  other compiled shapes agree to rounding;
+* statistics, argument errors, and a full-size AMR batch checked on sampled cells;
+* the autotuner leaves the caller's state alone, returns options that give the same
+  results, and answers from its cache the second time.
 """
 import numpy as np
 import pytest
@@ -110,6 +113,19 @@ def test_single_substep_matches_one_pass_bitwise(ctx):
         np.testing.assert_array_equal(gpu["Y"], one["Y"])
         np.testing.assert_array_equal(gpu["T"], one["T"])
         np.testing.assert_array_equal(gpu["nsteps"], one["nsteps"])
+    for s in range(1, chem.BATCH_SHAPES):
+        _agree_to_rounding(_run_batched(ctx, b, shape=s), one)
+
+
+def _agree_to_rounding(a, b):
+    """Another compiled shape: same algorithm, multiply-adds contracted differently, so
+    rounding-level differences in 99 % of the cells; the rest are ill-conditioned at
+    this long step (ignition in progress at its end: a rounding-seeded change of the
+    step sequence moves the ignition time), and are only held to 1e-2 on T."""
+    relT = np.abs(a["T"] - b["T"]) / b["T"]
+    assert np.all(a["status"] == 0)
+    assert np.quantile(relT, 0.99) <= 1e-10
+    assert relT.max() <= 1e-2
 
 
 def test_graph_recaptures_on_new_arguments(ctx):
@@ -176,3 +192,37 @@ def test_amr_batch_full_size_sampled(ctx):
         print(compare(g, ref))
     else:
         assert np.max(np.abs(g["T"] - ref["T"]) / ref["T"]) <= 1e-5
+
+
+def test_autotune_batched(ctx, tmp_path):
+    import torch
+    from paper_2506_02602_gb300 import chem
+    b = _batch(40, seed=25)
+    n = b["T"].size
+    rho, e = to_dev(b["rho"]), to_dev(b["e"])
+    Y, T = to_dev(b["Y"]), to_dev(b["T"])
+    off = torch.tensor(b["box_offset"], dtype=torch.int64, device="cuda")
+    dts = torch.tensor(b["box_dt"], dtype=torch.float64, device="cuda")
+    nsub = torch.tensor(b["box_nsub"], dtype=torch.int32, device="cuda")
+    cache = tmp_path / "tune.txt"
+    best, table = ctx.autotune_batched(rho, e, Y, T, off, dts, nsub, cache_path=str(cache))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(Y.cpu().numpy(), b["Y"])  # caller's state untouched
+    np.testing.assert_array_equal(T.cpu().numpy(), b["T"])
+    assert len(table) >= chem.BATCH_SHAPES + 2 and all(r["ms"] > 0 for r in table)
+    assert {r["shape"] for r in table} == set(range(chem.BATCH_SHAPES))
+    fastest = min(r["ms"] for r in table)
+    assert any(r["ms"] == fastest and r["shape"] == best["shape"] for r in table)
+    for s in range(chem.BATCH_SHAPES):
+        blk, regs, per = ctx.batch_shape_info(s)
+        assert blk in (64, 128, 256) and 0 < regs <= 255 and per >= 1
+    ref = _run_batched(ctx, b)
+    tuned = _run_batched(ctx, b, **best)
+    if best["shape"] == 0:
+        for k in ("Y", "T", "nsteps"):
+            np.testing.assert_array_equal(tuned[k], ref[k])
+    else:
+        _agree_to_rounding(tuned, ref)
+    again, table2 = ctx.autotune_batched(rho, e, Y, T, off, dts, nsub, cache_path=str(cache))
+    assert table2 == [] and again == best
+    assert len(cache.read_text().splitlines()) == 1
