@@ -241,6 +241,17 @@ def timed(fn, reps, stream):
     return best
 
 
+FALLBACK_REASONS = ("range", "residual", "negative", "temperature", "reactive", "judge")
+
+
+def fallback_reasons(mask):
+    """Fraction of cells per rejection reason of chem_surrogate_infer's fallback mask."""
+    import torch
+    counts = torch.bincount(mask.long().flatten(), minlength=7).cpu().numpy()
+    n = max(int(mask.numel()), 1)
+    return {name: float(counts[i + 1]) / n for i, name in enumerate(FALLBACK_REASONS)}
+
+
 def surrogate_leg(args, mech, dev, stream):
     """Data generation, training and inference of the learned surrogate (module docstring).
     Returns the leg's summary and a mixed-precision context holding the trained network."""
@@ -313,6 +324,8 @@ def surrogate_leg(args, mech, dev, stream):
             rel = (T - Tr).abs() / Tr
             fb = mask.bool()
             r[name] = {"cells_per_s": n / (t * 1e-3), "fallback_frac": float(fb.float().mean()),
+                       "fallback_reasons": fallback_reasons(mask),
+                       "p999_rel_T": float(torch.quantile(rel[::4].float(), 0.999)),  # every 4th cell
                        "max_rel_T": float(rel.max()),
                        "max_rel_T_accepted": float(rel[~fb].max()) if bool((~fb).any()) else 0.0,
                        "max_abs_Y": float((Y - Yr).abs().max()),
@@ -473,7 +486,8 @@ def run_ours(args, rank, world, local):
         res[v] = {"elapsed": elapsed, "kernel_ms": kernel_ms, "nsteps": ns,
                   "status": status.cpu().numpy(), "Y": Y.cpu().numpy(), "T": T.cpu().numpy()}
         if v == "hybrid":
-            res[v]["fallback_frac"] = float(fbmask.float().mean())
+            res[v]["fallback_frac"] = float((fbmask != 0).float().mean())
+            res[v]["fallback_reasons"] = fallback_reasons(fbmask)
     clk = clocks.stop()
 
     ref = res["fp64"]
@@ -513,6 +527,7 @@ def run_ours(args, rank, world, local):
         }
         if v == "hybrid":
             summary[v]["fallback_frac"] = r["fallback_frac"]
+            summary[v]["fallback_reasons"] = r["fallback_reasons"]
     ok = [v for v, _ in variants if summary[v]["meets_stated_error"]]
     head = max(ok, key=lambda v: summary[v]["value"])
     H = summary[head]

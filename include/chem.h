@@ -382,8 +382,11 @@ int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
  * Accepted cells get the projected Y, its T, status CHEM_CELL_OK and nsteps 0; rejected
  * cells are integrated with rtol, atol (one thread per cell, the context's variant) and
  * get status CHEM_CELL_SURROGATE, or the integrator's failure code, and their attempted
- * steps.  d_fallback_mask (nullable, device uint8 [ncells]) receives 1 for rejected
- * cells.  d_stats (nullable): status_count[CHEM_CELL_SURROGATE] counts fallbacks.
+ * steps.  d_fallback_mask (nullable, device uint8 [ncells]) receives 0 for accepted
+ * cells and, for rejected ones, the first gate that failed: 1 feature outside the
+ * training range, 2 element residual, 3 negative mass fraction, 4 temperature (no
+ * root or |dT| > max_dT), 5 judge: the step is not slow for the cell, 6 judge: error
+ * estimate above judge_tol.  d_stats (nullable): status_count[CHEM_CELL_SURROGATE] counts fallbacks.
  * gate may be NULL.  Errors: no trained or loaded network -> CHEM_ERR_STATE; arguments
  * as chem_integrate.  Asynchronous on stream.
  */
@@ -412,13 +415,18 @@ int chem_surrogate_grad(chem_ctx *ctx, const float *d_X, const float *d_T, int64
                         float *h_grad, float *h_loss, void *stream);
 
 /*
- * The network alone on B rows, as inference runs it (one fused kernel, activations kept
- * on chip): d_X [B x 16] normalised features (fp32 device), d_Y [B x 16] outputs (fp32
- * device, out; columns 9..15 zero).  Gives the same numbers as the forward pass of
- * chem_surrogate_grad.  Asynchronous on stream.  Errors: B < 0 or NULL arrays with
- * B > 0 -> CHEM_ERR_INVALID.  (Not a call of the paper's method: a check of the kernel.)
+ * The network alone on B rows (a check of the kernels; not a call of the paper's
+ * method): d_X [B x 16] normalised features (fp32 device), d_Y [B x 16] outputs (fp32
+ * device, out; columns 9..15 zero).  impl: 0 = the kernel inference uses (tcgen05
+ * tensor cores, tensor-memory accumulators, weights streamed by bulk copies), 1 = the
+ * one-kernel mma.sync version (same numbers as 2), 2 = the layer-by-layer GEMMs of
+ * training.  h_err (nullable, host): when given, the call synchronises and receives
+ * 1 if a bounded wait of the tensor-core kernel ran out (its outputs are then invalid),
+ * else 0.  Asynchronous on stream otherwise (impl 2 is synchronous).  Errors: B < 0,
+ * NULL arrays with B > 0, unknown impl -> CHEM_ERR_INVALID.
  */
-int chem_surrogate_forward(chem_ctx *ctx, const float *d_X, int64_t B, float *d_Y, void *stream);
+int chem_surrogate_forward(chem_ctx *ctx, const float *d_X, int64_t B, float *d_Y, int32_t impl,
+                           void *stream, int32_t *h_err);
 
 /*
  * chem_integrate_batched for callers that cannot allocate device memory during the call.

@@ -145,7 +145,7 @@ def load() -> C.CDLL:
         "chem_surrogate_load": (C.c_int, [vp, C.c_char_p]),
         "chem_surrogate_params": (C.c_int, [vp, vp, vp, i64]),
         "chem_surrogate_grad": (C.c_int, [vp, vp, vp, i64, vp, vp, vp, vp]),
-        "chem_surrogate_forward": (C.c_int, [vp, vp, i64, vp, vp]),
+        "chem_surrogate_forward": (C.c_int, [vp, vp, i64, vp, C.c_int32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -415,14 +415,18 @@ class Context:
                                                _stream(stream)))
         return Y, g, float(loss[0])
 
-    def surrogate_forward(self, X, stream=None):
-        """chem_surrogate_forward (the fused inference network) on an fp32 CUDA tensor
-        X [B, 16] of normalised features: returns Y [B, 16]."""
+    FWD_TC, FWD_FUSED, FWD_LAYERS = 0, 1, 2
+
+    def surrogate_forward(self, X, impl=0, stream=None, check=False):
+        """chem_surrogate_forward on an fp32 CUDA tensor X [B, 16] of normalised features:
+        returns Y [B, 16] (and, with check=True, the tensor-core kernel's error word)."""
         import torch
         B = X.shape[0]
         Y = torch.empty((B, 16), dtype=torch.float32, device=X.device)
-        self._raise(self.L.chem_surrogate_forward(self.h, _ptr(X), B, _ptr(Y), _stream(stream)))
-        return Y
+        err = C.c_int32(0)
+        self._raise(self.L.chem_surrogate_forward(self.h, _ptr(X), B, _ptr(Y), impl, _stream(stream),
+                                                  C.byref(err) if check else None))
+        return (Y, err.value) if check else Y
 
     def integrate_host(self, rho, e, Y, T, dt, rtol=1e-6, atol=1e-10, h=None, status=None,
                        nsteps=None, stream=None):

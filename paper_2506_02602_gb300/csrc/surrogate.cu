@@ -44,6 +44,10 @@ struct Surrogate {
   int64_t fb_cap = 0;
   int32_t *fb_idx = nullptr;
   unsigned int *fb_count = nullptr;
+  // the weights in the tensor-core kernel's layout (repacked when the weights change)
+  unsigned char *Wpk = nullptr;
+  bool packed = false;
+  int *tc_err = nullptr;  // error word of the tensor-core kernel (a wait ran out)
 };
 
 static void free_surrogate(Surrogate *s) {
@@ -62,6 +66,8 @@ static void free_surrogate(Surrogate *s) {
   cudaFree(s->Tok);
   cudaFree(s->fb_idx);
   cudaFree(s->fb_count);
+  cudaFree(s->Wpk);
+  cudaFree(s->tc_err);
   delete s;
 }
 
@@ -108,6 +114,9 @@ static cudaError_t alloc_params(Surrogate *s) {
   }
   SCHK(cudaMalloc(&s->dev_norm, 4 * 16 * sizeof(float)));
   SCHK(cudaMalloc(&s->fb_count, sizeof(unsigned int)));
+  SCHK(cudaMalloc(&s->Wpk, packed_weight_bytes()));
+  SCHK(cudaMalloc(&s->tc_err, sizeof(int)));
+  SCHK(cudaMemset(s->tc_err, 0, sizeof(int)));
   return cudaSuccess;
 }
 
@@ -124,6 +133,7 @@ static cudaError_t set_params(Surrogate *s, const float *h, cudaStream_t st) {
                      s->m + s->off_W[l], s->v + s->off_W[l], 0.0f, 0.9f, 0.999f, 1e-8f, 1, s->W[l],
                      s->WT[l], kSurN[l], kSurK[l], st));
   s->step = 0;
+  s->packed = false;
   return cudaSuccess;
 }
 
@@ -265,6 +275,7 @@ static cudaError_t forward_backward(Surrogate *s, TrainBufs &b, int64_t B, cudaS
 
 static cudaError_t adam_all(Surrogate *s, float lr, cudaStream_t st) {
   ++s->step;
+  s->packed = false;
   for (int l = 0; l < kSurLayers; ++l) {
     const int64_t nw = (int64_t)kSurN[l] * kSurK[l];
     SCHK(launch_adam(nw, s->param + s->off_W[l], s->grad + s->off_W[l], s->m + s->off_W[l],
@@ -334,16 +345,25 @@ static Surrogate *ensure_surrogate(chem_ctx *ctx, cudaError_t *err) {
 // Cells per inference chunk (features and outputs, 132 B a cell, are staged per chunk).
 constexpr int64_t kInferChunk = 1 << 22;
 
-// The fused network over n rows of features X (raw with norm, else normalised).
-static cudaError_t mlp_forward(const Surrogate *s, int64_t n, const float *X, const float *norm, float *O,
-                               cudaStream_t st) {
+// Forward kernels of the network: the tcgen05 one (inference), the mma.sync one-kernel
+// version and the layer-by-layer GEMMs of training (checks).
+enum { kFwdTc = 0, kFwdFused = 1, kFwdLayers = 2 };
+
+// The network over n rows of features X (raw with norm, else normalised), in one kernel.
+static cudaError_t mlp_forward(Surrogate *s, int64_t n, const float *X, const float *norm, float *O,
+                               cudaStream_t st, int impl = kFwdTc) {
   const __nv_bfloat16 *W[kSurLayers];
   const float *b[kSurLayers];
   for (int l = 0; l < kSurLayers; ++l) {
     W[l] = s->W[l];
     b[l] = s->param + s->off_b[l];
   }
-  return launch_mlp_fused(n, X, norm, W, b, O, st);
+  if (impl == kFwdFused) return launch_mlp_fused(n, X, norm, W, b, O, st);
+  if (!s->packed) {
+    SCHK(launch_pack_weights(W, s->Wpk, st));
+    s->packed = true;
+  }
+  return launch_mlp_tc(n, X, norm, s->Wpk, b, O, s->tc_err, st);
 }
 
 static cudaError_t ensure_infer_buffers(Surrogate *s, int64_t chunk, int64_t n) {
@@ -415,13 +435,36 @@ int chem_surrogate_grad(chem_ctx *ctx, const float *d_X, const float *d_T, int64
   return e == cudaSuccess ? CHEM_OK : sur_cuda(ctx, e, "surrogate forward/backward");
 }
 
-int chem_surrogate_forward(chem_ctx *ctx, const float *d_X, int64_t B, float *d_Y, void *stream) {
+int chem_surrogate_forward(chem_ctx *ctx, const float *d_X, int64_t B, float *d_Y, int32_t impl,
+                           void *stream, int32_t *h_err) {
   if (!ctx) return CHEM_ERR_INVALID;
   if (B < 0 || (B > 0 && (!d_X || !d_Y))) return sur_fail(ctx, CHEM_ERR_INVALID, "B >= 0, X and Y required");
+  if (impl < kFwdTc || impl > kFwdLayers) return sur_fail(ctx, CHEM_ERR_INVALID, "unknown forward kernel");
   cudaError_t e;
   Surrogate *s = ensure_surrogate(ctx, &e);
   if (!s) return sur_cuda(ctx, e, "allocating the surrogate");
-  e = mlp_forward(s, B, d_X, nullptr, d_Y, (cudaStream_t)stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (impl == kFwdLayers) {
+    if (B == 0) return CHEM_OK;
+    TrainBufs b;
+    e = b.alloc(B);
+    if (e == cudaSuccess) e = launch_to_bf16(B * kSurIn, d_X, b.Xbf, st);
+    if (e == cudaSuccess) e = layer_forward(s, 0, B, b.Xbf, nullptr, b.H[0], nullptr, st);
+    if (e == cudaSuccess) e = layer_forward(s, 1, B, b.H[0], nullptr, b.H[1], nullptr, st);
+    if (e == cudaSuccess) e = layer_forward(s, 2, B, b.H[1], nullptr, b.H[2], nullptr, st);
+    if (e == cudaSuccess) e = layer_forward(s, 3, B, b.H[2], nullptr, nullptr, d_Y, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    b.release();
+  } else {
+    if (h_err && impl == kFwdTc) e = cudaMemsetAsync(s->tc_err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = mlp_forward(s, B, d_X, nullptr, d_Y, st, impl);
+  }
+  if (e == cudaSuccess && h_err) {
+    int v = 0;
+    if (impl == kFwdTc) e = cudaMemcpyAsync(&v, s->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    *h_err = v;
+  }
   return e == cudaSuccess ? CHEM_OK : sur_cuda(ctx, e, "surrogate forward");
 }
 

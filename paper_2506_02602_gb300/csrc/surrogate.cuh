@@ -29,6 +29,16 @@ constexpr int64_t kSurParams = (int64_t)kSurHidden * kSurIn + kSurHidden +
                                2 * ((int64_t)kSurHidden * kSurHidden + kSurHidden) +
                                (int64_t)kSurOut * kSurHidden + kSurOut;
 
+// Why a cell was sent to the integrator (the fallback mask's values; 0 = accepted).
+enum {
+  kFbRange = 1,        // a feature outside the training box (with the margin)
+  kFbResidual = 2,     // element residual of the raw prediction too large
+  kFbNegative = 3,     // a mass fraction below -neg_tol after the projection
+  kFbTemperature = 4,  // no temperature root, or |T' - T0| > max_dT
+  kFbReactive = 5,     // judge: the step is not slow for the cell (judge_rate)
+  kFbJudge = 6,        // judge: error estimate above judge_tol
+};
+
 // Everything the inference epilogue needs besides the mechanism (passed by value).
 struct SurrogateConsts {
   float tmean[NSP], tstd[NSP];          // target normalisation
@@ -69,6 +79,13 @@ cudaError_t launch_surrogate_stats(chem_stats *st, int64_t n, const unsigned int
 cudaError_t launch_mlp_fused(int64_t n, const float *X, const float *norm,
                              const __nv_bfloat16 *const (&W)[kSurLayers],
                              const float *const (&b)[kSurLayers], float *O, cudaStream_t s);
+// The network on the 5th-generation tensor cores (mlp_tc.cu): weights repacked into the
+// kernel's operand layout by launch_pack_weights (packed_weight_bytes() bytes); err is
+// a device word set to 1 if one of the kernel's bounded waits ran out.
+cudaError_t launch_pack_weights(const __nv_bfloat16 *const (&W)[kSurLayers], unsigned char *Wpk, cudaStream_t s);
+size_t packed_weight_bytes();
+cudaError_t launch_mlp_tc(int64_t n, const float *X, const float *norm, const unsigned char *Wpk,
+                          const float *const (&b)[kSurLayers], float *O, int *err, cudaStream_t s);
 cudaError_t launch_lsrk_indexed(int variant, const MechTables &mt, const CellArgs &a,
                                 const StepParams &p, const int32_t *idx, const unsigned int *count,
                                 int64_t max_count, cudaStream_t s);

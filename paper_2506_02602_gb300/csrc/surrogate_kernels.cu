@@ -39,8 +39,22 @@ __device__ __forceinline__ double boxcox_d(double y, double lam) {
   return (pow(fmax(y, 1e-30), lam) - 1.0) / lam;
 }
 
-__device__ __forceinline__ double boxcox_inv_d(double z, double lam) {
-  return pow(fmax(1.0 + lam * z, 0.0), 1.0 / lam);
+// The features' transform in fp32 (they are fp32 network inputs).
+__device__ __forceinline__ float boxcox_f(double y, float lam) {
+  return (powf(fmaxf((float)y, 1e-30f), lam) - 1.0f) / lam;
+}
+
+// Y1 from Y0, its fp32 feature bc0 = BC(Y0) and the predicted increment d, as an
+// increment on Y0: with y = max(Y0, 1e-30) (the transform's floor) and 1 + lam bc0
+// standing for y^lam, the Box-Cox inverse of bc0 + d is y r with
+// r = (1 + lam d / (1 + lam bc0))^(1/lam), and Y1 = Y0 + y (r - 1).  The feature's
+// rounding cancels, d = 0 returns Y0 exactly, and a species absent from Y0 can form.
+// A base at or below zero (r = 0) gives Y1 = Y0 - y.
+__device__ __forceinline__ double boxcox_step(double y0, float bc0, float d, float lam) {
+  const double y = fmax(y0, 1e-30);
+  const float s = lam * d / fmaf(lam, bc0, 1.0f);
+  if (!(s > -1.0f)) return y0 - y;
+  return fma(y, (double)expm1f(log1pf(s) / lam), y0);
 }
 
 // Raw (un-normalised) features and, when Y1 is given, targets of n cells.
@@ -68,22 +82,18 @@ __global__ void k_features(const __grid_constant__ MechTables mt, int64_t n, con
   const double dt = dt_cell ? dt_cell[i] : dt_scalar;
   float *x = X + i * kSurIn;
   x[0] = (float)T;
-  x[1] = (float)log(fmax(p, 1e-30));
-  x[2] = (float)log10(dt);
-  double bc0[NSP];
+  x[1] = logf(fmaxf((float)p, 1e-30f));
+  x[2] = log10f((float)dt);
 #pragma unroll
-  for (int k = 0; k < NSP; ++k) {
-    bc0[k] = boxcox_d(y[k], lam);
-    x[3 + k] = (float)bc0[k];
-  }
+  for (int k = 0; k < NSP; ++k) x[3 + k] = boxcox_f(y[k], (float)lam);
 #pragma unroll
   for (int c = 12; c < kSurIn; ++c) x[c] = 0.0f;
-  if (Y1) {
+  if (Y1) {  // training targets: the fp64 increment (no cancellation of two fp32 values)
     float *t = Tg + i * kSurOut;
-#pragma unroll
     const double sc = dt_power == 0.0 ? 1.0 : pow(kSurDtRef / dt, dt_power);
 #pragma unroll
-    for (int k = 0; k < NSP; ++k) t[k] = (float)((boxcox_d(Y1[k * ld1 + i], lam) - bc0[k]) * sc);
+    for (int k = 0; k < NSP; ++k)
+      t[k] = (float)((boxcox_d(Y1[k * ld1 + i], lam) - boxcox_d(y[k], lam)) * sc);
 #pragma unroll
     for (int c = NSP; c < kSurOut; ++c) t[c] = 0.0f;
   }
@@ -218,20 +228,23 @@ __global__ void __launch_bounds__(128)
   if (i >= n) return;
   const float *x = Xraw + i * kSurIn;
   const float *o = O + i * kSurOut;
-  bool accept = Tok[i] != 0;
+  // reason of a rejection (the first gate that fails), reported in the fallback mask
+  int reason = Tok[i] != 0 ? 0 : kFbTemperature;
   // out-of-distribution: every feature within the training box widened by the margin
+  bool inbox = true;
 #pragma unroll
   for (int c = 0; c < 12; ++c) {
     const float w = sc.margin * (sc.fmax[c] - sc.fmin[c]);
-    accept &= x[c] >= sc.fmin[c] - w && x[c] <= sc.fmax[c] + w;
+    inbox &= x[c] >= sc.fmin[c] - w && x[c] <= sc.fmax[c] + w;
   }
+  if (!reason && !inbox) reason = kFbRange;
   double y0[NSP], y1[NSP];
-  const double unscale = sc.dt_power == 0.0 ? 1.0 : pow(dt / kSurDtRef, sc.dt_power);
+  const float unscale = sc.dt_power == 0.0 ? 1.0f : powf((float)(dt / kSurDtRef), (float)sc.dt_power);
 #pragma unroll
   for (int k = 0; k < NSP; ++k) {
     y0[k] = Y[k * ld + i];
-    const double d = ((double)o[k] * sc.tstd[k] + sc.tmean[k]) * unscale;
-    y1[k] = boxcox_inv_d((double)x[3 + k] + d, sc.lam);
+    const float d = fmaf(o[k], sc.tstd[k], sc.tmean[k]) * unscale;
+    y1[k] = boxcox_step(y0[k], x[3 + k], d, (float)sc.lam);
   }
   // element mass fractions before projection and the residual
   double z0[3] = {0.0, 0.0, 0.0}, r[3] = {0.0, 0.0, 0.0};
@@ -248,7 +261,7 @@ __global__ void __launch_bounds__(128)
     rn += r[el] * r[el];
     zn += z0[el] * z0[el];
   }
-  accept &= rn <= (double)sc.resid_max * sc.resid_max * zn;
+  if (!reason && !(rn <= (double)sc.resid_max * sc.resid_max * zn)) reason = kFbResidual;
   // weighted least-squares projection onto E Y = E Y0: Y'' = Y' - W E^T (E W E^T)^-1 r
   double w[NSP], M[3][3];
 #pragma unroll
@@ -275,8 +288,8 @@ __global__ void __launch_bounds__(128)
                M[0][2] * (M[1][0] * r[2] - r[1] * M[2][0])) * id;
     lamv[2] = (M[0][0] * (M[1][1] * r[2] - r[1] * M[2][1]) - M[0][1] * (M[1][0] * r[2] - r[1] * M[2][0]) +
                r[0] * (M[1][0] * M[2][1] - M[1][1] * M[2][0])) * id;
-  } else {
-    accept = false;
+  } else if (!reason) {
+    reason = kFbResidual;
   }
   double ymin = 1.0;
 #pragma unroll
@@ -287,20 +300,21 @@ __global__ void __launch_bounds__(128)
     y1[k] -= w[k] * corr;
     ymin = fmin(ymin, y1[k]);
   }
-  accept &= ymin >= -(double)sc.neg_tol;
+  if (!reason && !(ymin >= -(double)sc.neg_tol)) reason = kFbNegative;
   // temperature of the projected state (fp64 Newton from the input temperature)
   double yw[NSP];
 #pragma unroll
   for (int k = 0; k < NSP; ++k) yw[k] = y1[k] * mt.invW[k];
   double T1 = (double)x[0];
   const bool tok = solve_T(mt, yw, e[i] / R_U, T1);
-  accept &= tok && fabs(T1 - (double)x[0]) <= (double)sc.max_dT;
-  if (accept && sc.judge_tol > 0.0f) {
+  if (!reason && !(tok && fabs(T1 - (double)x[0]) <= (double)sc.max_dT)) reason = kFbTemperature;
+  if (!reason && sc.judge_tol > 0.0f) {
     double dT = 0.0, rate = 0.0;
     const bool jok = judge_defect<V>(mt, y0, y1, rho[i], e[i] / R_U, (double)x[0], T1, dt, dT, rate);
-    accept = jok && dT <= (double)sc.judge_tol * T1 && (sc.judge_rate < 0.0f || rate <= (double)sc.judge_rate);
+    if (!jok || !(sc.judge_rate < 0.0f || rate <= (double)sc.judge_rate)) reason = kFbReactive;
+    else if (!(dT <= (double)sc.judge_tol * T1)) reason = kFbJudge;
   }
-  if (accept) {
+  if (!reason) {
 #pragma unroll
     for (int k = 0; k < NSP; ++k) Y[k * ld + i] = y1[k];
     T[i] = T1;
@@ -308,7 +322,7 @@ __global__ void __launch_bounds__(128)
     if (nsteps) nsteps[i] = 0;
     if (mask) mask[i] = 0;
   } else {
-    if (mask) mask[i] = 1;
+    if (mask) mask[i] = (uint8_t)reason;
     const unsigned slot = atomicAdd(fb_count, 1u);
     fb_idx[slot] = (int32_t)(base + i);
   }

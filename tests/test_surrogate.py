@@ -82,11 +82,23 @@ def test_forward_backward_matches_fp64_oracle(lib):
     lo, dy = mlp.mse(Yo, Tt[:, :9])
     go = mlp.backward(params, pre, dy)
     Yg = Y.cpu().numpy()
-    # the fused inference kernel: same fragments, K order and epilogue -> same numbers
-    Yf = ctx.surrogate_forward(Xb.cuda()).cpu().numpy()
+    # the one-kernel mma.sync forward: same fragments, K order and epilogue -> same numbers
+    Yf = ctx.surrogate_forward(Xb.cuda(), impl=ctx.FWD_FUSED).cpu().numpy()
     np.testing.assert_array_equal(Yf, Yg)
-    Yf2 = ctx.surrogate_forward(Xb[:333].contiguous().cuda()).cpu().numpy()  # ragged last tile
+    Yf2 = ctx.surrogate_forward(Xb[:333].contiguous().cuda(), impl=ctx.FWD_FUSED).cpu().numpy()  # ragged tile
     np.testing.assert_array_equal(Yf2, Yg[:333])
+    np.testing.assert_array_equal(ctx.surrogate_forward(Xb.cuda(), impl=ctx.FWD_LAYERS).cpu().numpy(), Yg)
+    # the tcgen05 kernel inference uses: the tensor cores sum the K products in their own
+    # order, so FP32 sums differ in the last bits and a BF16 activation can round the
+    # other way; the outputs agree to BF16 level, and with the FP64 oracle as above
+    for rows in (B, 333, 129, 1):
+        Yt, err = ctx.surrogate_forward(Xb[:rows].contiguous().cuda(), check=True)
+        Yt = Yt.cpu().numpy()
+        assert err == 0
+        assert np.linalg.norm(Yt - Yg[:rows]) <= 5e-3 * np.linalg.norm(Yg[:rows]), rows
+        assert np.all(Yt[:, 9:] == 0.0)
+    Yt = ctx.surrogate_forward(Xb.cuda()).cpu().numpy()
+    assert np.linalg.norm(Yt[:, :9] - Yo) <= 2e-2 * np.linalg.norm(Yo)
     assert np.linalg.norm(Yg[:, :9] - Yo) <= 2e-2 * np.linalg.norm(Yo)
     assert np.all(Yg[:, 9:] == 0.0)
     assert loss == pytest.approx(lo, rel=2e-2)
@@ -197,7 +209,7 @@ def test_trained_network_gains_over_plain_integration(lib, trained):
     tp, Yp, Tp = best(lambda Y, T: ctx.integrate(cells["rho"], cells["e"], Y, T, dt))
     ts, Ys, Ts = best(lambda Y, T: ctx.surrogate_infer(cells["rho"], cells["e"], Y, T, dt, mask=mask))
     rel = ((Ts - Tp).abs() / Tp).max().item()
-    fb = mask.float().mean().item()
+    fb = (mask != 0).float().mean().item()
     print(f"plain {n / tp:.3e} cells/s, surrogate {n / ts:.3e} cells/s, fallback {fb:.4f}, max rel T {rel:.2e}")
     assert rel <= 1e-3
     assert fb < 0.5
