@@ -202,6 +202,13 @@ int build_tables(const chem_mechanism *m, MechTables *t) {
     t->f.troe_T2[j] = (float)t->troe_T2[j];
     for (int k = 0; k < NSP; ++k) t->f.effm1[j][k] = (float)t->effm1[j][k];
   }
+  for (int r = 0; r < 2; ++r)
+    for (int k = 0; k < NSP; ++k) {
+      for (int i = 0; i < 6; ++i) t->f.ec[r][k][i] = (float)t->ec[r][k][i];
+      for (int i = 0; i < 7; ++i) t->f.gc[r][k][i] = (float)t->gc[r][k][i];
+    }
+  t->f.T_mid = (float)t->T_mid;
+  t->f.ln_R_over_Pref = (float)t->ln_R_over_Pref;
   return CHEM_OK;
 }
 

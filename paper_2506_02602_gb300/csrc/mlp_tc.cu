@@ -142,6 +142,31 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// The same load without the wait, and the wait that completes it: the wait takes the
+// registers as in/out operands, so the compiler cannot use them before it.  Lets the
+// next chunk's load overlap the current chunk's arithmetic.
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait32(uint32_t (&r)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
   asm volatile(
@@ -358,20 +383,26 @@ __global__ void __launch_bounds__(TTHREADS, 1) k_mlp_tc(const __grid_constant__ 
       // 4. epilogue
       if (layer < 3) {
         const float *bl = sbias + layer * kSurHidden;
-#pragma unroll 1
-        for (int cc = 0; cc < COLS_PER_WARP / 32; ++cc) {
-          const int col0 = cblk * COLS_PER_WARP + cc * 32;
-          float v[32];
-          tmem_ld32(t_lane + (uint32_t)col0, v);
+        static_assert(COLS_PER_WARP == 64, "two 32-column chunks per warp");
+        uint32_t ra[32], rb[32];
+        const int colA = cblk * COLS_PER_WARP, colB = colA + 32;
+        tmem_ld32_async(t_lane + (uint32_t)colA, ra);
+        tmem_wait32(ra);
+        tmem_ld32_async(t_lane + (uint32_t)colB, rb);  // overlaps the first chunk's math
+        auto emit = [&](const uint32_t(&r)[32], int col0) {
 #pragma unroll
           for (int g = 0; g < 4; ++g) {
             __align__(16) __nv_bfloat16 hb[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) hb[i] = __float2bfloat16(gelu_f(v[g * 8 + i] + bl[col0 + g * 8 + i]));
+            for (int i = 0; i < 8; ++i)
+              hb[i] = __float2bfloat16(gelu_f(__uint_as_float(r[g * 8 + i]) + bl[col0 + g * 8 + i]));
             *reinterpret_cast<uint4 *>(sm + SM_H + core_off(row, col0 + g * 8, kSurHidden)) =
                 *reinterpret_cast<const uint4 *>(hb);
           }
-        }
+        };
+        emit(ra, colA);
+        tmem_wait32(rb);
+        emit(rb, colB);
       } else if (cblk == 0) {
         float v[16];
         tmem_ld16(t_lane, v);

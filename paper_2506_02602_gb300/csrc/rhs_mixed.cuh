@@ -39,10 +39,11 @@ __device__ __forceinline__ float troe_F_f32(const MechTables &mt, float T, float
   }
 }
 
-template <int J>
+// G: the precision of the Gibbs functions and ln(1/K_c) (double in the mixed variant,
+// float in the all-fp32 right-hand side of the surrogate's error judge).
+template <int J, typename G>
 __device__ __forceinline__ void reaction_mixed(const MechTables &mt, const RateInputsF &in,
-                                               const double (&g)[NSP], double lnRTP,
-                                               float (&wdot)[NSP]) {
+                                               const G (&g)[NSP], G lnRTP, float (&wdot)[NSP]) {
   constexpr RxStruct R = kRx[J];
   constexpr int dnu = n_prod(R) - n_reac(R);
   float lnkf = fmaf(mt.f.beta[J], in.lnT, mt.f.lnA[J]) - mt.f.Ta[J] * in.invT;
@@ -65,8 +66,8 @@ __device__ __forceinline__ void reaction_mixed(const MechTables &mt, const RateI
   if constexpr (R.r1 >= 0) qf *= in.c[R.r1];
   float q = qf;
   if (mt.reversible[J]) {
-    // ln(1/K_c) in fp64: products' g minus reactants' g plus (sum nu) ln(R_u T / p_ref)
-    double lnQ = g[R.p0] - g[R.r0];
+    // ln(1/K_c) in G: products' g minus reactants' g plus (sum nu) ln(R_u T / p_ref)
+    G lnQ = g[R.p0] - g[R.r0];
     if constexpr (R.p1 >= 0) lnQ += g[R.p1];
     if constexpr (R.r1 >= 0) lnQ -= g[R.r1];
     if constexpr (dnu == 1) lnQ += lnRTP;
@@ -83,12 +84,11 @@ __device__ __forceinline__ void reaction_mixed(const MechTables &mt, const RateI
   if constexpr (R.p1 >= 0) wdot[R.p1] += q;
 }
 
-template <int... J>
+template <typename G, int... J>
 __device__ __forceinline__ void all_reactions_mixed(const MechTables &mt, const RateInputsF &in,
-                                                    const double (&g)[NSP], double lnRTP,
-                                                    float (&wdot)[NSP],
+                                                    const G (&g)[NSP], G lnRTP, float (&wdot)[NSP],
                                                     std::integer_sequence<int, J...>) {
-  (reaction_mixed<J>(mt, in, g, lnRTP, wdot), ...);
+  (reaction_mixed<J, G>(mt, in, g, lnRTP, wdot), ...);
 }
 
 // dY/dt (fp32) of one cell at fixed (rho, e) from the fp32 stage state U.
@@ -127,6 +127,82 @@ __device__ __forceinline__ bool cell_rhs_mixed(const MechTables &mt, const float
   all_reactions_mixed(mt, in, g, lnRTP, wdot, std::make_integer_sequence<int, NRX>{});
 #pragma unroll
   for (int k = 0; k < NSP; ++k) F[k] = wdot[k] * mt.f.W[k] * invRho_f;
+  return true;
+}
+
+// Temperature from e/R_u and Y/W entirely in fp32 (for the error judge): Newton from T
+// (1500 K if not positive and finite), |dT| <= 2e-6 T within 12 iterations; false on
+// no convergence or a non-positive / non-finite iterate (the judge then rejects).
+__device__ __forceinline__ bool solve_T_f32(const MechTables &mt, const float (&yw)[NSP], float eR, float &T) {
+  float Tn = (isfinite(T) && T > 0.0f) ? T : 1500.0f;
+  int range = -1;
+  float m[6], d[5];
+  for (int it = 0; it < 12; ++it) {
+    const int r = Tn >= mt.f.T_mid;
+    if (r != range) {
+      range = r;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        float s = 0.0f;
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) s = fmaf(yw[k], mt.f.ec[range][k][i], s);
+        m[i] = s;
+      }
+      d[0] = m[0];
+      d[1] = 2.0f * m[1];
+      d[2] = 3.0f * m[2];
+      d[3] = 4.0f * m[3];
+      d[4] = 5.0f * m[4];
+    }
+    const float eT = fmaf(Tn, fmaf(Tn, fmaf(Tn, fmaf(Tn, fmaf(Tn, m[4], m[3]), m[2]), m[1]), m[0]), m[5]);
+    const float cv = fmaf(Tn, fmaf(Tn, fmaf(Tn, fmaf(Tn, d[4], d[3]), d[2]), d[1]), d[0]);
+    const float dT = (eT - eR) / cv;
+    Tn -= dT;
+    if (!isfinite(Tn) || Tn <= 0.0f) return false;
+    if (fabsf(dT) <= 2e-6f * Tn) {
+      T = Tn;
+      return true;
+    }
+  }
+  return false;
+}
+
+// dY/dt of one cell entirely in fp32 (temperature, Gibbs functions and ln(1/K_c)
+// included): the right-hand side of the surrogate's error judge, an estimator that
+// needs relative accuracy far coarser than fp32's.  T: in = guess, out = solved T.
+__device__ __forceinline__ bool cell_rhs_f32(const MechTables &mt, const float (&U)[NSP], float rho,
+                                             float invRho, float eR, float &T, float (&F)[NSP]) {
+  float yw[NSP];
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) yw[k] = U[k] * mt.f.invW[k];
+  if (!solve_T_f32(mt, yw, eR, T)) return false;
+  const float lnT = logf(T);
+  const float invT = 1.0f / T;
+  const float oml = 1.0f - lnT;
+  const int range = T >= mt.f.T_mid;
+  float g[NSP];
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) {
+    const float *gc = mt.f.gc[range][k];
+    const float gk = fmaf(T, fmaf(T, fmaf(T, fmaf(T, gc[4], gc[3]), gc[2]), gc[1]), fmaf(gc[5], invT, gc[6]));
+    g[k] = fmaf(gc[0], oml, gk);
+  }
+  const float lnRTP = lnT + mt.f.ln_R_over_Pref;
+  RateInputsF in;
+  in.lnT = lnT;
+  in.invT = invT;
+  in.T = T;
+  float ctot = 0.0f, wdot[NSP];
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) {
+    in.c[k] = fmaxf(rho * yw[k], 0.0f);
+    ctot += in.c[k];
+    wdot[k] = 0.0f;
+  }
+  in.ctot = ctot;
+  all_reactions_mixed(mt, in, g, lnRTP, wdot, std::make_integer_sequence<int, NRX>{});
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) F[k] = wdot[k] * mt.f.W[k] * invRho;
   return true;
 }
 

@@ -162,53 +162,45 @@ __global__ void k_normalize(int64_t n, int ncol, int ld, float *A, const float *
 
 // Temperature-error estimate of a surrogate result y1 (see the file comment): returns
 // false if a right-hand side fails, else sets dT = est (K) and rate = dt * the largest
-// relative rate of change at either end.
-// The right-hand sides use the context's variant (fp32 rates in the mixed one).
-template <int V>
+// relative rate of change at either end.  All in fp32 (cell_rhs_f32), whatever the
+// context's variant: an estimate compared with a tolerance of 5e-4 T needs nothing
+// finer; y1 - y0 is formed in fp64 first, so the defect does not lose it to rounding.
 __device__ __noinline__ bool judge_defect(const MechTables &mt, const double (&y0)[NSP],
-                                          const double (&y1)[NSP], double rho, double eR,
-                                          double T0, double T1, double dt, double &dT,
-                                          double &rate) {
-  double F0[NSP], F1[NSP];
-  double Ta = T0, Tb = T1;
-  const double invRho = 1.0 / rho;
-  bool ok;
-  if constexpr (V == CHEM_VARIANT_MIXED) {
-    float u0[NSP], u1[NSP], f0[NSP], f1[NSP];
-#pragma unroll
-    for (int k = 0; k < NSP; ++k) {
-      u0[k] = (float)y0[k];
-      u1[k] = (float)y1[k];
-    }
-    ok = cell_rhs_mixed(mt, u0, (float)rho, (float)invRho, eR, Ta, f0) &&
-         cell_rhs_mixed(mt, u1, (float)rho, (float)invRho, eR, Tb, f1);
-#pragma unroll
-    for (int k = 0; k < NSP; ++k) {
-      F0[k] = f0[k];
-      F1[k] = f1[k];
-    }
-  } else {
-    ok = cell_rhs(mt, y0, rho, invRho, eR, Ta, F0) && cell_rhs(mt, y1, rho, invRho, eR, Tb, F1);
-  }
-  if (!ok) return false;
-  const int range = T1 >= mt.T_mid;
-  double yw[NSP], m[6], d[5], r = 0.0, s = 0.0;
-#pragma unroll
-  for (int k = 0; k < NSP; ++k) yw[k] = y1[k] * mt.invW[k];
-  mix_ecoef(mt, range, yw, m);
-  cv_coef(m, d);
-  const double cvR = cv_over_R(d, T1);
+                                          const double (&y1)[NSP], double rho, double eR_d,
+                                          double T0, double T1, double dt, double &dT, double &rate) {
+  float u0[NSP], u1[NSP], F0[NSP], F1[NSP];
 #pragma unroll
   for (int k = 0; k < NSP; ++k) {
-    const double *c = mt.ec[range][k];
-    const double ukR = fma(T1, fma(T1, fma(T1, fma(T1, fma(T1, c[4], c[3]), c[2]), c[1]), c[0]), c[5]) * mt.invW[k];
-    const double defect = y1[k] - (y0[k] + 0.5 * dt * (F0[k] + F1[k]));
-    s = fma(fabs(ukR - eR), fabs(defect), s);
-    r = fmax(r, fmax(fabs(F0[k]) / (fabs(y0[k]) + 1e-6), fabs(F1[k]) / (fabs(y1[k]) + 1e-6)));
+    u0[k] = (float)y0[k];
+    u1[k] = (float)y1[k];
   }
-  rate = dt * r;
-  dT = s / cvR;
-  return isfinite(dT) && cvR > 0.0;
+  const float rho_f = (float)rho, invRho_f = (float)(1.0 / rho), eR = (float)eR_d;
+  float Ta = (float)T0, Tb = (float)T1;
+  if (!cell_rhs_f32(mt, u0, rho_f, invRho_f, eR, Ta, F0) || !cell_rhs_f32(mt, u1, rho_f, invRho_f, eR, Tb, F1))
+    return false;
+  const float T1f = (float)T1, hdt = 0.5f * (float)dt;
+  const int range = T1f >= mt.f.T_mid;
+  float m[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) {
+    const float yw = u1[k] * mt.f.invW[k];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) m[i] = fmaf(yw, mt.f.ec[range][k][i], m[i]);
+  }
+  const float cvR = fmaf(T1f, fmaf(T1f, fmaf(T1f, fmaf(T1f, 5.0f * m[4], 4.0f * m[3]), 3.0f * m[2]), 2.0f * m[1]), m[0]);
+  float r = 0.0f, sum = 0.0f;
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) {
+    const float *c = mt.f.ec[range][k];
+    const float ukR =
+        fmaf(T1f, fmaf(T1f, fmaf(T1f, fmaf(T1f, fmaf(T1f, c[4], c[3]), c[2]), c[1]), c[0]), c[5]) * mt.f.invW[k];
+    const float defect = (float)(y1[k] - y0[k]) - hdt * (F0[k] + F1[k]);
+    sum = fmaf(fabsf(ukR - eR), fabsf(defect), sum);
+    r = fmaxf(r, fmaxf(fabsf(F0[k]) / (fabsf(u0[k]) + 1e-6f), fabsf(F1[k]) / (fabsf(u1[k]) + 1e-6f)));
+  }
+  rate = dt * (double)r;
+  dT = (double)(sum / cvR);
+  return isfinite(dT) && cvR > 0.0f;
 }
 
 // The inference epilogue, one thread per cell.  Takes the network output O [n x 16]
@@ -310,7 +302,7 @@ __global__ void __launch_bounds__(128)
   if (!reason && !(tok && fabs(T1 - (double)x[0]) <= (double)sc.max_dT)) reason = kFbTemperature;
   if (!reason && sc.judge_tol > 0.0f) {
     double dT = 0.0, rate = 0.0;
-    const bool jok = judge_defect<V>(mt, y0, y1, rho[i], e[i] / R_U, (double)x[0], T1, dt, dT, rate);
+    const bool jok = judge_defect(mt, y0, y1, rho[i], e[i] / R_U, (double)x[0], T1, dt, dT, rate);
     if (!jok || !(sc.judge_rate < 0.0f || rate <= (double)sc.judge_rate)) reason = kFbReactive;
     else if (!(dT <= (double)sc.judge_tol * T1)) reason = kFbJudge;
   }
