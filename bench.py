@@ -15,6 +15,14 @@ steps; the headline is the fastest variant whose error against the FP64 result m
 its stated bound (mixed: 1e-5, hybrid: 1e-3 relative on T).  Every variant's rate,
 error and roofline fraction is in "variants".
 
+The shock-bubble leg ("shock_bubble") is the full hybrid on the 256^3 reactive
+shock-bubble field (chem_inputs.workloads.shock_bubble: 16.7M cells, AMR-like levels
+with 2^l substeps of 1e-8 / 2^l s): the surrogate, trained on the field's own state
+family (workloads.bubble_trajectory_starts), with its judge and the persistent
+work-stealing integrator (mixed precision) for the cells it rejects, per level,
+against plain fp64 and mixed batched integration of the whole field in one persistent
+launch.
+
 The surrogate leg ("surrogate") is the learned part's own workload: 48,000 seeded 0D
 ignition trajectories (phi U[0.5, 2], T0 U[900, 2200] K, p U[1, 30] atm) recorded by the
 GPU integrator, 2M (state, dt ~ logU[1e-9, 1e-7] s) -> state training pairs from 90 % of
@@ -66,6 +74,8 @@ def parse():
     ap.add_argument("--sur-traj", type=int, default=48000)
     ap.add_argument("--sur-epochs", type=int, default=100)
     ap.add_argument("--sur-cells", type=int, default=1 << 24)
+    ap.add_argument("--no-bubble", action="store_true", help="skip the shock-bubble hybrid leg")
+    ap.add_argument("--bubble-n", type=int, default=256)
     ap.add_argument("--cpu-sample", type=int, default=131072)
     ap.add_argument("--ref-sample", type=int, default=32768)
     return ap.parse_args()
@@ -250,6 +260,69 @@ def fallback_reasons(mask):
     counts = torch.bincount(mask.long().flatten(), minlength=7).cpu().numpy()
     n = max(int(mask.numel()), 1)
     return {name: float(counts[i + 1]) / n for i, name in enumerate(FALLBACK_REASONS)}
+
+
+def shock_bubble_leg(args, mech, dev, stream):
+    """The full hybrid on the shock-bubble field (module docstring)."""
+    import torch
+    from chem_inputs import workloads
+    from paper_2506_02602_gb300 import chem, surrogate
+    out = {}
+    t0 = time.perf_counter()
+    b = workloads.shock_bubble(args.bubble_n)
+    n = b["T"].size
+    plain = chem.Context(mech, "fp64")
+    mixed = chem.Context(mech, "mixed")
+    f64 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    T0, Y0 = f64(b["T"]), f64(b["Y"])
+    rho, e = plain.state_from_TPY(T0, f64(b["p"]), Y0)
+    del b["p"]
+    off = torch.tensor(b["box_offset"], dtype=torch.int64, device=dev)
+    bdt = f64(b["box_dt"])
+    nsub = torch.tensor(b["box_nsub"], dtype=torch.int32, device=dev)
+    out["field"] = {"cells": int(n), "levels": [int(x) for x in np.diff(b["box_offset"])][::-1],
+                    "box_dt": [float(x) for x in b["box_dt"]][::-1], "setup_s": time.perf_counter() - t0}
+    # surrogate for this field's state family
+    t0 = time.perf_counter()
+    gen = chem.Context(mech, "fp64", max_steps=4000)
+    starts = workloads.bubble_trajectory_starts(16000, seed=5)
+    st = surrogate.trajectory_states(gen, 16000, seed=5, starts=starts)
+    gen.close()
+    pairs = surrogate.make_pairs(plain, st, seed=5, dt_lo=1e-9, dt_hi=1e-8, max_pairs=2_000_000)
+    hyb = chem.Context(mech, "mixed")
+    loss = hyb.surrogate_train(pairs["rho"], pairs["e"], pairs["Y0"], pairs["dt"], pairs["Y1"], T0=pairs["T0"],
+                               epochs=60, batch=4096, lr=1e-3, seed=1, dt_power=1.0)
+    torch.cuda.synchronize()
+    out["train"] = {"trajectories": 16000, "pairs": int(pairs["T0"].numel()), "epochs": 60,
+                    "loss_first_last": [float(loss[0]), float(loss[-1])], "seconds": time.perf_counter() - t0}
+    del pairs, st
+    Y, T = Y0.clone(), T0.clone()
+    mask = torch.empty(n, dtype=torch.uint8, device=dev)
+
+    def reset():
+        Y.copy_(Y0)
+        T.copy_(T0)
+
+    t_plain = timed(lambda: (reset(), plain.integrate_batched(rho, e, Y, T, off, bdt, nsub, RTOL, ATOL,
+                                                              stream=stream)), 2, stream)
+    Yr, Tr = Y.clone(), T.clone()
+    t_mixed = timed(lambda: (reset(), mixed.integrate_batched(rho, e, Y, T, off, bdt, nsub, RTOL, ATOL,
+                                                              stream=stream)), 2, stream)
+    rel_m = float(((T - Tr).abs() / Tr).max())
+    t_hyb = timed(lambda: (reset(), surrogate.hybrid_levels(hyb, rho, e, Y, T, b["box_offset"], b["box_dt"],
+                                                            b["box_nsub"], RTOL, ATOL, mask=mask, stream=stream)),
+                  2, stream)
+    rel = (T - Tr).abs() / Tr
+    out["plain_fp64"] = {"cells_per_s": n / (t_plain * 1e-3), "ms": t_plain}
+    out["mixed"] = {"cells_per_s": n / (t_mixed * 1e-3), "ms": t_mixed, "max_rel_T": rel_m}
+    out["hybrid"] = {"cells_per_s": n / (t_hyb * 1e-3), "ms": t_hyb, "max_rel_T": float(rel.max()),
+                     "fallback_frac_last_substep": float((mask != 0).float().mean()),
+                     "fallback_reasons_last_substep": fallback_reasons(mask),
+                     "speedup_vs_plain_fp64": t_plain / t_hyb, "speedup_vs_mixed": t_mixed / t_hyb}
+    out["stated_error_T"] = 1e-3
+    for c in (plain, mixed, hyb):
+        c.close()
+    return out
 
 
 def surrogate_leg(args, mech, dev, stream):
@@ -574,6 +647,10 @@ def run_ours(args, rank, world, local):
     e2e_el, = max_over_ranks([e2e_el], world, dev)
     e2e_match = bool(np.array_equal(hY, res[head]["Y"]) and np.array_equal(hT, res[head]["T"]))
 
+    bubble = None
+    if not args.no_bubble:
+        bubble = shock_bubble_leg(args, mech, dev, stream)
+
     amr = None
     if not args.no_amr:
         amr = amr_leg(ctxs["mixed" if head == "hybrid" else head], max(2, min(args.steps, 3)), dev)
@@ -605,6 +682,7 @@ def run_ours(args, rank, world, local):
             "gpu_launches": args.steps * sum(1 if v != "hybrid" else 4 for v, _ in variants),
             "amr_batch": amr,
             "surrogate": sur,
+            "shock_bubble": bubble,
             "clocks": clk,
             "cpu_baseline": cpu,
             "parity_vs_oracle_sample": parity,

@@ -211,3 +211,73 @@ def log_uniform_dt(n, lo=1e-9, hi=1e-7, seed=3):
     """Step sizes drawn log-uniformly in [lo, hi]."""
     r = _rng(seed + 1000)
     return np.exp(r.uniform(np.log(lo), np.log(hi), n))
+
+
+def _bubble_mole(f):
+    """Mole fractions across the bubble interface: a fraction f of stoichiometric H2-O2
+    diluted by 70 % N2 (H2 : O2 : N2 = 0.2 : 0.1 : 0.7), the rest N2."""
+    f = np.asarray(f, dtype=np.float64)
+    X = np.zeros((len(_mech.SPECIES),) + f.shape)
+    X[IDX["H2"]] = 0.2 * f
+    X[IDX["O2"]] = 0.1 * f
+    X[IDX["N2"]] = 0.7 * f + (1.0 - f)
+    return X
+
+
+def shock_bubble(n=256, seed=4, dt=1e-8, fractions=(0.25, 0.08, 0.02)):
+    """Reactive shock-bubble field on n^3 cells (cell index (z n + y) n + x before the
+    level ordering below).  A sphere of radius 48 n/256 cells centred in the box holds
+    stoichiometric H2-O2 diluted 70 % by mole with N2, with a tanh interface of width
+    3 n/256 cells, in N2.  The half domain x < n/2 is shock-compressed (1500 K, 20 atm),
+    the rest is at 300 K, 1 atm; T and p carry +-0.5 % seeded noise.
+
+    AMR-like levels: cells are ranked by their distance to the two fronts (the shock
+    plane and the bubble surface, where the gradients are); the nearest fractions[2]
+    of the cells are level 3, the next up to fractions[1] level 2, up to fractions[0]
+    level 1, the rest level 0.  Level l takes 2^l substeps of dt / 2^l.  The cells are
+    returned ordered by level (stable within a level), one box per level: box_offset,
+    box_dt, box_nsub as in amr_batch; `perm` maps a returned cell to its grid index."""
+    r = _rng(seed)
+    s = n / 256.0
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    x, y, z = x.ravel() + 0.5, y.ravel() + 0.5, z.ravel() + 0.5
+    c = n / 2.0
+    rad = np.sqrt((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2)
+    del y, z
+    R, w = 48.0 * s, 3.0 * s
+    f = 0.5 * (1.0 - np.tanh((rad - R) / w))
+    shocked = x < c
+    N = x.size
+    T = np.where(shocked, 1500.0, 300.0) * (1.0 + 0.005 * r.uniform(-1.0, 1.0, N))
+    p = np.where(shocked, 20.0, 1.0) * ATM * (1.0 + 0.005 * r.uniform(-1.0, 1.0, N))
+    Y = mass_from_mole(_bubble_mole(f))
+    dist = np.minimum(np.abs(x - c), np.abs(rad - R))
+    del x, rad
+    order = np.argsort(dist, kind="stable")
+    level = np.zeros(N, dtype=np.int32)
+    n3, n2, n1 = (int(round(fr * N)) for fr in (fractions[2], fractions[1], fractions[0]))
+    level[order[:n1]] = 1
+    level[order[:n2]] = 2
+    level[order[:n3]] = 3
+    perm = np.argsort(-level, kind="stable")  # level 3 first: the stiffest boxes lead
+    counts = np.bincount(level, minlength=4)[::-1]
+    box_offset = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    levels = np.arange(3, -1, -1)
+    return {"T": T[perm], "p": p[perm], "Y": np.ascontiguousarray(Y[:, perm]), "level": level[perm],
+            "perm": perm, "box_offset": box_offset, "box_dt": dt / 2.0 ** levels,
+            "box_nsub": (2 ** levels).astype(np.int32), "fuel": f[perm]}
+
+
+def bubble_trajectory_starts(ntraj, seed=5):
+    """Initial states of the shock-bubble field's family for surrogate training: fuel
+    fraction f across the interface (a quarter pure N2, f = 0; a quarter log-uniform in
+    [1e-12, 1], the tanh tail of the interface; the rest U[0, 1]); half shocked (1500 K,
+    20 atm), half not (300 K, 1 atm); +-2 % uniform noise on T and p."""
+    r = _rng(seed)
+    u = r.uniform(0.0, 1.0, ntraj)
+    f = np.where(u < 0.25, 0.0, np.where(u < 0.5, 10.0 ** r.uniform(-12.0, 0.0, ntraj),
+                                         r.uniform(0.0, 1.0, ntraj)))
+    shocked = r.uniform(0.0, 1.0, ntraj) < 0.5
+    T = np.where(shocked, 1500.0, 300.0) * (1.0 + 0.02 * r.uniform(-1.0, 1.0, ntraj))
+    p = np.where(shocked, 20.0, 1.0) * ATM * (1.0 + 0.02 * r.uniform(-1.0, 1.0, ntraj))
+    return {"T": T, "p": p, "Y": mass_from_mole(_bubble_mole(f)), "fuel": f}

@@ -380,7 +380,8 @@ int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
  * (judge_rate), since along a growing mode with dt * lambda = 2 the defect does not
  * see an error.
  * Accepted cells get the projected Y, its T, status CHEM_CELL_OK and nsteps 0; rejected
- * cells are integrated with rtol, atol (one thread per cell, the context's variant) and
+ * cells are integrated with rtol, atol by the persistent work-stealing kernel of
+ * chem_integrate_batched (the fallback list is its queue; the context's variant) and
  * get status CHEM_CELL_SURROGATE, or the integrator's failure code, and their attempted
  * steps.  d_fallback_mask (nullable, device uint8 [ncells]) receives 0 for accepted
  * cells and, for rejected ones, the first gate that failed: 1 feature outside the

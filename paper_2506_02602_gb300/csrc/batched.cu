@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_lsrk_persistent(const __grid_co
   bool need = true;
   int done_cells = 0, tot_acc = 0, tot_rej = 0, tot_rhs = 0, max_steps = 0;
   int hist[6] = {0, 0, 0, 0, 0, 0};
+  const unsigned long long nq = a.nq_dev ? (unsigned long long)*a.nq_dev : (unsigned long long)a.n;
   for (;;) {
     const unsigned needmask = __ballot_sync(FULL, need);
     if (needmask) {
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_lsrk_persistent(const __grid_co
       if (need) {
         need = false;
         const unsigned long long slot = base + __popc(needmask & ((1u << lane) - 1u));
-        if (slot < (unsigned long long)a.n) {
+        if (slot < nq) {
           cell = order ? (int64_t)order[slot] : (int64_t)slot;
           const int b = find_box(a.box_off, a.nboxes, cell);
           sub_left = a.box_nsub[b];
@@ -182,14 +183,15 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_lsrk_persistent(const __grid_co
           for (int k = 0; k < NSP; ++k) a.Y[k * a.ld + cell] = c.X[k];
           a.T[cell] = c.T;
           if (a.h) a.h[cell] = c.h;
-          if (a.status) a.status[cell] = c.status;
+          if (a.status) a.status[cell] = c.status == CHEM_CELL_OK ? a.ok_status : c.status;
           if (a.nsteps) a.nsteps[cell] = c.nacc + c.nrej;
           ++done_cells;
           tot_acc += c.nacc;
           tot_rej += c.nrej;
           tot_rhs += c.nrhs;
           max_steps = max(max_steps, c.nacc + c.nrej);
-          if (c.status >= 0 && c.status < 6) ++hist[c.status];
+          const int hs = c.status == CHEM_CELL_OK ? a.ok_status : c.status;
+          if (hs >= 0 && hs < 6) ++hist[hs];
           cell = -1;
           need = true;
         }
@@ -276,6 +278,24 @@ static void launch_persistent(int shape, unsigned grid, cudaStream_t st, const M
     case 5: launch_persistent_t<V, 256, 2>(grid, st, mt, a, p, order, cursor); break;
     default: launch_persistent_t<V, 128, 2>(grid, st, mt, a, p, order, cursor); break;
   }
+}
+
+cudaError_t launch_persistent_queue(int variant, const MechTables &mt, const BatchArgs &a,
+                                    const StepParams &p, const int32_t *order,
+                                    unsigned long long *cursor, cudaStream_t st) {
+  if (a.n <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  int sms = 0, pblock = 0, per = 0, regs = 0;
+  e = persistent_shape(variant, 0, &pblock, &per, &regs, &sms);
+  if (e != cudaSuccess) return e;
+  const int64_t cap_ctas = (int64_t)sms * per, need = (a.n + pblock - 1) / pblock;
+  const unsigned grid = (unsigned)(cap_ctas < need ? cap_ctas : need);
+  if (variant == CHEM_VARIANT_MIXED)
+    launch_persistent<CHEM_VARIANT_MIXED>(0, grid, st, mt, a, p, order, cursor);
+  else
+    launch_persistent<CHEM_VARIANT_FP64>(0, grid, st, mt, a, p, order, cursor);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_batched(int variant, const MechTables &mt, const BatchArgs &a,

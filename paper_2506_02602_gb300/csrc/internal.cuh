@@ -50,6 +50,10 @@ struct BatchArgs {
   int32_t nboxes;
   const int32_t *cost_hint;
   chem_stats *stats;
+  // queue length read on the device (nullable: the queue holds n cells); lets a queue
+  // built on the device (the surrogate's fallback list) run without a host round trip
+  const unsigned int *nq_dev;
+  int32_t ok_status;  // status written for cells that finish OK (CHEM_CELL_OK unless set)
 };
 
 // Context-owned queue scratch of the batched path.
@@ -74,6 +78,11 @@ void surrogate_destroy(void *sur);
 cudaError_t launch_batched(int variant, const MechTables &mt, const BatchArgs &a,
                            const StepParams &p, const BatchScratch &s, int order_mode,
                            int ctas_per_sm, int shape, cudaStream_t st);
+// The persistent kernel over a given queue of cell indices (order[0 .. queue length))
+// with the default shape and all resident CTAs; resets the cursor first.
+cudaError_t launch_persistent_queue(int variant, const MechTables &mt, const BatchArgs &a,
+                                    const StepParams &p, const int32_t *order,
+                                    unsigned long long *cursor, cudaStream_t st);
 // Threads per CTA, resident CTAs per SM, registers per thread of a persistent-kernel
 // shape, and the device's SM count.
 cudaError_t persistent_shape(int variant, int shape, int *block, int *ctas_per_sm, int *regs, int *num_sms);

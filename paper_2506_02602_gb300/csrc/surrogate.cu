@@ -47,6 +47,11 @@ struct Surrogate {
   // the weights in the tensor-core kernel's layout (repacked when the weights change)
   unsigned char *Wpk = nullptr;
   bool packed = false;
+  // the fallback's one-box batch and queue cursor (persistent work-stealing kernel)
+  int64_t *box_off = nullptr;
+  double *box_dt = nullptr;
+  int32_t *box_nsub = nullptr;
+  unsigned long long *cursor = nullptr;
   int *tc_err = nullptr;  // error word of the tensor-core kernel (a wait ran out)
 };
 
@@ -68,6 +73,10 @@ static void free_surrogate(Surrogate *s) {
   cudaFree(s->fb_count);
   cudaFree(s->Wpk);
   cudaFree(s->tc_err);
+  cudaFree(s->box_off);
+  cudaFree(s->box_dt);
+  cudaFree(s->box_nsub);
+  cudaFree(s->cursor);
   delete s;
 }
 
@@ -116,6 +125,10 @@ static cudaError_t alloc_params(Surrogate *s) {
   SCHK(cudaMalloc(&s->fb_count, sizeof(unsigned int)));
   SCHK(cudaMalloc(&s->Wpk, packed_weight_bytes()));
   SCHK(cudaMalloc(&s->tc_err, sizeof(int)));
+  SCHK(cudaMalloc(&s->box_off, 2 * sizeof(int64_t)));
+  SCHK(cudaMalloc(&s->box_dt, sizeof(double)));
+  SCHK(cudaMalloc(&s->box_nsub, sizeof(int32_t)));
+  SCHK(cudaMalloc(&s->cursor, sizeof(unsigned long long)));
   SCHK(cudaMemset(s->tc_err, 0, sizeof(int)));
   return cudaSuccess;
 }
@@ -633,11 +646,15 @@ int chem_surrogate_infer(chem_ctx *ctx, const chem_state *state, int64_t n, doub
                                   state->d_nsteps ? state->d_nsteps + base : nullptr,
                                   d_mask ? d_mask + base : nullptr, s->fb_idx, s->fb_count, base, st);
   }
+  if (e == cudaSuccess) e = launch_one_box(s->box_off, s->box_dt, s->box_nsub, n, dt, st);
   if (e == cudaSuccess) {
-    CellArgs a{state->d_rho, state->d_e, state->d_Y, state->ldY, state->d_T, nullptr,
-               state->d_status, state->d_nsteps, n, d_stats};
-    StepParams p{dt, rtol, atol, chem_ctx_max_steps(ctx)};
-    e = launch_lsrk_indexed(chem_ctx_variant(ctx), mt, a, p, s->fb_idx, s->fb_count, n, st);
+    // the rejected cells: a queue (the fallback list, its length on the device) for the
+    // persistent work-stealing integrator, every cell one box of one step dt
+    BatchArgs a{state->d_rho, state->d_e, state->d_Y, state->ldY, state->d_T, nullptr,
+                state->d_status, state->d_nsteps, n, s->box_off, s->box_dt, s->box_nsub, 1,
+                nullptr, d_stats, s->fb_count, CHEM_CELL_SURROGATE};
+    StepParams p{0.0, rtol, atol, chem_ctx_max_steps(ctx)};
+    e = launch_persistent_queue(chem_ctx_variant(ctx), mt, a, p, s->fb_idx, s->cursor, st);
   }
   if (e == cudaSuccess && d_stats) e = launch_surrogate_stats(d_stats, n, s->fb_count, st);
   return e == cudaSuccess ? CHEM_OK : sur_cuda(ctx, e, "surrogate inference");

@@ -86,8 +86,8 @@ cudaError_t launch_pack_weights(const __nv_bfloat16 *const (&W)[kSurLayers], uns
 size_t packed_weight_bytes();
 cudaError_t launch_mlp_tc(int64_t n, const float *X, const float *norm, const unsigned char *Wpk,
                           const float *const (&b)[kSurLayers], float *O, int *err, cudaStream_t s);
-cudaError_t launch_lsrk_indexed(int variant, const MechTables &mt, const CellArgs &a,
-                                const StepParams &p, const int32_t *idx, const unsigned int *count,
-                                int64_t max_count, cudaStream_t s);
+// box_off = {0, n}, box_dt = {dt}, box_nsub = {1}: the fallback's one-box batch.
+cudaError_t launch_one_box(int64_t *box_off, double *box_dt, int32_t *box_nsub, int64_t n, double dt,
+                           cudaStream_t s);
 
 }  // namespace chem

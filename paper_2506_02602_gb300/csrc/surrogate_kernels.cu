@@ -1,7 +1,7 @@
 // surrogate_kernels.cu -- device kernels of the learned surrogate around the MLP:
 // featurisation, column statistics, the inference epilogue (inverse transform,
 // element-conservation projection, temperature solve, gate, fallback compaction) and
-// the index-driven fallback integration.
+// the one-box batch of the fallback integration.
 //
 // Features of a cell (12, padded to 16): T, ln p, log10 dt and the Box-Cox transforms
 // BC(Y_k) = (max(Y_k, 1e-30)^lam - 1) / lam of the 9 mass fractions; targets (9, padded
@@ -320,42 +320,13 @@ __global__ void __launch_bounds__(128)
   }
 }
 
-// Integrate the cells listed in idx[0 .. *count) in place (the surrogate's fallback);
-// threads past the count return at once, so no host synchronisation sizes the launch.
-// The per-cell arithmetic is cell.cuh's; status reports CHEM_CELL_SURROGATE for a
-// successful fallback (the cell was integrated instead), else the integrator's code.
-template <int V>
-__global__ void __launch_bounds__(128) k_lsrk_indexed(const __grid_constant__ MechTables mt,
-                                                      const CellArgs a, const StepParams p,
-                                                      const int32_t *__restrict__ idx,
-                                                      const unsigned int *count) {
-  load_math_tables();
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool live = t < (int64_t)*count;
-  CellState c;
-  c.nacc = c.nrej = c.nrhs = 0;
-  c.status = CHEM_CELL_OK;
-  int64_t i = -1;
-  if (live) {
-    i = idx[t];
-#pragma unroll
-    for (int k = 0; k < NSP; ++k) c.X[k] = a.Y[k * a.ld + i];
-    c.T = a.T[i];
-    c.h = CUDART_NAN;
-    cell_begin(c, a.rho[i], a.e[i], p.dt);
-    while (!c.done) cell_attempt<V>(mt, c, p);
-    cell_finish(mt, c);
-#pragma unroll
-    for (int k = 0; k < NSP; ++k) a.Y[k * a.ld + i] = c.X[k];
-    a.T[i] = c.T;
-    if (a.status) a.status[i] = c.status == CHEM_CELL_OK ? CHEM_CELL_SURROGATE : c.status;
-    if (a.nsteps) a.nsteps[i] = c.nacc + c.nrej;
-  }
-  if (a.stats) {
-    int hist[6];
-#pragma unroll
-    for (int s = 0; s < 6; ++s) hist[s] = live && (c.status == CHEM_CELL_OK ? s == CHEM_CELL_SURROGATE : c.status == s);
-    accumulate_stats(a.stats, live ? 1 : 0, c.nacc, c.nrej, c.nrhs, c.nacc + c.nrej, hist);
+// The one-box batch of the fallback integration: all n cells, step dt, one substep.
+__global__ void k_one_box(int64_t *box_off, double *box_dt, int32_t *box_nsub, int64_t n, double dt) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    box_off[0] = 0;
+    box_off[1] = n;
+    box_dt[0] = dt;
+    box_nsub[0] = 1;
   }
 }
 
@@ -437,14 +408,9 @@ cudaError_t launch_surrogate_finish(int variant, const MechTables &mt, const Sur
   return cudaGetLastError();
 }
 
-cudaError_t launch_lsrk_indexed(int variant, const MechTables &mt, const CellArgs &a,
-                                const StepParams &p, const int32_t *idx, const unsigned int *count,
-                                int64_t max_count, cudaStream_t s) {
-  if (max_count <= 0) return cudaSuccess;
-  if (variant == CHEM_VARIANT_MIXED)
-    k_lsrk_indexed<CHEM_VARIANT_MIXED><<<nblk(max_count, 128), 128, 0, s>>>(mt, a, p, idx, count);
-  else
-    k_lsrk_indexed<CHEM_VARIANT_FP64><<<nblk(max_count, 128), 128, 0, s>>>(mt, a, p, idx, count);
+cudaError_t launch_one_box(int64_t *box_off, double *box_dt, int32_t *box_nsub, int64_t n, double dt,
+                           cudaStream_t s) {
+  k_one_box<<<1, 32, 0, s>>>(box_off, box_dt, box_nsub, n, dt);
   return cudaGetLastError();
 }
 

@@ -19,7 +19,7 @@ from chem_inputs import workloads
 
 
 def trajectory_states(ctx, ntraj, seed=3, nstage=48, t0=1e-9, t_end=3e-3, nfine=16, post=5e-6,
-                      npost=8, device="cuda"):
+                      npost=8, device="cuda", starts=None):
     """States along ntraj ignition trajectories (dict of CUDA tensors rho, e, Y [S, m], T,
     plus the trajectory id and time of each state).
 
@@ -33,9 +33,11 @@ def trajectory_states(ctx, ntraj, seed=3, nstage=48, t0=1e-9, t_end=3e-3, nfine=
     post-ignition window is kept short).  A trajectory stops at the first pass-2
     integration that does not end with status 0; only status-0 states are recorded.
     Pass ctx a step limit of a few thousand (Context(..., max_steps=4000)): the cost of
-    every call is its stiffest cell's step count, run serially."""
+    every call is its stiffest cell's step count, run serially.  starts (optional): the
+    initial states {T, p, Y} (default: workloads.trajectory_starts(ntraj, seed))."""
     import torch
-    s = workloads.trajectory_starts(ntraj, seed=seed)
+    s = workloads.trajectory_starts(ntraj, seed=seed) if starts is None else starts
+    ntraj = len(s["T"])
     f64 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=device)
     T0 = f64(s["T"])
     rho, e = ctx.state_from_TPY(T0, f64(s["p"]), f64(s["Y"]))
@@ -178,3 +180,22 @@ def evaluate(ctx_sur, ctx_ref, states, dt, rtol=1e-6, atol=1e-10, gate=None, rep
             "max_abs_Y": float((Ys - Yr).abs().max().item()),
             "surrogate_cells_per_s": n / ts, "integrator_cells_per_s": n / tr, "speedup": tr / ts,
             "stats": stats.cpu().numpy().tolist()}
+
+
+def hybrid_levels(ctx, rho, e, Y, T, box_offset, box_dt, box_nsub, rtol=1e-6, atol=1e-10, gate=None,
+                  status=None, nsteps=None, mask=None, stream=None):
+    """One hydro step of a level-ordered field with the surrogate: for each box (cells
+    box_offset[b] .. box_offset[b+1], host arrays) box_nsub[b] chem_surrogate_infer calls
+    of box_dt[b] on that slice of the state (in place).  status / nsteps / mask receive
+    the last substep's values."""
+    import torch
+    for b in range(len(box_dt)):
+        a, z = int(box_offset[b]), int(box_offset[b + 1])
+        if z <= a:
+            continue
+        sl = slice(a, z)
+        for _ in range(int(box_nsub[b])):
+            ctx.surrogate_infer(rho[sl], e[sl], Y[:, sl], T[sl], float(box_dt[b]), rtol, atol,
+                                status=None if status is None else status[sl],
+                                nsteps=None if nsteps is None else nsteps[sl],
+                                mask=None if mask is None else mask[sl], gate=gate, stream=stream)
