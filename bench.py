@@ -23,6 +23,13 @@ work-stealing integrator (mixed precision) for the cells it rejects, per level,
 against plain fp64 and mixed batched integration of the whole field in one persistent
 launch.
 
+The Eq. 27 leg ("eq27") is the paper's own thread-divergence benchmark (Sec. 4.2.2,
+Eq. 27-28, Tables 4-5): 65,536 cells of H2 : O2 : N2 = 1 : 2 : 7 at 1 atm with the
+smooth (alpha = 1) and the divergent (alpha = 0.1) temperature profile, 100 successive
+steps of 1e-5 s (h and the temperature carried), timed as 100 chem_integrate calls and
+as one persistent launch with 100 substeps; the paper's V100 times (4.40 s and 5.12 s,
+its 13-species mechanism) are context, not a like-for-like target.
+
 The surrogate leg ("surrogate") is the learned part's own workload: 48,000 seeded 0D
 ignition trajectories (phi U[0.5, 2], T0 U[900, 2200] K, p U[1, 30] atm) recorded by the
 GPU integrator, 2M (state, dt ~ logU[1e-9, 1e-7] s) -> state training pairs from 90 % of
@@ -75,6 +82,7 @@ def parse():
     ap.add_argument("--sur-epochs", type=int, default=100)
     ap.add_argument("--sur-cells", type=int, default=1 << 24)
     ap.add_argument("--no-bubble", action="store_true", help="skip the shock-bubble hybrid leg")
+    ap.add_argument("--no-eq27", action="store_true", help="skip the Eq. 27 divergence benchmark leg")
     ap.add_argument("--bubble-n", type=int, default=256)
     ap.add_argument("--cpu-sample", type=int, default=131072)
     ap.add_argument("--ref-sample", type=int, default=32768)
@@ -260,6 +268,51 @@ def fallback_reasons(mask):
     counts = torch.bincount(mask.long().flatten(), minlength=7).cpu().numpy()
     n = max(int(mask.numel()), 1)
     return {name: float(counts[i + 1]) / n for i, name in enumerate(FALLBACK_REASONS)}
+
+
+def eq27_leg(mech, dev, stream):
+    """The Eq. 27 thread-divergence benchmark (module docstring)."""
+    import torch
+    from chem_inputs import workloads
+    from paper_2506_02602_gb300 import chem
+    out = {"cells": 65536, "steps": 100, "dt": 1e-5,
+           "paper_v100_s": {"alpha=1": 4.4032, "alpha=0.1": 5.1225}}
+    for variant in ("fp64", "mixed"):
+        ctx = chem.Context(mech, variant)
+        for alpha in (1.0, 0.1):
+            w = workloads.eq27_profile(alpha)
+            n = w["T"].size
+            f64 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+            T0, Y0 = f64(w["T"]), f64(w["Y"])
+            rho, e = ctx.state_from_TPY(T0, f64(w["p"]), Y0)
+            Y, T = Y0.clone(), T0.clone()
+            h = torch.empty(n, dtype=torch.float64, device=dev)
+            st = torch.empty(n, dtype=torch.int32, device=dev)
+
+            def calls():
+                Y.copy_(Y0); T.copy_(T0); h.fill_(float("nan"))
+                for _ in range(100):
+                    ctx.integrate(rho, e, Y, T, 1e-5, RTOL, ATOL, h=h, status=st, stream=stream)
+
+            off = torch.tensor([0, n], dtype=torch.int64, device=dev)
+            bdt = torch.tensor([1e-5], dtype=torch.float64, device=dev)
+            bsub = torch.tensor([100], dtype=torch.int32, device=dev)
+
+            def persistent():
+                Y.copy_(Y0); T.copy_(T0); h.fill_(float("nan"))
+                ctx.integrate_batched(rho, e, Y, T, off, bdt, bsub, RTOL, ATOL, h=h, status=st, stream=stream)
+
+            t_calls = timed(calls, 1, stream)
+            Tc, ok_c = T.clone(), bool((st == 0).all())
+            t_pers = timed(persistent, 1, stream)
+            out[f"{variant} alpha={alpha:g}"] = {
+                "calls_s": t_calls * 1e-3, "persistent_s": t_pers * 1e-3,
+                "cell_substeps_per_s": n * 100 / (min(t_calls, t_pers) * 1e-3),
+                "all_ok": ok_c and bool((st == 0).all()),
+                "max_rel_T_calls_vs_persistent": float(((T - Tc).abs() / Tc).max()),
+                "T_final_range_K": [float(T.min()), float(T.max())]}
+        ctx.close()
+    return out
 
 
 def shock_bubble_leg(args, mech, dev, stream):
@@ -647,6 +700,10 @@ def run_ours(args, rank, world, local):
     e2e_el, = max_over_ranks([e2e_el], world, dev)
     e2e_match = bool(np.array_equal(hY, res[head]["Y"]) and np.array_equal(hT, res[head]["T"]))
 
+    eq27 = None
+    if not args.no_eq27:
+        eq27 = eq27_leg(mech, dev, stream)
+
     bubble = None
     if not args.no_bubble:
         bubble = shock_bubble_leg(args, mech, dev, stream)
@@ -683,6 +740,7 @@ def run_ours(args, rank, world, local):
             "amr_batch": amr,
             "surrogate": sur,
             "shock_bubble": bubble,
+            "eq27": eq27,
             "clocks": clk,
             "cpu_baseline": cpu,
             "parity_vs_oracle_sample": parity,
