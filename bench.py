@@ -672,8 +672,13 @@ def run_ours(args, rank, world, local):
     d_Y, d_T = torch.empty_like(Y), torch.empty_like(T)
 
     def e2e_step():
+        """One step through the host-buffer path; returns its wall time.  Restoring the
+        host inputs (a benchmark artefact: an application hands over new data) is
+        outside the timed part; the host-device copies are inside."""
         hY[...] = h_Y0
         hT[...] = h_T0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         if head == "hybrid":  # no host entry point for the surrogate: copies in the timed region
             d_rho.copy_(h_rho, non_blocking=True)
             d_e.copy_(h_e, non_blocking=True)
@@ -689,14 +694,12 @@ def run_ours(args, rank, world, local):
         else:
             ctx.integrate_host(h_rho.numpy(), h_e.numpy(), hY, hT, DT, RTOL, ATOL,
                                status=h_st.numpy(), nsteps=h_ns.numpy(), stream=stream)
+        return time.perf_counter() - t0
 
     e2e_step()
     if world > 1:
         torch.distributed.barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        e2e_step()
-    e2e_el = time.perf_counter() - t0
+    e2e_el = sum(e2e_step() for _ in range(args.steps))
     e2e_el, = max_over_ranks([e2e_el], world, dev)
     e2e_match = bool(np.array_equal(hY, res[head]["Y"]) and np.array_equal(hT, res[head]["T"]))
 

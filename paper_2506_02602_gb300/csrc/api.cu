@@ -33,6 +33,10 @@ struct chem_ctx {
   size_t graph_key_len = 0;
   // learned surrogate (surrogate.cu), created by training or loading
   void *sur = nullptr;
+  // copy pipeline of chem_integrate_host: copy-in, copy-out and a second compute stream,
+  // and per-chunk events (created on first use)
+  cudaStream_t io[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev[3 * 8 + 2] = {};
 };
 
 namespace {
@@ -279,6 +283,10 @@ int chem_teardown(chem_ctx *ctx) {
   if (!ctx) return CHEM_OK;
   cudaDeviceSynchronize();
   if (ctx->host_scratch) cudaFree(ctx->host_scratch);
+  for (cudaStream_t &q : ctx->io)
+    if (q) cudaStreamDestroy(q);
+  for (cudaEvent_t &v : ctx->ev)
+    if (v) cudaEventDestroy(v);
   if (ctx->batch_scratch) cudaFree(ctx->batch_scratch);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -486,6 +494,59 @@ int chem_integrate_host(chem_ctx *ctx, int64_t n, const double *h_rho, const dou
     e = (call);                                          \
     if (e != cudaSuccess) return cuda_fail(ctx, e, what); \
   } while (0)
+  // Large calls: a chunked pipeline that overlaps the copies with the integration.
+  // Chunk c's cells go in on a copy-in stream, are integrated on one of two compute
+  // streams (the caller's and a private one, alternating, so one chunk's tail overlaps
+  // the next chunk's start), and come back on a copy-out stream; events order the
+  // three, and the caller's stream waits for the whole pipeline.
+  constexpr int kChunks = 4;
+  if (n >= (1 << 18)) {
+    for (cudaStream_t &q : ctx->io)
+      if (!q) CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking), "creating copy streams");
+    for (cudaEvent_t &v : ctx->ev)
+      if (!v) CK(cudaEventCreateWithFlags(&v, cudaEventDisableTiming), "creating events");
+    cudaStream_t in = ctx->io[0], out = ctx->io[1], comp2 = ctx->io[2];
+    cudaEvent_t ev_start = ctx->ev[3 * 8], ev_done = ctx->ev[3 * 8 + 1];
+    CK(cudaEventRecord(ev_start, s), "event");
+    CK(cudaStreamWaitEvent(in, ev_start, 0), "event wait");
+    CK(cudaStreamWaitEvent(comp2, ev_start, 0), "event wait");
+    const int64_t per = (n + kChunks - 1) / kChunks;
+    for (int c = 0; c < kChunks; ++c) {
+      const int64_t c0 = c * per, c1 = c0 + per < n ? c0 + per : n;
+      if (c1 <= c0) break;
+      const size_t m = (size_t)(c1 - c0), mb = m * sizeof(double);
+      cudaEvent_t ev_in = ctx->ev[3 * c], ev_comp = ctx->ev[3 * c + 1];
+      CK(cudaMemcpyAsync(d_rho + c0, h_rho + c0, mb, cudaMemcpyHostToDevice, in), "copy rho");
+      CK(cudaMemcpyAsync(d_e + c0, h_e + c0, mb, cudaMemcpyHostToDevice, in), "copy e");
+      CK(cudaMemcpyAsync(d_T + c0, h_T + c0, mb, cudaMemcpyHostToDevice, in), "copy T");
+      if (h_h) CK(cudaMemcpyAsync(d_h + c0, h_h + c0, mb, cudaMemcpyHostToDevice, in), "copy h");
+      CK(cudaMemcpy2DAsync(d_Y + c0, bytes, h_Y + c0, (size_t)ldY * sizeof(double), mb, NSP,
+                           cudaMemcpyHostToDevice, in), "copy Y");
+      CK(cudaEventRecord(ev_in, in), "event");
+      cudaStream_t cs = (c & 1) ? comp2 : s;
+      CK(cudaStreamWaitEvent(cs, ev_in, 0), "event wait");
+      CellArgs a{d_rho + c0, d_e + c0, d_Y + c0, (int64_t)nd, d_T + c0, h_h ? d_h + c0 : nullptr,
+                 d_status + c0, d_nsteps + c0, (int64_t)m, nullptr};
+      StepParams p{dt, rtol, atol, ctx->opt.max_steps};
+      CK(launch_lsrk(ctx->opt.variant, ctx->tables, a, p, ctx->opt.block_size, cs), "integration launch");
+      CK(cudaEventRecord(ev_comp, cs), "event");
+      CK(cudaStreamWaitEvent(out, ev_comp, 0), "event wait");
+      CK(cudaMemcpy2DAsync(h_Y + c0, (size_t)ldY * sizeof(double), d_Y + c0, bytes, mb, NSP,
+                           cudaMemcpyDeviceToHost, out), "copy Y back");
+      CK(cudaMemcpyAsync(h_T + c0, d_T + c0, mb, cudaMemcpyDeviceToHost, out), "copy T back");
+      if (h_h) CK(cudaMemcpyAsync(h_h + c0, d_h + c0, mb, cudaMemcpyDeviceToHost, out), "copy h back");
+      if (h_status)
+        CK(cudaMemcpyAsync(h_status + c0, d_status + c0, m * sizeof(int32_t), cudaMemcpyDeviceToHost, out),
+           "copy status back");
+      if (h_nsteps)
+        CK(cudaMemcpyAsync(h_nsteps + c0, d_nsteps + c0, m * sizeof(int32_t), cudaMemcpyDeviceToHost, out),
+           "copy nsteps back");
+    }
+    CK(cudaEventRecord(ev_done, out), "event");
+    CK(cudaStreamWaitEvent(s, ev_done, 0), "event wait");
+    CK(cudaStreamSynchronize(s), "synchronising");
+    return CHEM_OK;
+  }
   CK(cudaMemcpyAsync(d_rho, h_rho, bytes, cudaMemcpyHostToDevice, s), "copy rho");
   CK(cudaMemcpyAsync(d_e, h_e, bytes, cudaMemcpyHostToDevice, s), "copy e");
   CK(cudaMemcpyAsync(d_T, h_T, bytes, cudaMemcpyHostToDevice, s), "copy T");

@@ -178,6 +178,34 @@ def test_host_entry_matches_device_entry(ctx):
     np.testing.assert_array_equal(ns, dev["nsteps"])
 
 
+def test_host_entry_pipeline_matches_device_entry(ctx):
+    # 2^18 + 7 cells: the chunked copy/compute pipeline of the host entry (4 chunks,
+    # the last one ragged), with a padded Y pitch and the carried step h
+    d = W.detonation_slice(nx=512, ny=512)
+    n = 512 * 512 + 7
+    T0 = np.concatenate([d["T"], d["T"][:7]])
+    p = np.concatenate([d["p"], d["p"][:7]])
+    Y0 = np.concatenate([d["Y"], d["Y"][:, :7]], axis=1)
+    import torch
+    rho_d, e_d = ctx.state_from_TPY(to_dev(T0), to_dev(p), to_dev(Y0))
+    rho, e = rho_d.cpu().numpy(), e_d.cpu().numpy()
+    h0 = np.full(n, 1e-10)
+    dev = run_device(ctx, rho, e, Y0, T0, 2e-9, h=h0, ld=n + 5)
+    ld = n + 5
+    Y = np.zeros((Y0.shape[0], ld))
+    Y[:, :n] = Y0
+    T, h = T0.copy(), h0.copy()
+    st = np.zeros(n, np.int32)
+    ns = np.zeros(n, np.int32)
+    ctx.integrate_host(rho, e, Y, T, 2e-9, h=h, status=st, nsteps=ns)
+    np.testing.assert_array_equal(Y[:, :n], dev["Y"])
+    np.testing.assert_array_equal(Y[:, n:], 0.0)  # padding untouched
+    np.testing.assert_array_equal(T, dev["T"])
+    np.testing.assert_array_equal(h, dev["h"])
+    np.testing.assert_array_equal(st, dev["status"])
+    np.testing.assert_array_equal(ns, dev["nsteps"])
+
+
 def test_detonation_slice_full_size_sampled(ctx):
     # the full 1024 x 1024 slice in the benchmark's launch configuration; the oracle
     # integrates a seeded sample of cells one by one
