@@ -155,6 +155,20 @@ int build_tables(const chem_mechanism *m, MechTables *t) {
       t->gc[r][k][6] = -a[6];
     }
   }
+  {  // the largest |c_v' / c_v| of the tables on [200, 6000] K (1 K sampling)
+    double C = 0.0;
+    for (int k = 0; k < NSP; ++k)
+      for (int r = 0; r < 2; ++r) {
+        const double *a = r ? m->nasa_hi[k] : m->nasa_lo[k];
+        const double T0 = r ? Tmid : 200.0, T1 = r ? 6000.0 : Tmid;
+        for (double T = T0; T <= T1; T += 1.0) {
+          const double cv = a[0] - 1.0 + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
+          const double dcv = a[1] + T * (2.0 * a[2] + T * (3.0 * a[3] + T * 4.0 * a[4]));
+          if (cv > 0.1) C = std::fmax(C, std::fabs(dcv / cv));
+        }
+      }
+    t->newton_sq = C > 1e-6 ? 1e-12 / C : 1e-6;
+  }
   for (int j = 0; j < NRX; ++j) {
     t->A[j] = m->A[j];
     t->lnA[j] = std::log(m->A[j]);

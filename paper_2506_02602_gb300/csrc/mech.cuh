@@ -97,6 +97,10 @@ struct MechTables {
   double effm1[NRX][NSP];
   int32_t has_eff[NRX];
   double ln_R_over_Pref;  // ln(R_u / p_ref): ln(R_u T / p_ref) = ln T + this
+  // Newton's quadratic-convergence stop: after a step dT the remaining error is at most
+  // (C / 2) dT^2 with C = max |c_v' / c_v| of the tables on [200, 6000] K, so a step with
+  // dT^2 <= newton_sq T, newton_sq = 1e-12 / C, already leaves T within 1e-12 T / 2
+  double newton_sq;
   // element mass fraction (H, O, N) per unit mass fraction of species k:
   // n_ke A_e / sum_e' n_ke' A_e' (columns sum to 1, so conserving elements conserves sum Y)
   double Emat[3][NSP];

@@ -56,8 +56,10 @@ __device__ __forceinline__ void cv_coef(const double (&m)[6], double (&d)[5]) {
 }
 
 // Temperature from e/R_u and Y/W.  T: in = starting guess (1500 K if not positive and
-// finite), out = root.  Newton stops at |dT| <= 1e-12 T within 30 iterations; on a
-// non-positive / non-finite iterate or no convergence, bisection on [200, 6000] K.
+// finite), out = root.  Newton stops at |dT| <= 1e-12 T, or as soon as the quadratic
+// convergence bound guarantees that (dT^2 <= newton_sq T: the remaining error is then
+// below 1e-12 T / 2), within 30 iterations; on a non-positive / non-finite iterate or
+// no convergence, bisection on [200, 6000] K.
 __device__ __forceinline__ bool solve_T(const MechTables &mt, const double (&yw)[NSP], double eR,
                                      double &T) {
   double Tn = (isfinite(T) && T > 0.0) ? T : 1500.0;
@@ -75,7 +77,7 @@ __device__ __forceinline__ bool solve_T(const MechTables &mt, const double (&yw)
     const double dT = (e_over_R(m, Tn) - eR) / cv_over_R(d, Tn);
     Tn -= dT;
     if (!isfinite(Tn) || Tn <= 0.0) break;
-    if (fabs(dT) <= 1e-12 * Tn) {
+    if (fabs(dT) <= 1e-12 * Tn || dT * dT <= mt.newton_sq * Tn) {
       T = Tn;
       return true;
     }
