@@ -347,8 +347,8 @@ typedef struct {
   float resid_max;   /* [0.02] largest relative element-mass residual before projection */
   float neg_tol;     /* [1e-6] most negative mass fraction allowed after projection */
   float max_dT;      /* [200] largest accepted |T(t + dt) - T(t)|, K */
-  float judge_tol;   /* [5e-4] largest accepted error estimate relative to T (the trapezoid
-                        judge of chem_surrogate_infer); negative: no judge */
+  float judge_tol;   /* [5e-4] largest accepted error estimate relative to T (the
+                        quadrature judge of chem_surrogate_infer); negative: no judge */
   float judge_rate;  /* [1] largest dt * max_k |dY_k/dt| / (|Y_k| + 1e-6) at either end of
                         the step for the judge to accept; negative: no bound */
 } chem_surrogate_gate;
@@ -373,12 +373,12 @@ int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
  * Advance the state over dt with the surrogate (chem_state as in chem_integrate).  Per
  * cell: features -> network -> inverse transform -> fp64 projection -> fp64 temperature
  * -> gate (feature range, element residual, negativity, temperature solve, |dT|) ->
- * judge: with the integrator's right-hand side F0 = f(Y0), F1 = f(Y1), the trapezoidal
- * defect D = Y1 - Y0 - dt/2 (F0 + F1) gives the temperature-error estimate
- * sum_k |u_k(T1) - e| |D_k| / c_v(T1), which must not exceed judge_tol * T1 (u_k the
- * species internal energies per mass); and the step must be slow for the cell
- * (judge_rate), since along a growing mode with dt * lambda = 2 the defect does not
- * see an error.
+ * judge: with the integrator's right-hand side at Y0, Y1 and the Hermite midpoint
+ * Ym = (Y0 + Y1)/2 + dt/8 (F0 - F1), Simpson's defect D = Y1 - Y0 - dt/6 (F0 + 4 Fm + F1)
+ * gives the temperature-error estimate sum_k |u_k(T1) - e| |D_k| / c_v(T1), which must
+ * not exceed judge_tol * T1 (u_k the species internal energies per mass) times
+ * 1 - rate/2 + rate^2/12 (the defect's shrink factor along a growing mode); and the
+ * step must be slow for the cell (rate <= judge_rate, below).
  * Accepted cells get the projected Y, its T, status CHEM_CELL_OK and nsteps 0; rejected
  * cells are integrated with rtol, atol by the persistent work-stealing kernel of
  * chem_integrate_batched (the fallback list is its queue; the context's variant) and

@@ -12,20 +12,24 @@
 // sum Y too, in fp64.
 //
 // Error judge: the integrator's own right-hand side checks each candidate result.  With
-// F0 = f(Y0) and F1 = f(Y1) the trapezoidal corrector Yc = Y0 + dt/2 (F0 + F1) differs
-// from the exact solution by O(dt^3 |d3Y/dt3|) where the cell is smooth over dt, so the
+// F0 = f(Y0), F1 = f(Y1) and Fm = f(Ym) at the cubic Hermite midpoint
+// Ym = (Y0 + Y1) / 2 + dt/8 (F0 - F1), Simpson's rule Yc = Y0 + dt/6 (F0 + 4 Fm + F1)
+// differs from the exact solution by O(dt^5) where the cell is smooth over dt, so the
 // defect D = Y1 - Yc estimates the error of Y1.  At constant e the temperature moves by
 // -sum_k (u_k - e) dY_k / c_v for a change dY with sum_k dY_k = 0, so the judge takes
 //   est = sum_k |u_k(T1) - e| |D_k| / c_v(T1)
 // (no cancellation between species counted) and sends a cell with est > judge_tol * T1
 // to the integrator.  Stiff cells (dt beyond the fast time scales), where the
-// trapezoidal rule itself is not accurate, fail the check too.  Linearised, an error d
-// of Y1 shows in the defect as (I - dt/2 J) d, which vanishes along a growing mode with
-// dt * lambda = 2 (chain branching before ignition), so the judge also bounds the
-// cell's reactivity over the step,
-//   dt * max_k max(|F0_k| / (|Y0_k| + 1e-6), |F1_k| / (|Y1_k| + 1e-6)) <= judge_rate,
-// which keeps the factor at or above 1 - judge_rate / 2 (1e-6: the mass fraction below
-// which a species' share of the mixture energy is under ~1 K).
+// quadrature itself is not accurate, fail the check too.  Linearised, an error d of Y1
+// shows in the defect as (I - z/2 + z^2/12) d, z = dt J; the factor has no real root
+// (its minimum is 1/4, at z = 3) but shrinks along growing modes, so the judge also
+// bounds the cell's reactivity over the step,
+//   rate = dt * max_k max(|F0_k| / (|Y0_k| + 1e-6), |F1_k| / (|Y1_k| + 1e-6)) <= judge_rate,
+// and divides the estimate by the factor at z = rate, 1 - rate/2 + rate^2/12, before
+// comparing it with judge_tol * T (1e-6: the mass fraction below which a species'
+// share of the mixture energy is under ~1 K).  A trapezoidal check (two right-hand
+// sides) was tried first: its O(dt^3) truncation can cancel a surrogate error of the
+// same size, which let a few cells through with twice the tolerated error.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -178,7 +182,13 @@ __device__ __noinline__ bool judge_defect(const MechTables &mt, const double (&y
   float Ta = (float)T0, Tb = (float)T1;
   if (!cell_rhs_f32(mt, u0, rho_f, invRho_f, eR, Ta, F0) || !cell_rhs_f32(mt, u1, rho_f, invRho_f, eR, Tb, F1))
     return false;
-  const float T1f = (float)T1, hdt = 0.5f * (float)dt;
+  const float dtf = (float)dt;
+  float um[NSP], Fm[NSP];
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) um[k] = 0.5f * (u0[k] + u1[k]) + 0.125f * dtf * (F0[k] - F1[k]);
+  float Tm = 0.5f * (Ta + Tb);
+  if (!cell_rhs_f32(mt, um, rho_f, invRho_f, eR, Tm, Fm)) return false;
+  const float T1f = (float)T1, sdt = dtf * (1.0f / 6.0f);
   const int range = T1f >= mt.f.T_mid;
   float m[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
@@ -194,7 +204,7 @@ __device__ __noinline__ bool judge_defect(const MechTables &mt, const double (&y
     const float *c = mt.f.ec[range][k];
     const float ukR =
         fmaf(T1f, fmaf(T1f, fmaf(T1f, fmaf(T1f, fmaf(T1f, c[4], c[3]), c[2]), c[1]), c[0]), c[5]) * mt.f.invW[k];
-    const float defect = (float)(y1[k] - y0[k]) - hdt * (F0[k] + F1[k]);
+    const float defect = (float)(y1[k] - y0[k]) - sdt * (F0[k] + 4.0f * Fm[k] + F1[k]);
     sum = fmaf(fabsf(ukR - eR), fabsf(defect), sum);
     r = fmaxf(r, fmaxf(fabsf(F0[k]) / (fabsf(u0[k]) + 1e-6f), fabsf(F1[k]) / (fabsf(u1[k]) + 1e-6f)));
   }
@@ -304,7 +314,7 @@ __global__ void __launch_bounds__(128)
     double dT = 0.0, rate = 0.0;
     const bool jok = judge_defect(mt, y0, y1, rho[i], e[i] / R_U, (double)x[0], T1, dt, dT, rate);
     if (!jok || !(sc.judge_rate < 0.0f || rate <= (double)sc.judge_rate)) reason = kFbReactive;
-    else if (!(dT <= (double)sc.judge_tol * T1)) reason = kFbJudge;
+    else if (!(dT <= (double)sc.judge_tol * T1 * (1.0 - 0.5 * rate + rate * rate / 12.0))) reason = kFbJudge;
   }
   if (!reason) {
 #pragma unroll
