@@ -69,8 +69,6 @@ cudaError_t launch_surrogate_finish(int variant, const MechTables &mt, const Sur
                                     int64_t ld, double *T, int32_t *status, int32_t *nsteps,
                                     uint8_t *mask, int32_t *fb_idx, unsigned int *fb_count,
                                     int64_t base, cudaStream_t s);
-cudaError_t launch_norm_bf16(int64_t n, int ncol, int ld, const float *src, const float *mean,
-                             const float *inv_std, __nv_bfloat16 *dst, cudaStream_t s);
 cudaError_t launch_surrogate_stats(chem_stats *st, int64_t n, const unsigned int *fb_count,
                                    cudaStream_t s);
 // The whole network on n rows in one kernel (mlp_fused.cu): X [n x 16] raw features

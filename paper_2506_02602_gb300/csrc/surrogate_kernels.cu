@@ -340,16 +340,6 @@ __global__ void k_one_box(int64_t *box_off, double *box_dt, int32_t *box_nsub, i
   }
 }
 
-// dst (bf16) = (src - mean) * inv_std for the first ncol columns, zero elsewhere; src kept.
-__global__ void k_norm_bf16(int64_t n, int ncol, int ld, const float *__restrict__ src,
-                            const float *__restrict__ mean, const float *__restrict__ inv_std,
-                            __nv_bfloat16 *__restrict__ dst) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n * ld) return;
-  const int c = (int)(t % ld);
-  dst[t] = __float2bfloat16(c < ncol ? (src[t] - mean[c]) * inv_std[c] : 0.0f);
-}
-
 // Surrogate-call totals, launched after the fallback kernel on the same stream: every
 // cell counted once (cells = n overrides the fallback kernel's count of its own cells),
 // accepted cells as CHEM_CELL_OK (the fallback kernel counted the rejected ones by status).
@@ -361,13 +351,6 @@ __global__ void k_surrogate_stats(chem_stats *st, int64_t n, const unsigned int 
 }
 
 static unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
-
-cudaError_t launch_norm_bf16(int64_t n, int ncol, int ld, const float *src, const float *mean,
-                             const float *inv_std, __nv_bfloat16 *dst, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  k_norm_bf16<<<nblk(n * ld, 256), 256, 0, s>>>(n, ncol, ld, src, mean, inv_std, dst);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_surrogate_stats(chem_stats *st, int64_t n, const unsigned int *fb_count,
                                    cudaStream_t s) {
