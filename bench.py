@@ -229,7 +229,7 @@ MLP_FLOPS_PER_ROW = 2 * (16 * 256 + 256 * 256 * 2 + 256 * 16)  # padded 16-256-2
 # DRAM bytes (read + write) per cell of one k_lsrk launch, from an ncu capture of the
 # 131,072-cell slice (profiles/k_lsrk_detonation_slice.md), scaled by the cell count;
 # to be set to None whenever the kernel changes until it is captured again.
-TRAFFIC_PER_CELL = {"fp64": None, "mixed": None}
+TRAFFIC_PER_CELL = {"fp64": 12.742912e6 / 131072, "mixed": 12.703232e6 / 131072}
 
 
 def _bf16_peak():
