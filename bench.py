@@ -10,7 +10,7 @@ region, so the reported rate slightly understates the kernel.
 
 Variants: plain fp64, mixed precision (fp32 rates and stages, fp64 temperature solve,
 Gibbs terms, registers and control) and the hybrid (the learned surrogate with its
-error judge, mixed-precision integration of the cells it rejects), each timed over K
+error test, mixed-precision integration of the cells it rejects), each timed over K
 steps; the headline is the fastest variant whose error against the FP64 result meets
 its stated bound (mixed: 1e-5, hybrid: 1e-3 relative on T).  Every variant's rate,
 error and roofline fraction is in "variants".
@@ -18,7 +18,7 @@ error and roofline fraction is in "variants".
 The shock-bubble leg ("shock_bubble") is the full hybrid on the 256^3 reactive
 shock-bubble field (chem_inputs.workloads.shock_bubble: 16.7M cells, AMR-like levels
 with 2^l substeps of 1e-8 / 2^l s): the surrogate, trained on the field's own state
-family (workloads.bubble_trajectory_starts), with its judge and the persistent
+family (workloads.bubble_trajectory_starts), with its error test and the persistent
 work-stealing integrator (mixed precision) for the cells it rejects, per level,
 against plain fp64 and mixed batched integration of the whole field in one persistent
 launch.
@@ -265,7 +265,7 @@ def timed(fn, reps, stream):
     return best
 
 
-FALLBACK_REASONS = ("range", "residual", "negative", "temperature", "reactive", "judge")
+FALLBACK_REASONS = ("range", "residual", "negative", "temperature", "reactive", "error")
 
 
 def fallback_reasons(mask):

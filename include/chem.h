@@ -347,10 +347,10 @@ typedef struct {
   float resid_max;   /* [0.02] largest relative element-mass residual before projection */
   float neg_tol;     /* [1e-6] most negative mass fraction allowed after projection */
   float max_dT;      /* [200] largest accepted |T(t + dt) - T(t)|, K */
-  float judge_tol;   /* [5e-4] largest accepted error estimate relative to T (the
-                        quadrature judge of chem_surrogate_infer); negative: no judge */
-  float judge_rate;  /* [1] largest dt * max_k |dY_k/dt| / (|Y_k| + 1e-6) at either end of
-                        the step for the judge to accept; negative: no bound */
+  float err_tol;   /* [5e-4] largest accepted error estimate relative to T (the
+                        quadrature error test of chem_surrogate_infer); negative: no test */
+  float rate_max;  /* [1] largest dt * max_k |dY_k/dt| / (|Y_k| + 1e-6) at either end of
+                        the step for the test to accept; negative: no bound */
 } chem_surrogate_gate;
 
 /* Number of float parameters of the network (flat layout W0 [256x16], b0 [256], W1
@@ -373,12 +373,12 @@ int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
  * Advance the state over dt with the surrogate (chem_state as in chem_integrate).  Per
  * cell: features -> network -> inverse transform -> fp64 projection -> fp64 temperature
  * -> gate (feature range, element residual, negativity, temperature solve, |dT|) ->
- * judge: with the integrator's right-hand side at Y0, Y1 and the Hermite midpoint
+ * error test: with the integrator's right-hand side at Y0, Y1 and the Hermite midpoint
  * Ym = (Y0 + Y1)/2 + dt/8 (F0 - F1), Simpson's defect D = Y1 - Y0 - dt/6 (F0 + 4 Fm + F1)
  * gives the temperature-error estimate sum_k |u_k(T1) - e| |D_k| / c_v(T1), which must
- * not exceed judge_tol * T1 (u_k the species internal energies per mass) times
+ * not exceed err_tol * T1 (u_k the species internal energies per mass) times
  * 1 - rate/2 + rate^2/12 (the defect's shrink factor along a growing mode); and the
- * step must be slow for the cell (rate <= judge_rate, below).
+ * step must be slow for the cell (rate <= rate_max, below).
  * Accepted cells get the projected Y, its T, status CHEM_CELL_OK and nsteps 0; rejected
  * cells are integrated with rtol, atol by the persistent work-stealing kernel of
  * chem_integrate_batched (the fallback list is its queue; the context's variant) and
@@ -386,8 +386,8 @@ int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
  * steps.  d_fallback_mask (nullable, device uint8 [ncells]) receives 0 for accepted
  * cells and, for rejected ones, the first gate that failed: 1 feature outside the
  * training range, 2 element residual, 3 negative mass fraction, 4 temperature (no
- * root or |dT| > max_dT), 5 judge: the step is not slow for the cell, 6 judge: error
- * estimate above judge_tol.  d_stats (nullable): status_count[CHEM_CELL_SURROGATE] counts fallbacks.
+ * root or |dT| > max_dT), 5 error test: the step is not slow for the cell, 6 error test: error
+ * estimate above err_tol.  d_stats (nullable): status_count[CHEM_CELL_SURROGATE] counts fallbacks.
  * gate may be NULL.  Errors: no trained or loaded network -> CHEM_ERR_STATE; arguments
  * as chem_integrate.  Asynchronous on stream.
  */

@@ -103,8 +103,8 @@ class TrainCfg(C.Structure):
 
 class Gate(C.Structure):
     _fields_ = [("ood_margin", C.c_float), ("resid_max", C.c_float), ("neg_tol", C.c_float),
-                ("max_dT", C.c_float), ("judge_tol", C.c_float),
-                ("judge_rate", C.c_float)]
+                ("max_dT", C.c_float), ("err_tol", C.c_float),
+                ("rate_max", C.c_float)]
 
 
 ORDER_STIFFNESS, ORDER_NATURAL = 0, 1
@@ -373,7 +373,7 @@ class Context:
     def surrogate_infer(self, rho, e, Y, T, dt, rtol=1e-6, atol=1e-10, status=None, nsteps=None,
                         mask=None, stats=None, gate=None, stream=None):
         """chem_surrogate_infer: advance Y, T in place over dt; gate is a dict of
-        ood_margin / resid_max / neg_tol / max_dT / judge_tol / judge_rate (0 or missing =
+        ood_margin / resid_max / neg_tol / max_dT / err_tol / rate_max (0 or missing =
         default)."""
         n = rho.numel()
         st = State(_ptr(rho).value, _ptr(e).value, _ptr(Y).value, Y.stride(0), _ptr(T).value, None,

@@ -68,7 +68,7 @@ struct MechTablesF32 {
   float lnA0[NRX], beta0[NRX], Ta0[NRX];
   float troe_a[NRX], troe_i3[NRX], troe_i1[NRX], troe_T2[NRX];
   float effm1[NRX][NSP];
-  // fp32 thermo for the surrogate's error judge (all-fp32 right-hand side)
+  // fp32 thermo for the surrogate's error test (all-fp32 right-hand side)
   float ec[2][NSP][6];
   float gc[2][NSP][7];
   float T_mid, ln_R_over_Pref;

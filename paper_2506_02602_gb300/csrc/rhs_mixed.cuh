@@ -40,7 +40,7 @@ __device__ __forceinline__ float troe_F_f32(const MechTables &mt, float T, float
 }
 
 // G: the precision of the Gibbs functions and ln(1/K_c) (double in the mixed variant,
-// float in the all-fp32 right-hand side of the surrogate's error judge).
+// float in the all-fp32 right-hand side of the surrogate's error test).
 template <int J, typename G>
 __device__ __forceinline__ void reaction_mixed(const MechTables &mt, const RateInputsF &in,
                                                const G (&g)[NSP], G lnRTP, float (&wdot)[NSP]) {
@@ -130,9 +130,9 @@ __device__ __forceinline__ bool cell_rhs_mixed(const MechTables &mt, const float
   return true;
 }
 
-// Temperature from e/R_u and Y/W entirely in fp32 (for the error judge): Newton from T
+// Temperature from e/R_u and Y/W entirely in fp32 (for the error test): Newton from T
 // (1500 K if not positive and finite), |dT| <= 2e-6 T within 12 iterations; false on
-// no convergence or a non-positive / non-finite iterate (the judge then rejects).
+// no convergence or a non-positive / non-finite iterate (the test then rejects).
 __device__ __forceinline__ bool solve_T_f32(const MechTables &mt, const float (&yw)[NSP], float eR, float &T) {
   float Tn = (isfinite(T) && T > 0.0f) ? T : 1500.0f;
   int range = -1;
@@ -168,7 +168,7 @@ __device__ __forceinline__ bool solve_T_f32(const MechTables &mt, const float (&
 }
 
 // dY/dt of one cell entirely in fp32 (temperature, Gibbs functions and ln(1/K_c)
-// included): the right-hand side of the surrogate's error judge, an estimator that
+// included): the right-hand side of the surrogate's error test, an estimator that
 // needs relative accuracy far coarser than fp32's.  T: in = guess, out = solved T.
 __device__ __forceinline__ bool cell_rhs_f32(const MechTables &mt, const float (&U)[NSP], float rho,
                                              float invRho, float eR, float &T, float (&F)[NSP]) {

@@ -316,8 +316,8 @@ static SurrogateConsts make_consts(const Surrogate *s, const chem_surrogate_gate
   c.resid_max = g.resid_max;
   c.neg_tol = g.neg_tol;
   c.max_dT = g.max_dT;
-  c.judge_tol = g.judge_tol;
-  c.judge_rate = g.judge_rate;
+  c.err_tol = g.err_tol;
+  c.rate_max = g.rate_max;
   c.lam = s->lam;
   c.dt_power = s->dt_power;
   for (int el = 0; el < 3; ++el)
@@ -624,8 +624,8 @@ int chem_surrogate_infer(chem_ctx *ctx, const chem_state *state, int64_t n, doub
   if (g.resid_max == 0.0f) g.resid_max = 0.02f;
   if (g.neg_tol == 0.0f) g.neg_tol = 1e-6f;
   if (g.max_dT == 0.0f) g.max_dT = 200.0f;
-  if (g.judge_tol == 0.0f) g.judge_tol = 5e-4f;
-  if (g.judge_rate == 0.0f) g.judge_rate = 1.0f;
+  if (g.err_tol == 0.0f) g.err_tol = 5e-4f;
+  if (g.rate_max == 0.0f) g.rate_max = 1.0f;
   const int64_t chunk = n < kInferChunk ? n : kInferChunk;
   e = ensure_infer_buffers(s, chunk, n);
   if (e != cudaSuccess) return sur_cuda(ctx, e, "allocating inference buffers");

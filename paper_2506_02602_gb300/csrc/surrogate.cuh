@@ -35,8 +35,8 @@ enum {
   kFbResidual = 2,     // element residual of the raw prediction too large
   kFbNegative = 3,     // a mass fraction below -neg_tol after the projection
   kFbTemperature = 4,  // no temperature root, or |T' - T0| > max_dT
-  kFbReactive = 5,     // judge: the step is not slow for the cell (judge_rate)
-  kFbJudge = 6,        // judge: error estimate above judge_tol
+  kFbReactive = 5,     // error test: the step is not slow for the cell (rate_max)
+  kFbError = 6,        // error test: error estimate above err_tol
 };
 
 // Everything the inference epilogue needs besides the mechanism (passed by value).
@@ -47,8 +47,8 @@ struct SurrogateConsts {
   float resid_max;                      // max relative element residual before projection
   float neg_tol;                        // most negative mass fraction allowed after projection
   float max_dT;                         // largest accepted |T' - T0| (K)
-  float judge_tol;                      // largest estimated relative T error (<= 0: no judge)
-  float judge_rate;                     // largest dt * relative rate of change (< 0: no bound)
+  float err_tol;                      // largest estimated relative T error (<= 0: no test)
+  float rate_max;                     // largest dt * relative rate of change (< 0: no bound)
   double lam;                           // Box-Cox lambda
   double dt_power;                      // targets scaled by (kSurDtRef / dt)^dt_power
   double E[3][NSP];                     // element mass fraction per unit species mass fraction

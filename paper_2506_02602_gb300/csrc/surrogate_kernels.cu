@@ -11,22 +11,22 @@
 // by construction; the projection restores the element (H, O, N) mass fractions, hence
 // sum Y too, in fp64.
 //
-// Error judge: the integrator's own right-hand side checks each candidate result.  With
+// A-posteriori error test: the integrator's own right-hand side checks each candidate result.  With
 // F0 = f(Y0), F1 = f(Y1) and Fm = f(Ym) at the cubic Hermite midpoint
 // Ym = (Y0 + Y1) / 2 + dt/8 (F0 - F1), Simpson's rule Yc = Y0 + dt/6 (F0 + 4 Fm + F1)
 // differs from the exact solution by O(dt^5) where the cell is smooth over dt, so the
 // defect D = Y1 - Yc estimates the error of Y1.  At constant e the temperature moves by
-// -sum_k (u_k - e) dY_k / c_v for a change dY with sum_k dY_k = 0, so the judge takes
+// -sum_k (u_k - e) dY_k / c_v for a change dY with sum_k dY_k = 0, so the test takes
 //   est = sum_k |u_k(T1) - e| |D_k| / c_v(T1)
-// (no cancellation between species counted) and sends a cell with est > judge_tol * T1
+// (no cancellation between species counted) and sends a cell with est > err_tol * T1
 // to the integrator.  Stiff cells (dt beyond the fast time scales), where the
 // quadrature itself is not accurate, fail the check too.  Linearised, an error d of Y1
 // shows in the defect as (I - z/2 + z^2/12) d, z = dt J; the factor has no real root
-// (its minimum is 1/4, at z = 3) but shrinks along growing modes, so the judge also
+// (its minimum is 1/4, at z = 3) but shrinks along growing modes, so the test also
 // bounds the cell's reactivity over the step,
-//   rate = dt * max_k max(|F0_k| / (|Y0_k| + 1e-6), |F1_k| / (|Y1_k| + 1e-6)) <= judge_rate,
+//   rate = dt * max_k max(|F0_k| / (|Y0_k| + 1e-6), |F1_k| / (|Y1_k| + 1e-6)) <= rate_max,
 // and divides the estimate by the factor at z = rate, 1 - rate/2 + rate^2/12, before
-// comparing it with judge_tol * T (1e-6: the mass fraction below which a species'
+// comparing it with err_tol * T (1e-6: the mass fraction below which a species'
 // share of the mixture energy is under ~1 K).  A trapezoidal check (two right-hand
 // sides) was tried first: its O(dt^3) truncation can cancel a surrogate error of the
 // same size, which let a few cells through with twice the tolerated error.
@@ -169,7 +169,7 @@ __global__ void k_normalize(int64_t n, int ncol, int ld, float *A, const float *
 // relative rate of change at either end.  All in fp32 (cell_rhs_f32), whatever the
 // context's variant: an estimate compared with a tolerance of 5e-4 T needs nothing
 // finer; y1 - y0 is formed in fp64 first, so the defect does not lose it to rounding.
-__device__ __noinline__ bool judge_defect(const MechTables &mt, const double (&y0)[NSP],
+__device__ __noinline__ bool posterior_error(const MechTables &mt, const double (&y0)[NSP],
                                           const double (&y1)[NSP], double rho, double eR_d,
                                           double T0, double T1, double dt, double &dT, double &rate) {
   float u0[NSP], u1[NSP], F0[NSP], F1[NSP];
@@ -310,11 +310,11 @@ __global__ void __launch_bounds__(128)
   double T1 = (double)x[0];
   const bool tok = solve_T(mt, yw, e[i] / R_U, T1);
   if (!reason && !(tok && fabs(T1 - (double)x[0]) <= (double)sc.max_dT)) reason = kFbTemperature;
-  if (!reason && sc.judge_tol > 0.0f) {
+  if (!reason && sc.err_tol > 0.0f) {
     double dT = 0.0, rate = 0.0;
-    const bool jok = judge_defect(mt, y0, y1, rho[i], e[i] / R_U, (double)x[0], T1, dt, dT, rate);
-    if (!jok || !(sc.judge_rate < 0.0f || rate <= (double)sc.judge_rate)) reason = kFbReactive;
-    else if (!(dT <= (double)sc.judge_tol * T1 * (1.0 - 0.5 * rate + rate * rate / 12.0))) reason = kFbJudge;
+    const bool jok = posterior_error(mt, y0, y1, rho[i], e[i] / R_U, (double)x[0], T1, dt, dT, rate);
+    if (!jok || !(sc.rate_max < 0.0f || rate <= (double)sc.rate_max)) reason = kFbReactive;
+    else if (!(dT <= (double)sc.err_tol * T1 * (1.0 - 0.5 * rate + rate * rate / 12.0))) reason = kFbError;
   }
   if (!reason) {
 #pragma unroll

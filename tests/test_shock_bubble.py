@@ -1,6 +1,6 @@
 """GPU checks of the full hybrid on the reactive shock-bubble field (a 48^3 version of the
 256^3 workload): AMR-like levels with 2^l substeps, the surrogate (trained here on the
-field's own state family) with its error judge and the persistent work-stealing
+field's own state family) with its error test and the persistent work-stealing
 integrator for the cells it rejects, against plain FP64 batched integration, itself
 checked against the oracle on sampled cells."""
 import numpy as np

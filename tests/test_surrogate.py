@@ -10,7 +10,7 @@ oracle (oracle/mlp.py) and the integrator.
   projection) and energy exactly (T solved from e); rejected cells are integrated by the
   same arithmetic as chem_integrate (bit-identical); mask and statistics agree;
 * what the network gains: on a million held-out states at dt = 1e-9 s the surrogate
-  path (network, judge, fallback) is faster than plain integration of the same cells and
+  path (network, error test, fallback) is faster than plain integration of the same cells and
   within 1e-3 relative on T of it.
 """
 import numpy as np
