@@ -47,7 +47,7 @@ typedef enum {
   CHEM_OK = 0,
   CHEM_ERR_INVALID = -1,     /* bad argument; nothing was launched */
   CHEM_ERR_CUDA = -2,        /* a CUDA call or launch failed */
-  CHEM_ERR_UNSUPPORTED = -3, /* valid input this build has no kernel for */
+  CHEM_ERR_UNSUPPORTED = -3, /* valid input the compiled library has no kernel for */
   CHEM_ERR_NOMEM = -4,       /* a device allocation failed */
   CHEM_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
   CHEM_ERR_STATE = -6        /* call out of order (e.g. inference before training) */
@@ -148,7 +148,7 @@ typedef struct chem_ctx chem_ctx;
  * Create a context for mechanism *mech (copied; the caller keeps ownership).
  * Validates the mechanism: element balance of every reaction (integers), NASA-7
  * continuity of cp, h and s at T_mid (relative 1e-6), a common T_mid, positive molar
- * masses.  This build's kernels are specialised at compile time to the structure of
+ * masses.  The library's kernels are specialised at compile time to the structure of
  * the 9-species / 21-reaction H2-O2-N2 mechanism (species H2, O2, H2O, H, O, OH, HO2,
  * H2O2, N2 in that order; the reaction list of chem_inputs.mechanism): a mechanism
  * with other stoichiometry or reaction types returns CHEM_ERR_UNSUPPORTED.  Its

@@ -76,7 +76,7 @@ bool close_rel(double x, double y, double tol) {
 int build_tables(const chem_mechanism *m, MechTables *t) {
   if (m->n_species != NSP || m->n_reactions != NRX)
     return fail(nullptr, CHEM_ERR_UNSUPPORTED,
-                "this build is specialised to %d species / %d reactions (got %d / %d)", NSP, NRX,
+                "the library is compiled for %d species / %d reactions (got %d / %d)", NSP, NRX,
                 m->n_species, m->n_reactions);
   std::memset(t, 0, sizeof *t);
   const double Tmid = m->T_mid[0];
