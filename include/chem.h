@@ -466,10 +466,14 @@ int chem_integrate_batched_noalloc(chem_ctx *ctx, const chem_state *state, int64
 /*
  * Diagnostic: evaluate one of the device math routines the integration kernels use on
  * n fp64 arguments (device pointers d_x -> d_y), so tests can check them against the
- * CUDA library.  op: 0 table-driven exp, 1 table-driven log (Tang's methods, used by
- * the kernels), 2 library exp, 3 library log.  Not part of the integration path; the
- * paper has no counterpart.  Errors: unknown op or n < 0 -> CHEM_ERR_INVALID.
- * Asynchronous on stream.
+ * CUDA library and the IEEE-754 definitions.  op: 0 table-driven exp, 1 table-driven
+ * log (Tang's methods, used by the kernels), 2 library exp, 3 library log,
+ * 4 reciprocal with one Newton-Raphson step, 5 with two, 6 the hardware reciprocal
+ * approximation alone, 7 the integer-pipe fp64 -> fp32 rounding (widened back exactly),
+ * 8 the integer-pipe fp32 -> fp64 widening of the hardware-rounded fp32 of x,
+ * 9 / 10 the hi / lo fp32 parts of the 2^-12-grid split of x.  Not part of the
+ * integration path; the paper has no counterpart.  Errors: unknown op or n < 0 ->
+ * CHEM_ERR_INVALID.  Asynchronous on stream.
  */
 int chem_diag_math(int op, int64_t n, const double *d_x, double *d_y, void *stream);
 

@@ -156,8 +156,10 @@ def load() -> C.CDLL:
 
 
 def diag_math(op: int, x, stream=None):
-    """chem_diag_math: 0 table exp, 1 table log, 2 library exp, 3 library log on a
-    float64 CUDA tensor; returns a new tensor."""
+    """chem_diag_math on a float64 CUDA tensor; returns a new tensor.  op: 0 table exp,
+    1 table log, 2 library exp, 3 library log, 4 / 5 reciprocal with one / two
+    Newton-Raphson steps, 6 hardware reciprocal approximation, 7 integer-pipe fp64 ->
+    fp32, 8 integer-pipe fp32 -> fp64 of fp32(x), 9 / 10 hi / lo of the 2^-12 split."""
     import torch
     _check_f64_cuda("x", x)
     y = torch.empty_like(x)

@@ -153,6 +153,7 @@ int build_tables(const chem_mechanism *m, MechTables *t) {
       t->gc[r][k][4] = -a[4] / 20.0;
       t->gc[r][k][5] = a[5];
       t->gc[r][k][6] = -a[6];
+      for (int i = 0; i < 6; ++i) t->ecw[r][k][i] = t->ec[r][k][i] / m->W[k];
     }
   }
   {  // the largest |c_v' / c_v| of the tables on [200, 6000] K (1 K sampling)
@@ -227,6 +228,7 @@ int build_tables(const chem_mechanism *m, MechTables *t) {
     }
   t->f.T_mid = (float)t->T_mid;
   t->f.ln_R_over_Pref = (float)t->ln_R_over_Pref;
+  t->f.newton_sq = (float)t->newton_sq;
   return CHEM_OK;
 }
 

@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(128) k_probe(const __grid_constant__ MechTable
         Y[k] = a.Y[k * a.ld + i];
         yw[k] = Y[k] * mt.invW[k];
       }
-      if (isfinite(rho) && rho > 0.0 && solve_T(mt, yw, a.e[i] / R_U, T)) {
+      if (isfinite(rho) && rho > 0.0 && solve_T(mt, Y, a.e[i] / R_U, T)) {
         double c[NSP], wdot[NSP], dflux[NSP];
 #pragma unroll
         for (int k = 0; k < NSP; ++k) c[k] = fmax(rho * yw[k], 0.0);

@@ -95,7 +95,12 @@ __device__ __forceinline__ void cell_attempt(const MechTables &mt, CellState &c,
   double Xs[NSP], E[NSP];
   SReal U[NSP];
 #pragma unroll
-  for (int k = 0; k < NSP; ++k) { Xs[k] = c.X[k]; U[k] = (SReal)c.X[k]; E[k] = 0.0; }
+  for (int k = 0; k < NSP; ++k) {
+    Xs[k] = c.X[k];
+    if constexpr (kMixed) U[k] = d2f(c.X[k]);
+    else U[k] = c.X[k];
+    E[k] = 0.0;
+  }
   int failed = 0;
   double Tacc = c.T;  // temperature of the accepted state, set by stage 1
 #pragma unroll 1
@@ -109,11 +114,11 @@ __device__ __forceinline__ void cell_attempt(const MechTables &mt, CellState &c,
     if (s == 0) Tacc = c.T;
     const double ha = h * c_ls_a[s], hb = h * c_ls_b[s], he = h * c_ls_e[s];
     if constexpr (kMixed) {
-      const float ha_f = (float)ha;
+      const float ha_f = d2f(ha);
 #pragma unroll
       for (int k = 0; k < NSP; ++k) {
-        U[k] = fmaf(ha_f, F[k], (float)c.X[k]);
-        const double Fk = (double)F[k];
+        U[k] = fmaf(ha_f, F[k], d2f(c.X[k]));
+        const double Fk = f2d(F[k]);
         E[k] = fma(he, Fk, E[k]);
         c.X[k] = fma(hb, Fk, c.X[k]);
       }
@@ -133,12 +138,16 @@ __device__ __forceinline__ void cell_attempt(const MechTables &mt, CellState &c,
     c.done = true;
     return;
   }
+  // WRMS norm; the weights' reciprocals are Newton-Raphson-refined (two steps, within
+  // 2 ulp, in the fp64 variant; one step, ~2^-40 relative, in the mixed one, whose fp32
+  // stages perturb the estimate far more)
   double err = CUDART_NAN;
   if (!failed) {
     double sum = 0.0;
 #pragma unroll
     for (int k = 0; k < NSP; ++k) {
-      const double w = E[k] / fma(p.rtol, fmax(fabs(Xs[k]), fabs(c.X[k])), p.atol);
+      const double den = fma(p.rtol, max_abs(Xs[k], c.X[k]), p.atol);
+      const double w = E[k] * (kMixed ? rcp1(den) : rcp2(den));
       sum = fma(w, w, sum);
     }
     err = sqrt(sum * (1.0 / NSP));
@@ -154,6 +163,8 @@ __device__ __forceinline__ void cell_attempt(const MechTables &mt, CellState &c,
     c.h = h * 0.2;
     return;
   }
+  // the step factor stays IEEE fp64: an explicit scheme at its stability limit grows a
+  // perturbation of h along its weakly unstable modes into another rejection sequence
   const double fac = (err == 0.0) ? 5.0 : fmin(5.0, fmax(0.2, 0.9 / sqrt(sqrt(err))));
   if (err <= 1.0) {
     c.t += h;
@@ -170,10 +181,7 @@ __device__ __forceinline__ void cell_attempt(const MechTables &mt, CellState &c,
 // Temperature of the final state (fp64 Newton); a failure marks the cell.
 __device__ __forceinline__ void cell_finish(const MechTables &mt, CellState &c) {
   if (c.status == CHEM_CELL_NONFINITE) return;
-  double yw[NSP];
-#pragma unroll
-  for (int k = 0; k < NSP; ++k) yw[k] = c.X[k] * mt.invW[k];
-  if (!solve_T(mt, yw, c.eR, c.T)) {
+  if (!solve_T(mt, c.X, c.eR, c.T)) {
     if (c.status == CHEM_CELL_OK) c.status = CHEM_CELL_NEWTON_FAIL;
     c.T = CUDART_NAN;
   }

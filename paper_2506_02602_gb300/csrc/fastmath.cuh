@@ -88,4 +88,101 @@ __device__ __forceinline__ double log_t(double x) {
 __device__ __forceinline__ double log10_t(double x) { return log_t(x) * kInvLn10; }
 __device__ __forceinline__ double exp10_t(double x) { return exp_t(x * kLn10); }
 
+// ---- fp32 <-> fp64 conversions on the integer pipe ----
+// On GB300 a cvt between fp32 and fp64 takes an FP64-pipe slot, the same as a DFMA
+// (measured), and the mixed-precision right-hand side converts ~50 values per
+// evaluation.  These two build the IEEE-754 bit patterns with integer operations
+// instead.  Both give a signed zero for magnitudes below the fp32 normal range
+// (2^-126) and keep infinities and NaNs.
+
+// fp32 -> fp64: exact for normal numbers
+__device__ __forceinline__ double f2d(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t a = u & 0x7fffffffu;
+  uint32_t hi = (a >> 3) + 0x38000000u;     // exponent bias 127 -> 1023
+  if (a >= 0x7f800000u) hi |= 0x7ff00000u;  // inf / NaN: all-ones exponent
+  const bool tiny = a < 0x00800000u;
+  hi = tiny ? 0u : hi;
+  const uint32_t lo = tiny ? 0u : (u << 29);
+  return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)lo);
+}
+
+// fp64 -> fp32, rounded to nearest (ties to even); |d| >= 2^128 gives inf
+__device__ __forceinline__ float d2f(double d) {
+  const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+  const uint32_t a = hi & 0x7fffffffu;
+  uint32_t r = ((a - 0x38000000u) << 3) | (lo >> 29);  // exponent bias 1023 -> 127, 23 bits
+  const uint32_t guard = (lo >> 28) & 1u;
+  const uint32_t sticky = (lo & 0x0fffffffu) != 0u;
+  r += guard & (sticky | (r & 1u));  // a carry out of the fraction bumps the exponent
+  r = a >= 0x47f00000u ? 0x7f800000u : r;
+  r = (a > 0x7ff00000u || (a == 0x7ff00000u && lo != 0u)) ? 0x7fc00000u : r;
+  r = a < 0x38100000u ? 0u : r;
+  return __uint_as_float(r | (hi & 0x80000000u));
+}
+
+// ---- fp64 reciprocals ----
+// An IEEE fp64 divide costs ~9 FP64-pipe slots on GB300 (measured).  Here 1/x starts
+// from the hardware approximation rcp.approx.ftz.f64 and takes Newton-Raphson steps
+// r <- r + r (1 - x r), each of which squares the relative error (the approximation's
+// is near 2^-20): one step for a relative error near 2^-40 (Newton's derivative), two
+// for a result within an ulp or two.  x must be finite, nonzero and normal (0 gives
+// NaN).
+__device__ __forceinline__ double rcp_approx(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  return r;
+}
+__device__ __forceinline__ double rcp1(double x) {
+  const double r = rcp_approx(x);
+  return fma(r, fma(-x, r, 1.0), r);
+}
+__device__ __forceinline__ double rcp2(double x) {
+  const double r = rcp1(x);
+  return fma(r, fma(-x, r, 1.0), r);
+}
+
+// ---- fp64 tests and selects on the integer pipe ----
+// x positive, finite and normal
+__device__ __forceinline__ bool pos_normal(double x) {
+  return (uint32_t)__double2hiint(x) - 0x00100000u < 0x7fe00000u;
+}
+// a >= b for non-negative a, b (the bit patterns of non-negative doubles are ordered)
+__device__ __forceinline__ bool ge_nonneg(double a, double b) {
+  return __double_as_longlong(a) >= __double_as_longlong(b);
+}
+// max(|a|, |b|); a NaN operand gives NaN
+__device__ __forceinline__ double max_abs(double a, double b) {
+  const long long x = __double_as_longlong(a) & 0x7fffffffffffffffLL;
+  const long long y = __double_as_longlong(b) & 0x7fffffffffffffffLL;
+  return __longlong_as_double(x > y ? x : y);
+}
+// max(x, 0) (negative values, -0 and NaNs with the sign bit set give +0)
+__device__ __forceinline__ double clamp_nonneg(double x) {
+  const long long b = __double_as_longlong(x);
+  return __longlong_as_double(b & ~(b >> 63));
+}
+
+// x clamped to [-lim, lim] for lim > 0 (a NaN gives +-lim)
+__device__ __forceinline__ double clamp_abs(double x, double lim) {
+  const long long b = __double_as_longlong(x);
+  const long long l = __double_as_longlong(lim);
+  return (b & 0x7fffffffffffffffLL) > l ? __longlong_as_double((b & (long long)0x8000000000000000ULL) | l) : x;
+}
+
+// x = hi + lo for an fp64 x of magnitude below 2^12: hi is x truncated to a multiple of
+// 2^-12 (at most 24 significant bits, so exact in fp32) and lo = x - hi (|lo| < 2^-12)
+// rounded to fp32, an absolute error below 2^-37.  A signed sum of a few such hi parts
+// whose magnitude stays below 2^12 is exact in fp32, so an fp64 sum with heavy
+// cancellation (ln K_c from Gibbs functions of magnitude up to a few hundred) is
+// assembled in fp32 to within an ulp of the result plus ~1e-11.
+__device__ __forceinline__ void split_hilo(double x, float &hi, float &lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int n = 40 - ((int)((b >> 52) & 0x7ff) - 1023);  // fraction bits worth < 2^-12
+  const unsigned long long mask = n >= 53 ? 0ull : (n <= 0 ? ~0ull : (~0ull << n));
+  const double h = __longlong_as_double((long long)(b & mask));
+  hi = d2f(h);
+  lo = d2f(x - h);
+}
+
 }  // namespace chem

@@ -46,14 +46,14 @@ __global__ void k_state_from_TPY(const __grid_constant__ MechTables mt, int64_t 
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double Ti = T[i];
-  double yw[NSP], inv_w = 0.0;
+  double y[NSP], inv_w = 0.0;
 #pragma unroll
   for (int k = 0; k < NSP; ++k) {
-    yw[k] = Y[k * ld + i] * mt.invW[k];
-    inv_w += yw[k];
+    y[k] = Y[k * ld + i];
+    inv_w += y[k] * mt.invW[k];
   }
   double m[6];
-  mix_ecoef(mt, Ti >= mt.T_mid, yw, m);
+  mix_ecoef(mt, Ti >= mt.T_mid, y, 0.0, m);
   rho[i] = p[i] / (R_U * Ti * inv_w);
   e[i] = R_U * e_over_R(m, Ti);
 }

@@ -72,6 +72,7 @@ struct MechTablesF32 {
   float ec[2][NSP][6];
   float gc[2][NSP][7];
   float T_mid, ln_R_over_Pref;
+  float newton_sq;  // the fp64 Newton's stop constant (below), tested in fp32
 };
 
 // Per-context tables (host-built from chem_mechanism by build_tables()).
@@ -81,6 +82,8 @@ struct MechTables {
   double invW[NSP];
   // e_k W_k / R_u = sum_i ec[i] T^(i+1) + ec[5]: {a1 - 1, a2/2, a3/3, a4/4, a5/5, a6}
   double ec[2][NSP][6];
+  // the same per unit mass fraction (ec / W_k): mixture coefficients sum_k Y_k ecw_k
+  double ecw[2][NSP][6];
   // g_k / (R_u T) = h/RT - s/R = gc0 (1 - ln T) + gc1 T + gc2 T^2 + gc3 T^3 + gc4 T^4
   //                 + gc5 / T + gc6  with {a1, -a2/2, -a3/6, -a4/12, -a5/20, a6, -a7}
   double gc[2][NSP][7];

@@ -9,11 +9,15 @@
 // operation counts):
 //   - exponentials and logarithms are the table-driven exp_t / log_t (fastmath.cuh);
 //   - g_k / RT comes from one combined NASA-7 polynomial per species (6 FMAs);
-//   - Newton works on mixture coefficients m_i = sum_k (Y_k / W_k) ec_ki, assembled once
-//     per evaluation (54 FMAs), so each iteration is two Horner chains and a divide;
+//   - Newton works on mixture coefficients m_i = sum_k Y_k (ec_ki / W_k), assembled once
+//     per evaluation (54 FMAs), so each iteration is two Horner chains and a reciprocal;
 //   - equilibrium constants come from per-species G_k = exp(-g_k / RT) and 1/G_k:
 //     1/K_c,j = prod_reactants G * prod_products (1/G) * (R_u T / p_ref)^(sum nu), i.e.
-//     9 exponentials + 9 divides per evaluation instead of one exponential per reaction;
+//     9 exponentials + 9 reciprocals per evaluation instead of one exponential per
+//     reaction;
+//   - reciprocals are Newton-Raphson-refined hardware approximations (rcp1 / rcp2), ~3.5
+//     and ~5.7 FP64-pipe slots against ~9 for an IEEE divide; compares, clamps and
+//     fp32 <-> fp64 conversions run on the integer pipe (fastmath.cuh);
 //   - forward rates are exp(ln A + beta ln T - Ta / T), one exponential per reaction
 //     (none for temperature-independent rates or A T^-1, A T^-2 with no activation).
 #pragma once
@@ -26,16 +30,18 @@
 
 namespace chem {
 
-// Mixture internal-energy coefficients: e/R_u = T (m0 + T (m1 + T (m2 + T (m3 + T m4)))) + m5
-__device__ __forceinline__ void mix_ecoef(const MechTables &mt, int range, const double (&yw)[NSP],
-                                          double (&m)[6]) {
+// Mixture internal-energy coefficients from mass fractions, shifted by the target:
+// e/R_u - eR = T (m0 + T (m1 + T (m2 + T (m3 + T m4)))) + m5
+__device__ __forceinline__ void mix_ecoef(const MechTables &mt, int range, const double (&Y)[NSP],
+                                          double eR, double (&m)[6]) {
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     double s = 0.0;
 #pragma unroll
-    for (int k = 0; k < NSP; ++k) s = fma(yw[k], mt.ec[range][k][i], s);
+    for (int k = 0; k < NSP; ++k) s = fma(Y[k], mt.ecw[range][k][i], s);
     m[i] = s;
   }
+  m[5] -= eR;
 }
 
 __device__ __forceinline__ double e_over_R(const double (&m)[6], double T) {
@@ -55,42 +61,46 @@ __device__ __forceinline__ void cv_coef(const double (&m)[6], double (&d)[5]) {
   d[4] = 5.0 * m[4];
 }
 
-// Temperature from e/R_u and Y/W.  T: in = starting guess (1500 K if not positive and
-// finite), out = root.  Newton stops at |dT| <= 1e-12 T, or as soon as the quadratic
-// convergence bound guarantees that (dT^2 <= newton_sq T: the remaining error is then
-// below 1e-12 T / 2), within 30 iterations; on a non-positive / non-finite iterate or
-// no convergence, bisection on [200, 6000] K.
-__device__ __forceinline__ bool solve_T(const MechTables &mt, const double (&yw)[NSP], double eR,
-                                     double &T) {
-  double Tn = (isfinite(T) && T > 0.0) ? T : 1500.0;
-  int range = Tn >= mt.T_mid;
+// Temperature from e/R_u and the mass fractions Y.  T: in = starting guess (1500 K if not
+// positive and finite), out = root.  Newton stops at |dT| <= 1e-12 T, or as soon as the
+// quadratic convergence bound guarantees that (dT^2 <= newton_sq T: the remaining error
+// is then below 1e-12 T / 2), within 30 iterations; on a non-positive / non-finite
+// iterate or no convergence, bisection on [200, 6000] K.  The step divides by c_v through
+// a reciprocal with relative error ~2^-40 (a perturbed Newton step converges the same
+// way), the stop test runs in fp32 on the rounded dT and T (it only decides when to
+// stop), and the range and sign tests run on the integer pipe.
+__device__ __forceinline__ bool solve_T(const MechTables &mt, const double (&Y)[NSP], double eR,
+                                        double &T) {
+  double Tn = pos_normal(T) ? T : 1500.0;
+  int range = ge_nonneg(Tn, mt.T_mid);
   double m[6], d[5];
-  mix_ecoef(mt, range, yw, m);
+  mix_ecoef(mt, range, Y, eR, m);
   cv_coef(m, d);
   for (int it = 0; it < 30; ++it) {
-    const int r = Tn >= mt.T_mid;
+    const int r = ge_nonneg(Tn, mt.T_mid);
     if (r != range) {
       range = r;
-      mix_ecoef(mt, range, yw, m);
+      mix_ecoef(mt, range, Y, eR, m);
       cv_coef(m, d);
     }
-    const double dT = (e_over_R(m, Tn) - eR) / cv_over_R(d, Tn);
+    const double dT = e_over_R(m, Tn) * rcp1(cv_over_R(d, Tn));
     Tn -= dT;
-    if (!isfinite(Tn) || Tn <= 0.0) break;
-    if (fabs(dT) <= 1e-12 * Tn || dT * dT <= mt.newton_sq * Tn) {
+    if (!pos_normal(Tn)) break;
+    const float dTf = d2f(dT), Tf = d2f(Tn);
+    if (fabsf(dTf) <= 1e-12f * Tf || dTf * dTf <= mt.f.newton_sq * Tf) {
       T = Tn;
       return true;
     }
   }
   // bracketed fallback
   double lo = 200.0, hi = 6000.0, mlo[6], mhi[6];
-  mix_ecoef(mt, lo >= mt.T_mid, yw, mlo);
-  mix_ecoef(mt, hi >= mt.T_mid, yw, mhi);
-  if (e_over_R(mlo, lo) - eR > 0.0 || e_over_R(mhi, hi) - eR < 0.0) return false;
+  mix_ecoef(mt, lo >= mt.T_mid, Y, eR, mlo);
+  mix_ecoef(mt, hi >= mt.T_mid, Y, eR, mhi);
+  if (e_over_R(mlo, lo) > 0.0 || e_over_R(mhi, hi) < 0.0) return false;
   for (int it = 0; it < 200 && hi - lo > 1e-13 * hi; ++it) {
     const double mid = 0.5 * (lo + hi);
-    mix_ecoef(mt, mid >= mt.T_mid, yw, m);
-    if (e_over_R(m, mid) - eR > 0.0) hi = mid; else lo = mid;
+    mix_ecoef(mt, mid >= mt.T_mid, Y, eR, m);
+    if (e_over_R(m, mid) > 0.0) hi = mid; else lo = mid;
   }
   T = 0.5 * (lo + hi);
   return true;
@@ -118,7 +128,7 @@ __device__ __forceinline__ double troe_F(const MechTables &mt, double T, double 
     const double cc = -0.4 - 0.67 * lFc;
     const double nn = 0.75 - 1.27 * lFc;
     const double x = log10_t(Pr) + cc;
-    const double f1 = x / (nn - 0.14 * x);
+    const double f1 = x * rcp2(nn - 0.14 * x);
     return exp10_t(lFc / (1.0 + f1 * f1));
   }
 }
@@ -149,8 +159,8 @@ __device__ __forceinline__ void reaction(const MechTables &mt, const RateInputs 
   }
   if constexpr (R.type == FALLOFF) {
     const double k0 = exp_t(fma(mt.beta0[J], in.lnT, mt.lnA0[J]) - mt.Ta0[J] * in.invT);
-    const double Pr = k0 * M / kf;
-    kf = (Pr > 0.0) ? kf * (Pr / (1.0 + Pr)) * troe_F<J>(mt, T, in.invT, Pr) : 0.0;
+    const double Pr = k0 * M * rcp2(kf);
+    kf = (Pr > 0.0) ? kf * (Pr * rcp2(1.0 + Pr)) * troe_F<J>(mt, T, in.invT, Pr) : 0.0;
   }
   double qf = kf * in.c[R.r0];
   if constexpr (R.r1 >= 0) qf *= in.c[R.r1];
@@ -195,11 +205,11 @@ __device__ __forceinline__ void production_rates(const MechTables &mt, double T,
                                                  double *dflux = nullptr) {
   RateInputs in;
   in.lnT = log_t(T);
-  in.invT = 1.0 / T;
-  in.RTP = R_U * T / P_REF;
-  in.PRT = 1.0 / in.RTP;
+  in.invT = rcp2(T);
+  in.RTP = (R_U / P_REF) * T;
+  in.PRT = (P_REF / R_U) * in.invT;
   const double oml = 1.0 - in.lnT;
-  const int range = T >= mt.T_mid;
+  const int range = ge_nonneg(T, mt.T_mid);
   double ctot = 0.0;
 #pragma unroll
   for (int k = 0; k < NSP; ++k) {
@@ -209,9 +219,9 @@ __device__ __forceinline__ void production_rates(const MechTables &mt, double T,
     double g = fma(T, fma(T, fma(T, fma(T, gc[4], gc[3]), gc[2]), gc[1]), fma(gc[5], in.invT, gc[6]));
     g = fma(gc[0], oml, g);
     // clamp keeps G finite far outside the tables' range
-    g = fmin(fmax(g, -700.0), 700.0);
+    g = clamp_abs(g, 700.0);
     in.G[k] = exp_t(-g);
-    in.iG[k] = 1.0 / in.G[k];
+    in.iG[k] = rcp2(in.G[k]);
     wdot[k] = 0.0;
     if constexpr (kDestr) dflux[k] = 0.0;
   }
@@ -223,13 +233,10 @@ __device__ __forceinline__ void production_rates(const MechTables &mt, double T,
 // Returns false when the temperature solve fails.
 __device__ __forceinline__ bool cell_rhs(const MechTables &mt, const double (&Y)[NSP], double rho,
                                          double invRho, double eR, double &T, double (&F)[NSP]) {
-  double yw[NSP];
-#pragma unroll
-  for (int k = 0; k < NSP; ++k) yw[k] = Y[k] * mt.invW[k];
-  if (!solve_T(mt, yw, eR, T)) return false;
+  if (!solve_T(mt, Y, eR, T)) return false;
   double c[NSP], wdot[NSP];
 #pragma unroll
-  for (int k = 0; k < NSP; ++k) c[k] = fmax(rho * yw[k], 0.0);
+  for (int k = 0; k < NSP; ++k) c[k] = clamp_nonneg(rho * (Y[k] * mt.invW[k]));
   production_rates(mt, T, c, wdot);
 #pragma unroll
   for (int k = 0; k < NSP; ++k) F[k] = wdot[k] * mt.W[k] * invRho;

@@ -2,14 +2,16 @@
 //
 // The same right-hand side as rhs.cuh (Eq. 10, 14-16), split by precision:
 //   fp64: the temperature solve (Newton on the mixture NASA-7 coefficients), ln T, 1/T,
-//         the Gibbs functions g_k / RT and the equilibrium exponents
-//         ln(1 / K_c,j) = sum_k nu_jk g_k + (sum_k nu_jk) ln(R_u T / p_ref);
+//         the Gibbs functions g_k / RT and ln(R_u T / p_ref);
 //   fp32: forward rate coefficients, third-body sums, Troe fall-off, reverse rates
-//         k_r = exp(ln k_f + ln(1 / K_c)) (one fp32 exponential of an fp64-assembled
-//         exponent), the law-of-mass-action products, production rates and F.
-// The fp32 work runs on the FMA/MUFU pipes, 64x the FP64 pipe's throughput on GB300;
-// what stays in fp64 is the part whose accuracy decides the temperature and the
-// equilibrium state.
+//         k_r = exp(ln k_f + ln(1 / K_c)), the law-of-mass-action products, production
+//         rates and F.
+// The equilibrium exponents ln(1 / K_c,j) = sum_k nu_jk g_k + (sum_k nu_jk) ln(R_u T / p_ref)
+// are the fp64 sums rounded once to fp32: each fp64 term is split into an fp32 hi part
+// on a 2^-12 grid (whose sums are exact in fp32) and an fp32 lo part, so the sum needs
+// no fp64 add.  The fp32 work runs on the FMA/MUFU pipes, 64x the FP64 pipe's throughput
+// on GB300; what stays in fp64 is the part whose accuracy decides the temperature and
+// the equilibrium state, and the conversions between the two run on the integer pipe.
 #pragma once
 
 #include "rhs.cuh"
@@ -39,13 +41,48 @@ __device__ __forceinline__ float troe_F_f32(const MechTables &mt, float T, float
   }
 }
 
-// G: the precision of the Gibbs functions and ln(1/K_c) (double in the mixed variant,
-// float in the all-fp32 right-hand side of the surrogate's error test).
-template <int J, typename G>
-__device__ __forceinline__ void reaction_mixed(const MechTables &mt, const RateInputsF &in,
-                                               const G (&g)[NSP], G lnRTP, float (&wdot)[NSP]) {
+// The ingredients of ln(1/K_c,j) = sum_k nu_jk g_k + (sum_k nu_jk) ln(R_u T / p_ref).
+// GibbsHL (mixed variant): the fp64 g_k / RT and ln(R_u T / p_ref) as fp32 hi/lo pairs
+// (split_hilo); the hi parts sum exactly in fp32 and the lo parts carry the rest, so
+// the fp32 ln(1/K_c) is the fp64 sum rounded once (to within ~1e-11) without an fp64
+// add per term.  GibbsF (the error test's all-fp32 right-hand side): plain fp32.
+struct GibbsHL {
+  float h[NSP], l[NSP];
+  float rh, rl;
+};
+struct GibbsF {
+  float g[NSP];
+  float r;
+};
+
+template <int J>
+__device__ __forceinline__ float ln_inv_kc(const GibbsHL &g) {
   constexpr RxStruct R = kRx[J];
   constexpr int dnu = n_prod(R) - n_reac(R);
+  float h = g.h[R.p0] - g.h[R.r0], l = g.l[R.p0] - g.l[R.r0];
+  if constexpr (R.p1 >= 0) { h += g.h[R.p1]; l += g.l[R.p1]; }
+  if constexpr (R.r1 >= 0) { h -= g.h[R.r1]; l -= g.l[R.r1]; }
+  if constexpr (dnu == 1) { h += g.rh; l += g.rl; }
+  if constexpr (dnu == -1) { h -= g.rh; l -= g.rl; }
+  return h + l;
+}
+
+template <int J>
+__device__ __forceinline__ float ln_inv_kc(const GibbsF &g) {
+  constexpr RxStruct R = kRx[J];
+  constexpr int dnu = n_prod(R) - n_reac(R);
+  float q = g.g[R.p0] - g.g[R.r0];
+  if constexpr (R.p1 >= 0) q += g.g[R.p1];
+  if constexpr (R.r1 >= 0) q -= g.g[R.r1];
+  if constexpr (dnu == 1) q += g.r;
+  if constexpr (dnu == -1) q -= g.r;
+  return q;
+}
+
+template <int J, typename Gibbs>
+__device__ __forceinline__ void reaction_mixed(const MechTables &mt, const RateInputsF &in,
+                                               const Gibbs &g, float (&wdot)[NSP]) {
+  constexpr RxStruct R = kRx[J];
   float lnkf = fmaf(mt.f.beta[J], in.lnT, mt.f.lnA[J]) - mt.f.Ta[J] * in.invT;
   float kf = mt.kconst[J] == 1 ? mt.f.A[J] : expf(lnkf);
   float M = 0.0f;
@@ -66,13 +103,7 @@ __device__ __forceinline__ void reaction_mixed(const MechTables &mt, const RateI
   if constexpr (R.r1 >= 0) qf *= in.c[R.r1];
   float q = qf;
   if (mt.reversible[J]) {
-    // ln(1/K_c) in G: products' g minus reactants' g plus (sum nu) ln(R_u T / p_ref)
-    G lnQ = g[R.p0] - g[R.r0];
-    if constexpr (R.p1 >= 0) lnQ += g[R.p1];
-    if constexpr (R.r1 >= 0) lnQ -= g[R.r1];
-    if constexpr (dnu == 1) lnQ += lnRTP;
-    if constexpr (dnu == -1) lnQ -= lnRTP;
-    const float kr = (kf > 0.0f) ? expf(lnkf + (float)lnQ) : 0.0f;
+    const float kr = (kf > 0.0f) ? expf(lnkf + ln_inv_kc<J>(g)) : 0.0f;
     float qr = kr * in.c[R.p0];
     if constexpr (R.p1 >= 0) qr *= in.c[R.p1];
     q = qf - qr;
@@ -84,11 +115,11 @@ __device__ __forceinline__ void reaction_mixed(const MechTables &mt, const RateI
   if constexpr (R.p1 >= 0) wdot[R.p1] += q;
 }
 
-template <typename G, int... J>
+template <typename Gibbs, int... J>
 __device__ __forceinline__ void all_reactions_mixed(const MechTables &mt, const RateInputsF &in,
-                                                    const G (&g)[NSP], G lnRTP, float (&wdot)[NSP],
+                                                    const Gibbs &g, float (&wdot)[NSP],
                                                     std::integer_sequence<int, J...>) {
-  (reaction_mixed<J, G>(mt, in, g, lnRTP, wdot), ...);
+  (reaction_mixed<J, Gibbs>(mt, in, g, wdot), ...);
 }
 
 // dY/dt (fp32) of one cell at fixed (rho, e) from the fp32 stage state U.
@@ -96,26 +127,26 @@ __device__ __forceinline__ void all_reactions_mixed(const MechTables &mt, const 
 __device__ __forceinline__ bool cell_rhs_mixed(const MechTables &mt, const float (&U)[NSP],
                                                float rho_f, float invRho_f, double eR, double &T,
                                                float (&F)[NSP]) {
-  double yw[NSP];
+  double Y[NSP];
 #pragma unroll
-  for (int k = 0; k < NSP; ++k) yw[k] = (double)U[k] * mt.invW[k];
-  if (!solve_T(mt, yw, eR, T)) return false;
+  for (int k = 0; k < NSP; ++k) Y[k] = f2d(U[k]);
+  if (!solve_T(mt, Y, eR, T)) return false;
   const double lnT = log_t(T);
-  const double invT = 1.0 / T;
+  const double invT = rcp1(T);
   const double oml = 1.0 - lnT;
-  const int range = T >= mt.T_mid;
-  double g[NSP];
+  const int range = ge_nonneg(T, mt.T_mid);
+  GibbsHL g;
 #pragma unroll
   for (int k = 0; k < NSP; ++k) {
     const double *gc = mt.gc[range][k];
-    double gk = fma(T, fma(T, fma(T, fma(T, gc[4], gc[3]), gc[2]), gc[1]), fma(gc[5], invT, gc[6]));
-    g[k] = fma(gc[0], oml, gk);
+    const double gk = fma(T, fma(T, fma(T, fma(T, gc[4], gc[3]), gc[2]), gc[1]), fma(gc[5], invT, gc[6]));
+    split_hilo(fma(gc[0], oml, gk), g.h[k], g.l[k]);
   }
-  const double lnRTP = lnT + mt.ln_R_over_Pref;
+  split_hilo(lnT + mt.ln_R_over_Pref, g.rh, g.rl);
   RateInputsF in;
-  in.lnT = (float)lnT;
-  in.invT = (float)invT;
-  in.T = (float)T;
+  in.lnT = d2f(lnT);
+  in.invT = d2f(invT);
+  in.T = d2f(T);
   float ctot = 0.0f, wdot[NSP];
 #pragma unroll
   for (int k = 0; k < NSP; ++k) {
@@ -124,7 +155,7 @@ __device__ __forceinline__ bool cell_rhs_mixed(const MechTables &mt, const float
     wdot[k] = 0.0f;
   }
   in.ctot = ctot;
-  all_reactions_mixed(mt, in, g, lnRTP, wdot, std::make_integer_sequence<int, NRX>{});
+  all_reactions_mixed(mt, in, g, wdot, std::make_integer_sequence<int, NRX>{});
 #pragma unroll
   for (int k = 0; k < NSP; ++k) F[k] = wdot[k] * mt.f.W[k] * invRho_f;
   return true;
@@ -180,14 +211,14 @@ __device__ __forceinline__ bool cell_rhs_f32(const MechTables &mt, const float (
   const float invT = 1.0f / T;
   const float oml = 1.0f - lnT;
   const int range = T >= mt.f.T_mid;
-  float g[NSP];
+  GibbsF g;
 #pragma unroll
   for (int k = 0; k < NSP; ++k) {
     const float *gc = mt.f.gc[range][k];
     const float gk = fmaf(T, fmaf(T, fmaf(T, fmaf(T, gc[4], gc[3]), gc[2]), gc[1]), fmaf(gc[5], invT, gc[6]));
-    g[k] = fmaf(gc[0], oml, gk);
+    g.g[k] = fmaf(gc[0], oml, gk);
   }
-  const float lnRTP = lnT + mt.f.ln_R_over_Pref;
+  g.r = lnT + mt.f.ln_R_over_Pref;
   RateInputsF in;
   in.lnT = lnT;
   in.invT = invT;
@@ -200,7 +231,7 @@ __device__ __forceinline__ bool cell_rhs_f32(const MechTables &mt, const float (
     wdot[k] = 0.0f;
   }
   in.ctot = ctot;
-  all_reactions_mixed(mt, in, g, lnRTP, wdot, std::make_integer_sequence<int, NRX>{});
+  all_reactions_mixed(mt, in, g, wdot, std::make_integer_sequence<int, NRX>{});
 #pragma unroll
   for (int k = 0; k < NSP; ++k) F[k] = wdot[k] * mt.f.W[k] * invRho;
   return true;

@@ -80,7 +80,7 @@ __global__ void k_features(const __grid_constant__ MechTables mt, int64_t n, con
     inv_w += yw[k];
   }
   double T = Tg0 ? Tg0[i] : CUDART_NAN;
-  const bool good = isfinite(rho[i]) && rho[i] > 0.0 && isfinite(e[i]) && solve_T(mt, yw, e[i] / R_U, T);
+  const bool good = isfinite(rho[i]) && rho[i] > 0.0 && isfinite(e[i]) && solve_T(mt, y, e[i] / R_U, T);
   if (!good) T = 1500.0;
   const double p = rho[i] * R_U * T * inv_w;
   const double dt = dt_cell ? dt_cell[i] : dt_scalar;
@@ -304,11 +304,8 @@ __global__ void __launch_bounds__(128)
   }
   if (!reason && !(ymin >= -(double)sc.neg_tol)) reason = kFbNegative;
   // temperature of the projected state (fp64 Newton from the input temperature)
-  double yw[NSP];
-#pragma unroll
-  for (int k = 0; k < NSP; ++k) yw[k] = y1[k] * mt.invW[k];
   double T1 = (double)x[0];
-  const bool tok = solve_T(mt, yw, e[i] / R_U, T1);
+  const bool tok = solve_T(mt, y1, e[i] / R_U, T1);
   if (!reason && !(tok && fabs(T1 - (double)x[0]) <= (double)sc.max_dT)) reason = kFbTemperature;
   if (!reason && sc.err_tol > 0.0f) {
     double dT = 0.0, rate = 0.0;

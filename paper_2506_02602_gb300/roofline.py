@@ -5,9 +5,9 @@ per attempted RK step, five right-hand-side evaluations plus the register update
 the WRMS norm of Eq. 21-22; per cell, the final temperature solve.  Each right-hand
 side is counted from the mechanism structure in the formulation the kernels use:
 
-  Newton on mixture coefficients (assembly + 2 iterations), ln T, 1/T, per species the
-  NASA-7 Gibbs function (one combined polynomial) and G_k = exp(-g_k/RT) with its
-  reciprocal, per reaction the
+  Newton on mixture coefficients sum_k Y_k ec_k / W_k (assembly + 2 iterations), ln T,
+  1/T, per species the NASA-7 Gibbs function (one combined polynomial) and
+  G_k = exp(-g_k/RT) with its reciprocal, per reaction the
   Arrhenius exponential, the products of the law of mass action (Eq. 16) with the
   equilibrium-constant factors, the third-body sums, the Troe fall-off terms, and the
   conversion F_k = W_k wdot_k / rho.
@@ -37,8 +37,8 @@ NEWTON_ITERS = 2
 
 
 def newton_flops(iters: int = NEWTON_ITERS) -> int:
-    assembly = NSP + 6 * NSP * 2          # Y/W, 6 mixture coefficients x 9 FMAs
-    per_iter = 5 * 2 + (4 * 2 + 4) + 3 + 1  # e(T) Horner, cv(T) Horner + scalings, update, test
+    assembly = 6 * NSP * 2 + 4 + 1        # 6 mixture coefficients x 9 FMAs, c_v scalings, - e/R
+    per_iter = 5 * 2 + 4 * 2 + 2 + 1      # e(T) and c_v(T) Horner, reciprocal x residual, update
     return assembly + iters * per_iter
 
 
@@ -47,7 +47,7 @@ def rhs_flops(mech: dict | None = None) -> int:
     temperature-independent rates (no exponential) and third-body efficiency lists."""
     T = TRANSCENDENTAL
     f = newton_flops()
-    f += NSP                                   # concentrations
+    f += 2 * NSP                               # concentrations rho Y_k / W_k
     f += T + 1 + 2 + 1 + 1 + (NSP - 1)         # ln T, 1/T, RT/p, p/RT, 1 - ln T, total conc.
     f += NSP * (12 + T + 1)                    # g/RT (6 FMAs), G = exp(-g), 1/G
     for j, (nr, npr, typ, troe_n) in enumerate(_RX):
@@ -92,13 +92,14 @@ def launch_flops(total_attempted_steps: int, ncells: int, mech: dict | None = No
 
 def rhs_flops_mixed_fp64(mech: dict | None = None) -> int:
     """The part of one mixed-precision right-hand side that stays fp64: the temperature
-    solve, ln T, 1/T, the Gibbs functions and the equilibrium exponents ln(1/K_c)."""
+    solve, ln T, 1/T, the Gibbs functions and ln(R T / p), and the split of each of those
+    into the fp32 hi / lo parts from which ln(1/K_c) is summed in fp32 (one fp64
+    subtraction each; the sums themselves are fp32 and not credited)."""
     T = TRANSCENDENTAL
-    f = NSP + newton_flops()                   # Y/W from the fp32 stage state, Newton
+    f = newton_flops()
     f += T + 1 + 1 + 1                         # ln T, 1/T, 1 - ln T, ln(R T / p)
     f += NSP * 12                              # g_k / RT: 6 FMAs each
-    for j, (nr, npr, typ, troe_n) in enumerate(_RX):
-        f += (nr + npr - 1) + (1 if nr != npr else 0)  # ln(1/K_c)
+    f += NSP + 1                               # x - hi of the splits
     return f
 
 

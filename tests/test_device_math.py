@@ -1,6 +1,8 @@
-"""The kernels' table-driven fp64 exp / log (Tang's methods) against the CUDA library
-and the host's libm, on the GPU through chem_diag_math: at most 2 ulp apart over the
-argument ranges the integrator uses."""
+"""The kernels' device math on the GPU through chem_diag_math: the table-driven fp64
+exp / log (Tang's methods) against the CUDA library and the host's libm (at most 2 ulp
+apart over the argument ranges the integrator uses); the Newton-Raphson reciprocals
+against exact division; the integer-pipe fp32 <-> fp64 conversions and the 2^-12-grid
+hi/lo split against their IEEE-754 definitions (numpy's round-to-nearest-even)."""
 import numpy as np
 import pytest
 
@@ -48,3 +50,81 @@ def test_log_matches_library(lib):
     assert ulps(mine[nz], cuda[nz]).max() <= 2.0
     assert ulps(mine[nz], ref[nz]).max() <= 2.0
     assert mine[-4] == 0.0
+
+
+def test_reciprocals(lib):
+    """rcp2 within 2 ulp of the exact 1/x; the hardware approximation within 2^-19
+    relative, one Newton-Raphson step (rcp1) within 2^-38: each step squares the error."""
+    rng = np.random.default_rng(9)
+    x = np.concatenate([np.exp(rng.uniform(-690, 690, 200000)), -np.exp(rng.uniform(-690, 690, 50000)),
+                        rng.uniform(150.0, 6500.0, 100000), rng.uniform(1e-3, 1e4, 100000),
+                        [1.0, 2.0, 0.5, 3.0, 1500.0, 1e-300, 1e300]])
+    exact = 1.0 / x
+    r2 = lib.diag_math(5, _dev(x)).cpu().numpy()
+    r1 = lib.diag_math(4, _dev(x)).cpu().numpy()
+    r0 = lib.diag_math(6, _dev(x)).cpu().numpy()
+    assert ulps(r2, exact).max() <= 2.0
+    e1 = np.abs(r1 / exact - 1.0).max()
+    e0 = np.abs(r0 / exact - 1.0).max()
+    assert e0 <= 2.0 ** -19, e0
+    assert e1 <= 2.0 ** -38, e1
+    assert e1 <= 2.0 * e0 * e0 + 2.0 ** -52
+
+
+def _f32(x):
+    """IEEE round-to-nearest-even fp64 -> fp32 (numpy), with magnitudes below the fp32
+    normal range taken to signed zero."""
+    with np.errstate(over="ignore"):
+        f = np.asarray(x, dtype=np.float64).astype(np.float32).astype(np.float64)
+    tiny = np.abs(np.asarray(x)) < 2.0 ** -126
+    return np.where(tiny, np.copysign(0.0, x), f)
+
+
+def test_fp64_to_fp32_conversion(lib):
+    rng = np.random.default_rng(10)
+    x = np.concatenate([
+        rng.standard_normal(100000) * np.exp(rng.uniform(-80, 80, 100000)),
+        np.exp(rng.uniform(-100, 100, 50000)) * rng.choice([-1.0, 1.0], 50000),
+        # ties and near-ties: fp32 values plus half an fp32 ulp, and a hair either side
+        *[(lambda f: f + 0.5 * np.spacing(f.astype(np.float32)).astype(np.float64) * s)(
+            rng.uniform(1.0, 2.0, 20000).astype(np.float32).astype(np.float64) * 2.0 ** rng.integers(-120, 120, 20000))
+          for s in (1.0, 1.0 + 1e-12, 1.0 - 1e-12)],
+        [0.0, -0.0, 1.0, -1.0, 3.4028234663852886e38, 3.4028235677973366e38, 1e39, -1e300,
+         2.0 ** -126, 2.0 ** -127, -1e-300, 1.1754942e-38],
+    ])
+    got = lib.diag_math(7, _dev(x)).cpu().numpy()
+    want = _f32(x)
+    same = (got == want) & (np.signbit(got) == np.signbit(want))
+    assert same.all(), x[~same][:5]
+    special = np.array([np.inf, -np.inf, np.nan])
+    g = lib.diag_math(7, _dev(special)).cpu().numpy()
+    assert g[0] == np.inf and g[1] == -np.inf and np.isnan(g[2])
+
+
+def test_fp32_to_fp64_conversion(lib):
+    rng = np.random.default_rng(11)
+    f = np.concatenate([rng.standard_normal(100000) * np.exp(rng.uniform(-80, 80, 100000)),
+                        [0.0, -0.0, 1.0, 2.0 ** -126, -(2.0 ** -126), 3.4028234663852886e38, 1e-45]])
+    f = f.astype(np.float32).astype(np.float64)       # exact fp32 values
+    got = lib.diag_math(8, _dev(f)).cpu().numpy()
+    want = np.where(np.abs(f) < 2.0 ** -126, np.copysign(0.0, f), f)
+    assert np.array_equal(got, want)
+    g = lib.diag_math(8, _dev(np.array([np.inf, -np.inf, np.nan]))).cpu().numpy()
+    assert g[0] == np.inf and g[1] == -np.inf and np.isnan(g[2])
+
+
+def test_hilo_split(lib):
+    """hi is x truncated toward zero to a multiple of 2^-12, exactly; hi + lo = x to 2^-37;
+    signed sums of a few hi parts are exact in fp32."""
+    rng = np.random.default_rng(12)
+    x = np.concatenate([rng.uniform(-700.0, 700.0, 200000), rng.uniform(-1e-3, 1e-3, 20000),
+                        rng.uniform(-4000.0, 4000.0, 20000), [0.0, 2.0 ** -12, -(2.0 ** -12), 1e-20, 1023.75]])
+    hi = lib.diag_math(9, _dev(x)).cpu().numpy()
+    lo = lib.diag_math(10, _dev(x)).cpu().numpy()
+    assert np.array_equal(hi, np.trunc(x * 4096.0) / 4096.0)
+    assert np.abs(hi + lo - x).max() <= 2.0 ** -37
+    # the fp32 sum of hi parts of |x| < 1000 equals the exact sum
+    h = hi[:200000].reshape(-1, 4)
+    s32 = (((h[:, 0].astype(np.float32) - h[:, 1].astype(np.float32)) + h[:, 2].astype(np.float32))
+           - h[:, 3].astype(np.float32))
+    assert np.array_equal(s32.astype(np.float64), h[:, 0] - h[:, 1] + h[:, 2] - h[:, 3])
