@@ -186,12 +186,14 @@ int build_tables(const chem_mechanism *m, MechTables *t) {
       t->troe_i1[j] = kRx[j].troe_n ? 1.0 / m->troe[j][2] : 0.0;
       t->troe_T2[j] = m->troe[j][3];
     }
-    int any = 0;
+    int any = 0, mask = 0;
     for (int k = 0; k < NSP; ++k) {
       t->effm1[j][k] = kRx[j].type == ELEM ? 0.0 : m->eff[j][k] - 1.0;
       any |= t->effm1[j][k] != 0.0;
+      mask |= (t->effm1[j][k] != 0.0) << k;
     }
     t->has_eff[j] = any;
+    t->eff_mask[j] = mask;
   }
   // element matrix (standard atomic masses of H, O, N)
   const double amass[CHEM_NUM_ELEMENTS] = {1.008e-3, 15.999e-3, 14.007e-3};

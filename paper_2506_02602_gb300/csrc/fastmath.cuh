@@ -1,13 +1,16 @@
-// fastmath.cuh -- table-driven fp64 exp and log for the FP64-pipe-bound kernels.
+// fastmath.cuh -- fp64 device math for the FP64-pipe-bound kernels: table-driven exp
+// and log, Newton-Raphson reciprocals, and fp32 <-> fp64 conversions, compares and
+// clamps on the integer pipe.
 //
 // On GB300 the FP64 pipe issues 2 lanes per clock per SM, and a library fp64 exp takes
 // about 20 of those slots (log about 37).  The right-hand side needs ~38 exponentials
 // and ~5 logarithms, so these two functions dominate its FP64 cost.  The versions here
 // follow Tang's table-driven methods (ACM TOMS 15 (1989) 144-157 for exp, 16 (1990)
 // 378-400 for log) with Taylor polynomials, in about 10 FP64 operations each; the
-// exponent and table-index arithmetic runs on the integer pipe and the 64-entry tables
-// live in shared memory.  Accuracy is about 1 ulp on the ranges used (checked against the
-// CUDA library functions by the GPU tests through chem_diag_math).
+// exponent and table-index arithmetic runs on the integer pipe and the 128-entry (exp)
+// and 65-entry (log) tables live in shared memory.  Accuracy is about 1 ulp on the
+// ranges used (checked against the CUDA library functions by the GPU tests through
+// chem_diag_math).
 #pragma once
 
 #include <cstdint>
@@ -19,44 +22,51 @@ namespace chem {
 // Per-block copies of the tables: divergent table reads from shared memory cost far
 // less latency than L1 round trips.  Every kernel that calls exp_t / log_t fills them
 // first with load_math_tables() (all threads, then a barrier).
-__shared__ double s_exp2_64[64];
+__shared__ double s_exp2_128[128];
 __shared__ double s_log_inv[65];
 __shared__ double s_log_tab[65];
 __shared__ double s_log_tab_m1[65];
 
 __device__ __forceinline__ void load_math_tables() {
-  for (int i = threadIdx.x; i < 65; i += blockDim.x) {
-    if (i < 64) s_exp2_64[i] = k_exp2_64[i];
-    s_log_inv[i] = k_log_inv[i];
-    s_log_tab[i] = k_log_tab[i];
-    s_log_tab_m1[i] = k_log_tab_m1[i];
+  for (int i = threadIdx.x; i < 128; i += blockDim.x) {
+    s_exp2_128[i] = k_exp2_128[i];
+    if (i < 65) {
+      s_log_inv[i] = k_log_inv[i];
+      s_log_tab[i] = k_log_tab[i];
+      s_log_tab_m1[i] = k_log_tab_m1[i];
+    }
   }
   __syncthreads();
 }
 
-// exp(x).  Exact to ~1 ulp for x in [-708, 709]; the table index k is clamped with
-// integer min/max and the 2^m scale is applied by a multiply, so arguments outside
-// that range still give +inf above and a value below 1e-290 in magnitude below,
-// with no fp64 compares.  Kept out of line: the right-hand side calls it ~38 times,
-// and one shared copy keeps the kernel's code within the instruction cache (measured
-// 4 % faster than inlining it on GB300).
+// exp(x).  About 1 ulp for x in [-708, 709]: x = (128 m + j) ln2/128 + r, |r| <= ln2/256,
+// e^r - 1 by its degree-5 Taylor polynomial (truncation below 6e-19 relative), and the
+// scale 2^m added to the exponent field of the table entry 2^(j/128) on the integer
+// pipe (10 FP64-pipe operations in all).  Arguments beyond +-710 are first clamped there
+// on the integer pipe, so they still give +inf above and a positive value below 1e-307
+// below, however large; a NaN stays NaN.  Kept out of line: the right-hand side calls it
+// ~38 times, and one shared copy keeps the kernel's code within the instruction cache
+// (measured 4 % faster than inlining it on GB300).
 static __device__ __noinline__ double exp_t(double x) {
+  const long long kLim = 0x40863000'00000000LL;  // 710.0
+  const long long b = __double_as_longlong(x);
+  const long long ab = b & 0x7fffffffffffffffLL;
+  if (ab > kLim && ab <= 0x7ff0000000000000LL) x = __longlong_as_double((b & (long long)0x8000000000000000ULL) | kLim);
   const double kShift = 6755399441055744.0;  // 1.5 * 2^52: rounds to an integer in the low bits
-  const double t = fma(x, kInvLn2x64, kShift);
-  const int k = min(max(__double2loint(t), -65408), 65471);  // 2^(k>>6) stays a normal double
+  const double t = fma(x, kInvLn2x128, kShift);
+  const int k = min(max(__double2loint(t), -130816), 130943);  // 2^(k>>7) stays a normal double
   const double kd = (double)k;
-  double r = fma(-kd, kLn2d64Hi, x);
-  r = fma(-kd, kLn2d64Lo, r);
-  // e^r - 1 = r + r^2/2 + r^3/6 + r^4/24 + r^5/120 + r^6/720, |r| <= ln2/128
-  double p = fma(r, 1.0 / 720.0, 1.0 / 120.0);
-  p = fma(r, p, 1.0 / 24.0);
+  double r = fma(-kd, kLn2d128Hi, x);
+  r = fma(-kd, kLn2d128Lo, r);
+  // e^r - 1 = r + r^2/2 + r^3/6 + r^4/24 + r^5/120
+  double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
   p = fma(r, p, 1.0 / 6.0);
   p = fma(r, p, 0.5);
   p = fma(r, p, 1.0);
   p = r * p;
-  const double tj = s_exp2_64[k & 63];
-  const double scale = __hiloint2double(((k >> 6) + 1023) << 20, 0);
-  return fma(tj, p, tj) * scale;
+  const double tj = s_exp2_128[k & 127];
+  const double ts = __hiloint2double(__double2hiint(tj) + ((k >> 7) << 20), __double2loint(tj));
+  return fma(ts, p, ts);
 }
 
 // log(x) for positive normal finite x (the kernels' arguments: temperatures, F_cent,

@@ -99,6 +99,7 @@ struct MechTables {
   // third-body efficiencies minus one: [M] = sum_k c_k + sum_k effm1 c_k
   double effm1[NRX][NSP];
   int32_t has_eff[NRX];
+  int32_t eff_mask[NRX];  // bit k set where effm1[j][k] != 0 (the fp64 sums skip the rest)
   double ln_R_over_Pref;  // ln(R_u / p_ref): ln(R_u T / p_ref) = ln T + this
   // Newton's quadratic-convergence stop: after a step dT the remaining error is at most
   // (C / 2) dT^2 with C = max |c_v' / c_v| of the tables on [200, 6000] K, so a step with

@@ -11,10 +11,12 @@
 //   - g_k / RT comes from one combined NASA-7 polynomial per species (6 FMAs);
 //   - Newton works on mixture coefficients m_i = sum_k Y_k (ec_ki / W_k), assembled once
 //     per evaluation (54 FMAs), so each iteration is two Horner chains and a reciprocal;
-//   - equilibrium constants come from per-species G_k = exp(-g_k / RT) and 1/G_k:
+//   - equilibrium constants come from per-species G_k = exp(-g_k / RT):
 //     1/K_c,j = prod_reactants G * prod_products (1/G) * (R_u T / p_ref)^(sum nu), i.e.
 //     9 exponentials + 9 reciprocals per evaluation instead of one exponential per
-//     reaction;
+//     reaction; with a_k = c_k / G_k the net rate of progress is
+//     k_f (prod_reactants c - prod_reactants G * prod_products a * (R_u T / p_ref)^(sum nu)),
+//     one FMA for the reverse direction;
 //   - reciprocals are Newton-Raphson-refined hardware approximations (rcp1 / rcp2), ~3.5
 //     and ~5.7 FP64-pipe slots against ~9 for an IEEE divide; compares, clamps and
 //     fp32 <-> fp64 conversions run on the integer pipe (fastmath.cuh);
@@ -111,7 +113,7 @@ struct RateInputs {
   double lnT, invT, RTP, PRT, ctot;
   double c[NSP];   // clamped concentrations, mol/m^3
   double G[NSP];   // exp(-g_k / (R_u T))
-  double iG[NSP];  // 1 / G_k
+  double iG[NSP];  // 1 / G_k (with the one-way fluxes) or c_k / G_k (net rates only)
 };
 
 // Troe broadening factor (Gilbert, Luther & Troe 1983).
@@ -154,7 +156,8 @@ __device__ __forceinline__ void reaction(const MechTables &mt, const RateInputs 
     M = in.ctot;
     if (mt.has_eff[J]) {
 #pragma unroll
-      for (int k = 0; k < NSP; ++k) M = fma(mt.effm1[J][k], in.c[k], M);
+      for (int k = 0; k < NSP; ++k)
+        if ((mt.eff_mask[J] >> k) & 1) M = fma(mt.effm1[J][k], in.c[k], M);
     }
   }
   if constexpr (R.type == FALLOFF) {
@@ -162,28 +165,45 @@ __device__ __forceinline__ void reaction(const MechTables &mt, const RateInputs 
     const double Pr = k0 * M * rcp2(kf);
     kf = (Pr > 0.0) ? kf * (Pr * rcp2(1.0 + Pr)) * troe_F<J>(mt, T, in.invT, Pr) : 0.0;
   }
-  double qf = kf * in.c[R.r0];
-  if constexpr (R.r1 >= 0) qf *= in.c[R.r1];
-  double q = qf, qr = 0.0;
-  if (mt.reversible[J]) {
-    double kr = kf * in.G[R.r0];
-    if constexpr (R.r1 >= 0) kr *= in.G[R.r1];
-    kr *= in.iG[R.p0];
-    if constexpr (R.p1 >= 0) kr *= in.iG[R.p1];
-    if constexpr (dnu == 1) kr *= in.RTP;
-    if constexpr (dnu == -1) kr *= in.PRT;
-    qr = kr * in.c[R.p0];
-    if constexpr (R.p1 >= 0) qr *= in.c[R.p1];
-    q = qf - qr;
-  }
-  if constexpr (R.type == THIRD_BODY) q *= M;
+  double q;
   if constexpr (kDestr) {
+    double qf = kf * in.c[R.r0];
+    if constexpr (R.r1 >= 0) qf *= in.c[R.r1];
+    double qr = 0.0;
+    q = qf;
+    if (mt.reversible[J]) {
+      double kr = kf * in.G[R.r0];
+      if constexpr (R.r1 >= 0) kr *= in.G[R.r1];
+      kr *= in.iG[R.p0];
+      if constexpr (R.p1 >= 0) kr *= in.iG[R.p1];
+      if constexpr (dnu == 1) kr *= in.RTP;
+      if constexpr (dnu == -1) kr *= in.PRT;
+      qr = kr * in.c[R.p0];
+      if constexpr (R.p1 >= 0) qr *= in.c[R.p1];
+      q = qf - qr;
+    }
     const double m = (R.type == THIRD_BODY) ? M : 1.0;
     dflux[R.r0] += m * qf;
     if constexpr (R.r1 >= 0) dflux[R.r1] += m * qf;
     dflux[R.p0] += m * qr;
     if constexpr (R.p1 >= 0) dflux[R.p1] += m * qr;
+  } else {
+    // q = k_f (prod c_reactants - prod G_reactants prod (c / G)_products (R_u T / p)^dnu),
+    // the same net rate as k_f prod c - k_r prod c with k_r = k_f / K_c
+    double cf = in.c[R.r0];
+    if constexpr (R.r1 >= 0) cf *= in.c[R.r1];
+    if (mt.reversible[J]) {
+      double gr = in.G[R.r0];
+      if constexpr (R.r1 >= 0) gr *= in.G[R.r1];
+      if constexpr (dnu == 1) gr *= in.RTP;
+      if constexpr (dnu == -1) gr *= in.PRT;
+      double ap = in.iG[R.p0];
+      if constexpr (R.p1 >= 0) ap *= in.iG[R.p1];
+      cf = fma(-gr, ap, cf);
+    }
+    q = kf * cf;
   }
+  if constexpr (R.type == THIRD_BODY) q *= M;
   wdot[R.r0] -= q;
   if constexpr (R.r1 >= 0) wdot[R.r1] -= q;
   wdot[R.p0] += q;
@@ -221,7 +241,7 @@ __device__ __forceinline__ void production_rates(const MechTables &mt, double T,
     // clamp keeps G finite far outside the tables' range
     g = clamp_abs(g, 700.0);
     in.G[k] = exp_t(-g);
-    in.iG[k] = rcp2(in.G[k]);
+    in.iG[k] = kDestr ? rcp2(in.G[k]) : c[k] * rcp2(in.G[k]);
     wdot[k] = 0.0;
     if constexpr (kDestr) dflux[k] = 0.0;
   }

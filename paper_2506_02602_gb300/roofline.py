@@ -49,16 +49,15 @@ def rhs_flops(mech: dict | None = None) -> int:
     f = newton_flops()
     f += 2 * NSP                               # concentrations rho Y_k / W_k
     f += T + 1 + 2 + 1 + 1 + (NSP - 1)         # ln T, 1/T, RT/p, p/RT, 1 - ln T, total conc.
-    f += NSP * (12 + T + 1)                    # g/RT (6 FMAs), G = exp(-g), 1/G
+    f += NSP * (12 + T + 1 + 1)                # g/RT (6 FMAs), G = exp(-g), 1/G, c/G
     for j, (nr, npr, typ, troe_n) in enumerate(_RX):
         kconst = mech is not None and mech["b"][j] == 0.0 and mech["Ea"][j] == 0.0
         f += 0 if kconst else T + 4            # Arrhenius exponential
-        f += nr                                # forward product
-        f += nr + npr + (1 if nr != npr else 0) + npr + 1  # reverse rate, product, difference
+        f += (nr - 1) + 1                      # prod c_reactants, times k_f
+        f += (nr - 1) + (1 if nr != npr else 0) + (npr - 1) + 2  # prod G, prod c/G, (RT/p)^dnu, FMA
         f += nr + npr                          # production-rate updates
-        if typ != 0:
-            has_eff = mech is None or any(abs(x - 1.0) > 0 for x in mech["eff"][j])
-            f += 2 * NSP if has_eff else 0     # [M]
+        if typ != 0:                           # [M]: one FMA per efficiency != 1
+            f += 2 * (NSP if mech is None else sum(abs(x - 1.0) > 0 for x in mech["eff"][j]))
         if typ == 1:
             f += 1
         if typ == 2:
