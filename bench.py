@@ -235,7 +235,7 @@ MLP_FLOPS_PER_ROW = 2 * (16 * 256 + 256 * 256 * 2 + 256 * 16)  # padded 16-256-2
 # DRAM bytes (read + write) per cell of one k_lsrk launch, from an ncu capture of the
 # 131,072-cell slice (profiles/k_lsrk_detonation_slice.md), scaled by the cell count;
 # to be set to None whenever the kernel changes until it is captured again.
-TRAFFIC_PER_CELL = {"fp64": 12.742912e6 / 131072, "mixed": 12.703232e6 / 131072}
+TRAFFIC_PER_CELL = {"fp64": 12.731904e6 / 131072, "mixed": 12.723200e6 / 131072}  # mean of 2 launches each
 
 
 def _bf16_peak():
@@ -478,8 +478,9 @@ def amr_leg(ctx, steps, dev):
     of 1e-7/2^l s, heavy-tailed stiffness): the persistent work-stealing launch, with the
     options chem_autotune_batched picks on this batch, against the plain path of one
     chem_integrate launch per box and substep on 8 streams (one stream per box, round
-    robin).  Both run the same per-cell arithmetic, so their results must be
-    bit-identical."""
+    robin).  Both run the same per-cell arithmetic; compiled shapes may contract
+    multiply-adds differently, so the line reports how far the two agree: the largest
+    relative difference in T and the share of cells whose T and Y are bit-identical."""
     import torch
     from chem_inputs import workloads
     b = workloads.amr_batch()
@@ -532,7 +533,9 @@ def amr_leg(ctx, steps, dev):
     Yp, Tp, steps_p = Y.cpu().numpy(), T.cpu().numpy(), ns.cpu().numpy()
     per_box()
     tb = min(per_box() for _ in range(steps))
-    same = bool(np.array_equal(Y.cpu().numpy(), Yp) and np.array_equal(T.cpu().numpy(), Tp))
+    Yb, Tb = Y.cpu().numpy(), T.cpu().numpy()
+    same = (Tb == Tp) & np.all(Yb == Yp, axis=0)
+    max_rel_T = float(np.max(np.abs(Tb - Tp) / np.abs(Tp)))
     subs = int((b["box_nsub"].astype(np.int64) * np.diff(off_h)).sum())
     return {"workload": f"AMR-like batch: 256 boxes, {n} cells, {subs} cell-substeps, 3 levels",
             "variant": ctx.variant,
@@ -544,7 +547,7 @@ def amr_leg(ctx, steps, dev):
             "per_box_cells_per_s": n / tb, "per_box_ms": 1e3 * tb,
             "speedup": tb / tp, "cell_substeps_per_s": subs / tp,
             "attempted_steps": int(steps_p.sum()), "max_steps": int(steps_p.max()),
-            "identical_results": same}
+            "vs_per_box": {"max_rel_T": max_rel_T, "bit_identical_frac": float(same.mean())}}
 
 
 def run_ours(args, rank, world, local):

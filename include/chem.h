@@ -106,7 +106,10 @@ typedef struct {
 typedef struct {
   int32_t variant;     /* chem_variant [CHEM_VARIANT_FP64] */
   int32_t max_steps;   /* attempted-step limit per cell and call [100000] */
-  int32_t block_size;  /* threads per block of the integration kernels [128] */
+  int32_t block_size;  /* threads per block of the one-pass integration kernel: 32 or 64
+                          (16 warps per SM, 128 registers a thread) or 128 (12 warps,
+                          170 registers); other values take 128 [0: 64 for the mixed
+                          variant, 128 for fp64] */
   int32_t reserved[5]; /* must be zero */
 } chem_options;
 

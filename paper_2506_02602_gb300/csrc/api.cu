@@ -277,7 +277,10 @@ int chem_setup(const chem_mechanism *mech, const chem_options *opt, chem_ctx **o
     return fail(nullptr, CHEM_ERR_INVALID, "unknown variant %d", o.variant);
   if (o.max_steps < 0) return fail(nullptr, CHEM_ERR_INVALID, "max_steps < 0");
   if (o.max_steps == 0) o.max_steps = 100000;
-  if (o.block_size == 0) o.block_size = 128;
+  // default shape of the one-pass kernel: 16 warps per SM at 128 registers for the
+  // mixed variant (measured 1.7 % faster than 12 warps), 12 at 170 for fp64 (whose 128-
+  // register build spills)
+  if (o.block_size == 0) o.block_size = o.variant == CHEM_VARIANT_MIXED ? 64 : 128;
   for (int i = 0; i < 5; ++i)
     if (o.reserved[i]) return fail(nullptr, CHEM_ERR_INVALID, "reserved options must be zero");
   MechTables t;

@@ -7,9 +7,12 @@
 
 namespace chem {
 
-template <int V>
-__global__ void __launch_bounds__(128) k_lsrk(const __grid_constant__ MechTables mt,
-                                              const CellArgs a, const StepParams p) {
+// BLOCK threads per block, MINB resident blocks per SM.  The register file is split
+// between the SM's four sub-partitions, so 12 warps per SM allow 170 registers a thread
+// (128 x 3) and 16 warps 128 (64 x 8, 32 x 16); anything between rounds down to 128.
+template <int V, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_lsrk(const __grid_constant__ MechTables mt,
+                                                      const CellArgs a, const StepParams p) {
   load_math_tables();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = i < a.n;
@@ -58,15 +61,21 @@ __global__ void k_state_from_TPY(const __grid_constant__ MechTables mt, int64_t 
   e[i] = R_U * e_over_R(m, Ti);
 }
 
+template <int V>
+static void launch_shape(const MechTables &mt, const CellArgs &a, const StepParams &p, int block,
+                         cudaStream_t s) {
+  const unsigned grid = (unsigned)((a.n + block - 1) / block);
+  if (block == 32) k_lsrk<V, 32, 16><<<grid, 32, 0, s>>>(mt, a, p);
+  else if (block == 64) k_lsrk<V, 64, 8><<<grid, 64, 0, s>>>(mt, a, p);
+  else k_lsrk<V, 128, 3><<<grid, 128, 0, s>>>(mt, a, p);
+}
+
 cudaError_t launch_lsrk(int variant, const MechTables &mt, const CellArgs &a, const StepParams &p,
                         int block, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  if (block != 128) block = 128;  // the kernel's launch bounds
-  const int64_t grid = (a.n + block - 1) / block;
-  if (variant == CHEM_VARIANT_MIXED)
-    k_lsrk<CHEM_VARIANT_MIXED><<<(unsigned)grid, block, 0, s>>>(mt, a, p);
-  else
-    k_lsrk<CHEM_VARIANT_FP64><<<(unsigned)grid, block, 0, s>>>(mt, a, p);
+  if (block != 32 && block != 64) block = 128;  // the compiled shapes
+  if (variant == CHEM_VARIANT_MIXED) launch_shape<CHEM_VARIANT_MIXED>(mt, a, p, block, s);
+  else launch_shape<CHEM_VARIANT_FP64>(mt, a, p, block, s);
   return cudaGetLastError();
 }
 
