@@ -350,9 +350,9 @@ typedef struct {
   float resid_max;   /* [0.02] largest relative element-mass residual before projection */
   float neg_tol;     /* [1e-6] most negative mass fraction allowed after projection */
   float max_dT;      /* [200] largest accepted |T(t + dt) - T(t)|, K */
-  float err_tol;   /* [5e-4] largest accepted error estimate relative to T (the
+  float err_tol;   /* [6e-4] largest accepted error estimate relative to T (the
                         quadrature error test of chem_surrogate_infer); negative: no test */
-  float rate_max;  /* [1] largest dt * max_k |dY_k/dt| / (|Y_k| + 1e-6) at either end of
+  float rate_max;  /* [1.5] largest dt * max_k |dY_k/dt| / (|Y_k| + 1e-6) at either end of
                         the step for the test to accept; negative: no bound */
 } chem_surrogate_gate;
 

@@ -320,8 +320,13 @@ static SurrogateConsts make_consts(const Surrogate *s, const chem_surrogate_gate
   c.rate_max = g.rate_max;
   c.lam = s->lam;
   c.dt_power = s->dt_power;
-  for (int el = 0; el < 3; ++el)
-    for (int k = 0; k < NSP; ++k) c.E[el][k] = mt.Emat[el][k];
+  for (int el = 0; el < 3; ++el) {
+    c.emask[el] = 0;
+    for (int k = 0; k < NSP; ++k) {
+      c.E[el][k] = mt.Emat[el][k];
+      c.emask[el] |= (mt.Emat[el][k] != 0.0) << k;
+    }
+  }
   return c;
 }
 
@@ -624,8 +629,8 @@ int chem_surrogate_infer(chem_ctx *ctx, const chem_state *state, int64_t n, doub
   if (g.resid_max == 0.0f) g.resid_max = 0.02f;
   if (g.neg_tol == 0.0f) g.neg_tol = 1e-6f;
   if (g.max_dT == 0.0f) g.max_dT = 200.0f;
-  if (g.err_tol == 0.0f) g.err_tol = 5e-4f;
-  if (g.rate_max == 0.0f) g.rate_max = 1.0f;
+  if (g.err_tol == 0.0f) g.err_tol = 6e-4f;
+  if (g.rate_max == 0.0f) g.rate_max = 1.5f;
   const int64_t chunk = n < kInferChunk ? n : kInferChunk;
   e = ensure_infer_buffers(s, chunk, n);
   if (e != cudaSuccess) return sur_cuda(ctx, e, "allocating inference buffers");

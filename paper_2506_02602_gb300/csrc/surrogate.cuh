@@ -52,6 +52,7 @@ struct SurrogateConsts {
   double lam;                           // Box-Cox lambda
   double dt_power;                      // targets scaled by (kSurDtRef / dt)^dt_power
   double E[3][NSP];                     // element mass fraction per unit species mass fraction
+  int32_t emask[3];                     // bit k set where E[el][k] != 0 (the sums skip the rest)
 };
 
 cudaError_t launch_features(const MechTables &mt, int64_t n, const double *rho, const double *e,

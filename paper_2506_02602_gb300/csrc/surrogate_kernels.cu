@@ -45,7 +45,13 @@ __device__ __forceinline__ double boxcox_d(double y, double lam) {
 
 // The features' transform in fp32 (they are fp32 network inputs).
 __device__ __forceinline__ float boxcox_f(double y, float lam) {
-  return (powf(fmaxf((float)y, 1e-30f), lam) - 1.0f) / lam;
+  return (powf(fmaxf(d2f(y), 1e-30f), lam) - 1.0f) / lam;
+}
+
+// max(x, c) for c > 0 on the integer pipe (a negative x, whose bit pattern is a negative
+// integer, gives c)
+__device__ __forceinline__ double max_pos(double x, double c) {
+  return __double_as_longlong(x) > __double_as_longlong(c) ? x : c;
 }
 
 // Y1 from Y0, its fp32 feature bc0 = BC(Y0) and the predicted increment d, as an
@@ -55,10 +61,10 @@ __device__ __forceinline__ float boxcox_f(double y, float lam) {
 // rounding cancels, d = 0 returns Y0 exactly, and a species absent from Y0 can form.
 // A base at or below zero (r = 0) gives Y1 = Y0 - y.
 __device__ __forceinline__ double boxcox_step(double y0, float bc0, float d, float lam) {
-  const double y = fmax(y0, 1e-30);
+  const double y = max_pos(y0, 1e-30);
   const float s = lam * d / fmaf(lam, bc0, 1.0f);
   if (!(s > -1.0f)) return y0 - y;
-  return fma(y, (double)expm1f(log1pf(s) / lam), y0);
+  return fma(y, f2d(expm1f(log1pf(s) / lam)), y0);
 }
 
 // Raw (un-normalised) features and, when Y1 is given, targets of n cells.
@@ -71,23 +77,23 @@ __global__ void k_features(const __grid_constant__ MechTables mt, int64_t n, con
                            uint8_t *ok) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double yw[NSP], y[NSP];
+  double y[NSP];
   double inv_w = 0.0;
 #pragma unroll
   for (int k = 0; k < NSP; ++k) {
     y[k] = Y0[k * ld0 + i];
-    yw[k] = y[k] * mt.invW[k];
-    inv_w += yw[k];
+    inv_w = fma(y[k], mt.invW[k], inv_w);
   }
   double T = Tg0 ? Tg0[i] : CUDART_NAN;
-  const bool good = isfinite(rho[i]) && rho[i] > 0.0 && isfinite(e[i]) && solve_T(mt, y, e[i] / R_U, T);
+  const bool good =
+      isfinite(rho[i]) && rho[i] > 0.0 && isfinite(e[i]) && solve_T(mt, y, e[i] * (1.0 / R_U), T);
   if (!good) T = 1500.0;
   const double p = rho[i] * R_U * T * inv_w;
   const double dt = dt_cell ? dt_cell[i] : dt_scalar;
   float *x = X + i * kSurIn;
-  x[0] = (float)T;
-  x[1] = logf(fmaxf((float)p, 1e-30f));
-  x[2] = log10f((float)dt);
+  x[0] = d2f(T);
+  x[1] = logf(fmaxf(d2f(p), 1e-30f));
+  x[2] = log10f(d2f(dt));
 #pragma unroll
   for (int k = 0; k < NSP; ++k) x[3 + k] = boxcox_f(y[k], (float)lam);
 #pragma unroll
@@ -167,28 +173,27 @@ __global__ void k_normalize(int64_t n, int ncol, int ld, float *A, const float *
 // Temperature-error estimate of a surrogate result y1 (see the file comment): returns
 // false if a right-hand side fails, else sets dT = est (K) and rate = dt * the largest
 // relative rate of change at either end.  All in fp32 (cell_rhs_f32), whatever the
-// context's variant: an estimate compared with a tolerance of 5e-4 T needs nothing
+// context's variant: an estimate compared with a tolerance of ~5e-4 T needs nothing
 // finer; y1 - y0 is formed in fp64 first, so the defect does not lose it to rounding.
 __device__ __noinline__ bool posterior_error(const MechTables &mt, const double (&y0)[NSP],
-                                          const double (&y1)[NSP], double rho, double eR_d,
-                                          double T0, double T1, double dt, double &dT, double &rate) {
+                                             const double (&y1)[NSP], float rho_f, float eR,
+                                             float T0, float T1f, float dtf, float &dT, float &rate) {
   float u0[NSP], u1[NSP], F0[NSP], F1[NSP];
 #pragma unroll
   for (int k = 0; k < NSP; ++k) {
-    u0[k] = (float)y0[k];
-    u1[k] = (float)y1[k];
+    u0[k] = d2f(y0[k]);
+    u1[k] = d2f(y1[k]);
   }
-  const float rho_f = (float)rho, invRho_f = (float)(1.0 / rho), eR = (float)eR_d;
-  float Ta = (float)T0, Tb = (float)T1;
+  const float invRho_f = 1.0f / rho_f;
+  float Ta = T0, Tb = T1f;
   if (!cell_rhs_f32(mt, u0, rho_f, invRho_f, eR, Ta, F0) || !cell_rhs_f32(mt, u1, rho_f, invRho_f, eR, Tb, F1))
     return false;
-  const float dtf = (float)dt;
   float um[NSP], Fm[NSP];
 #pragma unroll
   for (int k = 0; k < NSP; ++k) um[k] = 0.5f * (u0[k] + u1[k]) + 0.125f * dtf * (F0[k] - F1[k]);
   float Tm = 0.5f * (Ta + Tb);
   if (!cell_rhs_f32(mt, um, rho_f, invRho_f, eR, Tm, Fm)) return false;
-  const float T1f = (float)T1, sdt = dtf * (1.0f / 6.0f);
+  const float sdt = dtf * (1.0f / 6.0f);
   const int range = T1f >= mt.f.T_mid;
   float m[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
@@ -204,12 +209,12 @@ __device__ __noinline__ bool posterior_error(const MechTables &mt, const double 
     const float *c = mt.f.ec[range][k];
     const float ukR =
         fmaf(T1f, fmaf(T1f, fmaf(T1f, fmaf(T1f, fmaf(T1f, c[4], c[3]), c[2]), c[1]), c[0]), c[5]) * mt.f.invW[k];
-    const float defect = (float)(y1[k] - y0[k]) - sdt * (F0[k] + 4.0f * Fm[k] + F1[k]);
+    const float defect = d2f(y1[k] - y0[k]) - sdt * (F0[k] + 4.0f * Fm[k] + F1[k]);
     sum = fmaf(fabsf(ukR - eR), fabsf(defect), sum);
     r = fmaxf(r, fmaxf(fabsf(F0[k]) / (fabsf(u0[k]) + 1e-6f), fabsf(F1[k]) / (fabsf(u1[k]) + 1e-6f)));
   }
-  rate = dt * (double)r;
-  dT = (double)(sum / cvR);
+  rate = dtf * r;
+  dT = sum / cvR;
   return isfinite(dT) && cvR > 0.0f;
 }
 
@@ -241,41 +246,46 @@ __global__ void __launch_bounds__(128)
   }
   if (!reason && !inbox) reason = kFbRange;
   double y0[NSP], y1[NSP];
-  const float unscale = sc.dt_power == 0.0 ? 1.0f : powf((float)(dt / kSurDtRef), (float)sc.dt_power);
+  const float unscale =
+      sc.dt_power == 0.0 ? 1.0f : powf(d2f(dt) * (float)(1.0 / kSurDtRef), d2f(sc.dt_power));
 #pragma unroll
   for (int k = 0; k < NSP; ++k) {
     y0[k] = Y[k * ld + i];
     const float d = fmaf(o[k], sc.tstd[k], sc.tmean[k]) * unscale;
     y1[k] = boxcox_step(y0[k], x[3 + k], d, (float)sc.lam);
   }
-  // element mass fractions before projection and the residual
+  // element mass fractions before projection and the residual (terms with a zero
+  // element fraction skipped: uniform branches on the masks)
   double z0[3] = {0.0, 0.0, 0.0}, r[3] = {0.0, 0.0, 0.0};
 #pragma unroll
   for (int el = 0; el < 3; ++el)
 #pragma unroll
-    for (int k = 0; k < NSP; ++k) {
-      z0[el] += sc.E[el][k] * y0[k];
-      r[el] += sc.E[el][k] * (y1[k] - y0[k]);
-    }
+    for (int k = 0; k < NSP; ++k)
+      if ((sc.emask[el] >> k) & 1) {
+        z0[el] = fma(sc.E[el][k], y0[k], z0[el]);
+        r[el] = fma(sc.E[el][k], y1[k] - y0[k], r[el]);
+      }
   double rn = 0.0, zn = 0.0;
 #pragma unroll
   for (int el = 0; el < 3; ++el) {
-    rn += r[el] * r[el];
-    zn += z0[el] * z0[el];
+    rn = fma(r[el], r[el], rn);
+    zn = fma(z0[el], z0[el], zn);
   }
   if (!reason && !(rn <= (double)sc.resid_max * sc.resid_max * zn)) reason = kFbResidual;
   // weighted least-squares projection onto E Y = E Y0: Y'' = Y' - W E^T (E W E^T)^-1 r
   double w[NSP], M[3][3];
 #pragma unroll
-  for (int k = 0; k < NSP; ++k) w[k] = fmax(y1[k], 1e-12);
+  for (int k = 0; k < NSP; ++k) w[k] = max_pos(y1[k], 1e-12);
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
+    for (int b = a; b < 3; ++b) {
       double s = 0.0;
 #pragma unroll
-      for (int k = 0; k < NSP; ++k) s += sc.E[a][k] * w[k] * sc.E[b][k];
+      for (int k = 0; k < NSP; ++k)
+        if (((sc.emask[a] & sc.emask[b]) >> k) & 1) s = fma(sc.E[a][k] * w[k], sc.E[b][k], s);
       M[a][b] = s;
+      M[b][a] = s;
     }
   // 3x3 solve by Cramer's rule (M is symmetric positive definite for the H, O, N rows)
   const double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
@@ -283,7 +293,7 @@ __global__ void __launch_bounds__(128)
                      M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
   double lamv[3] = {0.0, 0.0, 0.0};
   if (det != 0.0 && isfinite(det)) {
-    const double id = 1.0 / det;
+    const double id = rcp2(det);
     lamv[0] = (r[0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (r[1] * M[2][2] - M[1][2] * r[2]) +
                M[0][2] * (r[1] * M[2][1] - M[1][1] * r[2])) * id;
     lamv[1] = (M[0][0] * (r[1] * M[2][2] - M[1][2] * r[2]) - r[0] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
@@ -293,25 +303,29 @@ __global__ void __launch_bounds__(128)
   } else if (!reason) {
     reason = kFbResidual;
   }
-  double ymin = 1.0;
+  // the correction, and the negativity test on the fp32-rounded result (a NaN fails it)
+  bool neg = false;
 #pragma unroll
   for (int k = 0; k < NSP; ++k) {
     double corr = 0.0;
 #pragma unroll
-    for (int el = 0; el < 3; ++el) corr += sc.E[el][k] * lamv[el];
-    y1[k] -= w[k] * corr;
-    ymin = fmin(ymin, y1[k]);
+    for (int el = 0; el < 3; ++el)
+      if ((sc.emask[el] >> k) & 1) corr = fma(sc.E[el][k], lamv[el], corr);
+    y1[k] = fma(-w[k], corr, y1[k]);
+    neg |= !(d2f(y1[k]) >= -sc.neg_tol);
   }
-  if (!reason && !(ymin >= -(double)sc.neg_tol)) reason = kFbNegative;
+  if (!reason && neg) reason = kFbNegative;
   // temperature of the projected state (fp64 Newton from the input temperature)
-  double T1 = (double)x[0];
-  const bool tok = solve_T(mt, y1, e[i] / R_U, T1);
-  if (!reason && !(tok && fabs(T1 - (double)x[0]) <= (double)sc.max_dT)) reason = kFbTemperature;
+  const double eR = e[i] * (1.0 / R_U);
+  double T1 = f2d(x[0]);
+  const bool tok = solve_T(mt, y1, eR, T1);
+  const float T1f = d2f(T1);
+  if (!reason && !(tok && fabsf(T1f - x[0]) <= sc.max_dT)) reason = kFbTemperature;
   if (!reason && sc.err_tol > 0.0f) {
-    double dT = 0.0, rate = 0.0;
-    const bool jok = posterior_error(mt, y0, y1, rho[i], e[i] / R_U, (double)x[0], T1, dt, dT, rate);
-    if (!jok || !(sc.rate_max < 0.0f || rate <= (double)sc.rate_max)) reason = kFbReactive;
-    else if (!(dT <= (double)sc.err_tol * T1 * (1.0 - 0.5 * rate + rate * rate / 12.0))) reason = kFbError;
+    float dT = 0.0f, rate = 0.0f;
+    const bool jok = posterior_error(mt, y0, y1, d2f(rho[i]), d2f(eR), x[0], T1f, d2f(dt), dT, rate);
+    if (!jok || !(sc.rate_max < 0.0f || rate <= sc.rate_max)) reason = kFbReactive;
+    else if (!(dT <= sc.err_tol * T1f * (1.0f - 0.5f * rate + rate * rate * (1.0f / 12.0f)))) reason = kFbError;
   }
   if (!reason) {
 #pragma unroll
