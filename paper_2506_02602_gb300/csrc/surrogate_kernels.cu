@@ -222,8 +222,10 @@ __device__ __noinline__ bool posterior_error(const MechTables &mt, const double 
 // (z-scored BC increments), the raw features X (un-normalised: T, ln p, log10 dt,
 // BC(Y0)) and the state; writes accepted cells (Y'', T'', status OK, nsteps 0) and
 // appends rejected ones to the fallback list.
+// 4 blocks of 128 per SM (16 warps): the register cap of 128 costs 4 bytes of spill
+// stores, against 8 warps at the uncapped 255 registers.
 template <int V>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 4)
     k_surrogate_finish(const __grid_constant__ MechTables mt, const __grid_constant__ SurrogateConsts sc,
                        int64_t n, double dt, const float *__restrict__ O,
                        const float *__restrict__ Xraw, const uint8_t *__restrict__ Tok,
