@@ -637,7 +637,7 @@ def run_ours(args, rank, world, local):
             note = "fp64 pipe; credited flops (exp/log = 20) / CUDA-event launch time"
         elif v == "mixed":
             flops = roofline.launch_flops_mixed_fp64(int(r["nsteps"].sum()), n, mech)
-            note = "fp64 pipe; credited fp64 part only (temperature solve, Gibbs, ln Kc, fp64 registers, control)"
+            note = "fp64 pipe; credited fp64 part only (temperature solve, Gibbs, hi/lo splits for ln Kc, fp64 registers, control)"
         if v == "hybrid":
             # the fused network kernel, timed alone on the surrogate leg's rows
             mk = sur["mlp_kernel"]
