@@ -65,10 +65,14 @@ typedef enum {
 } chem_cell_status;
 
 typedef enum {
-  CHEM_VARIANT_FP64 = 0,  /* every operation in fp64 */
+  CHEM_VARIANT_FP64 = 0,  /* every value in fp64 (reciprocals by Newton-Raphson refinement
+                             of the hardware approximation, within 2 ulp except in the
+                             temperature solve's step, 2^-40; that solve's stop test
+                             compares the fp32-rounded step and temperature) */
   CHEM_VARIANT_MIXED = 1  /* rates and RK stage derivatives in fp32; temperature solve,
-                             Gibbs/equilibrium terms, solution and error registers and
-                             step control in fp64 */
+                             Gibbs functions, solution and error registers and step
+                             control in fp64; ln(1/K_c) is the fp64 sum of the Gibbs
+                             terms rounded once to fp32 for the fp32 reverse rate */
 } chem_variant;
 
 /*
