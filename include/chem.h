@@ -441,29 +441,30 @@ int chem_surrogate_forward(chem_ctx *ctx, const float *d_X, int64_t B, float *d_
  * The paper has no counterpart.
  *
  * Some callers cannot allocate at that moment:
- *   - code that runs while a CUDA graph is being captured, where cudaMalloc is not
- *     allowed;
  *   - host solvers whose memory arena has already taken the GPU's memory and forbids
  *     allocations made outside it;
- *   - time-critical loops that cannot afford cudaMalloc's latency and implicit
- *     synchronisation.
+ *   - time-critical loops that cannot afford cudaMalloc's latency and the implicit
+ *     synchronisation that cudaMalloc and cudaFree bring.
  *
  * This entry point integrates exactly like chem_integrate_batched, with the same
- * arguments, results and errors. It calls no cudaMalloc, cudaFree or other allocating
- * routine. The queue scratch comes from a fixed array compiled into the library: about
- * 5 MiB, which every GPU that loads the library keeps until the process exits.
+ * arguments, argument checks, error codes and results. It calls no cudaMalloc, cudaFree
+ * or other allocating routine. The queue scratch comes from a fixed array compiled into
+ * the library: about 5 MiB, which every GPU that loads the library keeps until the
+ * process exits.
  *
  * Limits and rules:
  *   - At most 1,048,576 cells per call. Larger ncells returns CHEM_ERR_INVALID with a
  *     message, before anything is launched.
  *   - opt->use_graph is ignored: the launches go straight to the stream; opt->shape is
  *     honoured.
- *   - Set-up: the first call on each device looks up the array's device address, with
- *     that device current. Make that first call outside any stream capture.
- *   - Every call on a device shares the one array. Each call clears the parts that must
- *     start at zero, but two calls whose work overlaps on the GPU race on it, even from
- *     different contexts or streams. Order such calls on one stream, or synchronise
- *     between them.
+ *   - Set-up: every call looks up the array's device address in the current device's
+ *     context (so a device reset never leaves a stale address). The first call in a
+ *     context also loads the library's device code there: make that first call on each
+ *     device before any stream capture.
+ *   - Every call on a device shares the one array, and the array keeps the last call's
+ *     contents. Each call clears the parts that must start at zero, but two calls whose
+ *     work overlaps on the GPU race on it, even from different contexts or streams. Order
+ *     such calls on one stream, or synchronise between them.
  */
 int chem_integrate_batched_noalloc(chem_ctx *ctx, const chem_state *state, int64_t ncells,
                                    const chem_batch *batch, double rtol, double atol,

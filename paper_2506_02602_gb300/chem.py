@@ -218,6 +218,26 @@ def _check_f64_cuda(name, t, n=None):
         raise ChemError(ERR_INVALID, f"{name} has fewer than {n} cells")
 
 
+def _check_cells(n, rho, e, Y, T, h=None, status=None, nsteps=None, cost_hint=None):
+    """The state tensors of one call hold at least n cells, with the dtypes of chem.h:
+    rho, e, T (and h) float64 CUDA vectors, Y float64 [S, ld] planes with ld >= n and
+    contiguous rows, status / nsteps / cost_hint int32 CUDA vectors."""
+    import torch
+    if n < 0:
+        raise ChemError(ERR_INVALID, "ncells < 0")
+    for nm, t in (("rho", rho), ("e", e), ("T", T), ("h", h)):
+        if t is not None:
+            _check_f64_cuda(nm, t)
+            if t.numel() < n:
+                raise ChemError(ERR_INVALID, f"{nm} has {t.numel()} < {n} cells")
+    _check_f64_cuda("Y", Y)
+    if Y.dim() != 2 or Y.stride(1) != 1 or Y.shape[1] < n or Y.stride(0) < n:
+        raise ChemError(ERR_INVALID, "Y must be [S, ld] planes with contiguous rows and ld >= ncells")
+    for nm, t in (("status", status), ("nsteps", nsteps), ("cost_hint", cost_hint)):
+        if t is not None and (t.device.type != "cuda" or t.dtype != torch.int32 or t.numel() < n):
+            raise ChemError(ERR_INVALID, f"{nm} must be an int32 CUDA tensor of >= {n} cells")
+
+
 class Context:
     """A chem_ctx bound to one mechanism and precision variant."""
 
@@ -287,8 +307,7 @@ class Context:
         box_nsub (int32 [nb]) are CUDA tensors; the state tensors are as in integrate."""
         import torch
         n = rho.numel()
-        for nm, t in (("rho", rho), ("e", e), ("Y", Y), ("T", T)):
-            _check_f64_cuda(nm, t, n)
+        _check_cells(n, rho, e, Y, T, h, status, nsteps, cost_hint)
         if box_offset.dtype != torch.int64 or box_nsub.dtype != torch.int32 or box_dt.dtype != torch.float64:
             raise ChemError(ERR_INVALID, "box_offset int64, box_dt float64, box_nsub int32 expected")
         st = State(_ptr(rho).value, _ptr(e).value, _ptr(Y).value, Y.stride(0), _ptr(T).value,
@@ -335,16 +354,18 @@ class Context:
                                   order=ORDER_STIFFNESS, ctas_per_sm=0, cost_hint=None,
                                   stream=None, ncells=None, shape=0):
         """chem_integrate_batched_noalloc: the batched integration for callers that cannot
-        allocate device memory during the call (inside a graph capture, under a memory
-        arena that owns the GPU, in latency-bound loops).  The scratch is a fixed array in
-        the library: at most 1,048,576 cells per call, and calls that overlap on the GPU
-        race on it.  Arguments as integrate_batched; ncells overrides rho.numel()."""
+        allocate device memory during the call (under a memory arena that owns the GPU, in
+        latency-bound loops).  The scratch is a fixed array in the library: at most
+        1,048,576 cells per call, and calls that overlap on the GPU race on it.  Arguments
+        and checks as integrate_batched; ncells (at most the tensors' cell count)
+        overrides rho.numel()."""
         import torch
         fn = self.L.chem_integrate_batched_noalloc
         fn.restype = C.c_int
         fn.argtypes = [C.c_void_p, C.POINTER(State), C.c_int64, C.POINTER(Batch), C.c_double,
                        C.c_double, C.POINTER(BatchOptions), C.c_void_p, C.c_void_p]
-        n = rho.numel() if ncells is None else ncells
+        n = rho.numel() if ncells is None else int(ncells)
+        _check_cells(n, rho, e, Y, T, h, status, nsteps, cost_hint)
         if box_offset.dtype != torch.int64 or box_nsub.dtype != torch.int32 or box_dt.dtype != torch.float64:
             raise ChemError(ERR_INVALID, "box_offset int64, box_dt float64, box_nsub int32 expected")
         st = State(_ptr(rho).value, _ptr(e).value, _ptr(Y).value, Y.stride(0), _ptr(T).value,

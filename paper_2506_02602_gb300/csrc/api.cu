@@ -259,6 +259,31 @@ int check_step(chem_ctx *ctx, double dt, double rtol, double atol) {
 
 }  // namespace
 
+namespace chem {
+
+int check_batched_call(chem_ctx *ctx, const chem_state *state, int64_t ncells,
+                       const chem_batch *batch, double rtol, double atol,
+                       const chem_batch_options *opt, chem_batch_options *o) {
+  if (!ctx) return fail(nullptr, CHEM_ERR_INVALID, "ctx is NULL");
+  int rc = check_state(ctx, state, ncells);
+  if (rc) return rc;
+  rc = check_step(ctx, 1.0, rtol, atol);
+  if (rc) return rc;
+  if (ncells > INT32_MAX) return fail(ctx, CHEM_ERR_INVALID, "batched calls hold at most 2^31-1 cells");
+  *o = chem_batch_options{};
+  if (opt) *o = *opt;
+  if (o->order != CHEM_ORDER_STIFFNESS && o->order != CHEM_ORDER_NATURAL)
+    return fail(ctx, CHEM_ERR_INVALID, "unknown queue order %d", o->order);
+  if (o->shape < 0 || o->shape >= CHEM_BATCH_SHAPES || o->ctas_per_sm < 0)
+    return fail(ctx, CHEM_ERR_INVALID, "invalid batch options (shape %d, ctas_per_sm %d)", o->shape,
+                o->ctas_per_sm);
+  if (!batch || batch->nboxes < 1 || !batch->d_box_offset || !batch->d_box_dt || !batch->d_box_nsub)
+    return fail(ctx, CHEM_ERR_INVALID, "batch needs nboxes >= 1 and its three device arrays");
+  return CHEM_OK;
+}
+
+}  // namespace chem
+
 extern "C" {
 
 int chem_version(void) { return 10000; }
@@ -382,20 +407,9 @@ static int batch_scratch(chem_ctx *ctx, int64_t n, BatchScratch *out) {
 int chem_integrate_batched(chem_ctx *ctx, const chem_state *state, int64_t ncells,
                            const chem_batch *batch, double rtol, double atol,
                            const chem_batch_options *opt, void *stream, chem_stats *d_stats) {
-  if (!ctx) return fail(nullptr, CHEM_ERR_INVALID, "ctx is NULL");
-  int rc = check_state(ctx, state, ncells);
-  if (rc) return rc;
-  rc = check_step(ctx, 1.0, rtol, atol);
-  if (rc) return rc;
-  if (ncells > INT32_MAX) return fail(ctx, CHEM_ERR_INVALID, "batched calls hold at most 2^31-1 cells");
   chem_batch_options o{};
-  if (opt) o = *opt;
-  if (o.order != CHEM_ORDER_STIFFNESS && o.order != CHEM_ORDER_NATURAL)
-    return fail(ctx, CHEM_ERR_INVALID, "unknown queue order %d", o.order);
-  if (o.shape < 0 || o.shape >= CHEM_BATCH_SHAPES || o.ctas_per_sm < 0)
-    return fail(ctx, CHEM_ERR_INVALID, "invalid batch options (shape %d, ctas_per_sm %d)", o.shape, o.ctas_per_sm);
-  if (!batch || batch->nboxes < 1 || !batch->d_box_offset || !batch->d_box_dt || !batch->d_box_nsub)
-    return fail(ctx, CHEM_ERR_INVALID, "batch needs nboxes >= 1 and its three device arrays");
+  int rc = check_batched_call(ctx, state, ncells, batch, rtol, atol, opt, &o);
+  if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   if (ncells == 0) {
     if (d_stats) {

@@ -25,7 +25,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 #include <string>
 
 #include "cell.cuh"
@@ -336,39 +335,28 @@ cudaError_t launch_batched(int variant, const MechTables &mt, const BatchArgs &a
 // ------------------------------------------------------------------------------------
 // Allocation-free variant of chem_integrate_batched.
 //
-// Some callers cannot allocate device memory at the moment they integrate: code that
-// runs while a CUDA graph is being captured (cudaMalloc is not allowed there), host
-// solvers whose memory arena has already claimed the GPU's memory and forbids allocations
-// made behind its back, and time-critical loops that cannot afford cudaMalloc's latency
-// and implicit synchronisation.  For them the queue scratch of the batched path lives in
-// the fixed array below, which every GPU that loads this library keeps until the process
-// exits.  Only host code needs its device address, taken once per device with
-// cudaGetSymbolAddress: the array's name in host code is a stand-in, not an address a
-// kernel can use.
+// Some callers cannot allocate device memory at the moment they integrate: host solvers
+// whose memory arena has already claimed the GPU's memory and forbids allocations made
+// behind its back, and time-critical loops that cannot afford cudaMalloc's latency and
+// implicit synchronisation.  For them the queue scratch of the batched path lives in the
+// fixed array below, which every GPU that loads this library keeps until the process
+// exits.  Only host code needs its device address, taken with cudaGetSymbolAddress with
+// the caller's device current: the array's name in host code is a stand-in, not an
+// address a kernel can use.
 namespace chem {
 
 constexpr int64_t kNoAllocMaxCells = 1 << 20;  // 1,048,576 cells: 5 MiB + 512 B of scratch
 // layout: cursor at 0, bucket counts at 256, queue order at 512, buckets after the order
 static __device__ __align__(256) unsigned char g_noalloc_scratch[512 + kNoAllocMaxCells * 5];
 
-static std::mutex g_noalloc_mu;
-static void *g_noalloc_addr[256];  // device address of g_noalloc_scratch, per device ordinal
-
-// Device address of the fixed scratch on the current device (looked up once per device).
+// Device address of the fixed scratch in the current device's context.  It is looked up
+// on every call rather than cached: a device reset or a re-created primary context loads
+// the module again at another address, and a cached pointer would then be stale.  The
+// first lookup in a context loads the module (allocating nothing the caller sees); later
+// ones are a table lookup in the runtime.
 static cudaError_t noalloc_scratch(void **addr) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_noalloc_addr[dev] = p;
-  }
-  *addr = g_noalloc_addr[dev];
-  return cudaSuccess;
+  *addr = nullptr;
+  return cudaGetSymbolAddress(addr, g_noalloc_scratch);
 }
 
 }  // namespace chem
@@ -379,37 +367,19 @@ extern "C" int chem_integrate_batched_noalloc(chem_ctx *ctx, const chem_state *s
                                               const chem_batch_options *opt, void *stream,
                                               chem_stats *d_stats) {
   using namespace chem;
-  if (!ctx) return CHEM_ERR_INVALID;
-  std::string &err = chem_ctx_error(ctx);
-  auto bad = [&](const char *msg) {
-    err = msg;
-    return CHEM_ERR_INVALID;
-  };
-  if (!state) return bad("state is NULL");
-  if (ncells < 0) return bad("ncells < 0");
-  if (ncells > kNoAllocMaxCells)
-    return bad("chem_integrate_batched_noalloc holds at most 1048576 cells (fixed scratch); "
-               "split the batch or use chem_integrate_batched");
-  if (!(rtol > 0.0) || !std::isfinite(rtol)) return bad("rtol must be > 0");
-  if (!(atol >= 0.0) || !std::isfinite(atol)) return bad("atol must be >= 0");
+  // the same argument rules and messages as chem_integrate_batched, then the size limit
   chem_batch_options o{};
-  if (opt) o = *opt;
-  if (o.order != CHEM_ORDER_STIFFNESS && o.order != CHEM_ORDER_NATURAL) return bad("unknown queue order");
-  if (o.shape < 0 || o.shape >= CHEM_BATCH_SHAPES || o.ctas_per_sm < 0) return bad("invalid batch options");
-  if (!batch || batch->nboxes < 1 || !batch->d_box_offset || !batch->d_box_dt || !batch->d_box_nsub)
-    return bad("batch needs nboxes >= 1 and its three device arrays");
-  if (ncells > 0) {
-    if (!state->d_rho || !state->d_e || !state->d_Y || !state->d_T)
-      return bad("rho, e, Y and T are required");
-    if (state->ldY < ncells) return bad("ldY < ncells");
-    const uintptr_t a8 = reinterpret_cast<uintptr_t>(state->d_rho) | reinterpret_cast<uintptr_t>(state->d_e) |
-                         reinterpret_cast<uintptr_t>(state->d_Y) | reinterpret_cast<uintptr_t>(state->d_T) |
-                         reinterpret_cast<uintptr_t>(state->d_h);
-    if (a8 & 7u) return bad("state pointers must be 8-byte aligned");
+  int rc = check_batched_call(ctx, state, ncells, batch, rtol, atol, opt, &o);
+  if (rc) return rc;
+  std::string &err = chem_ctx_error(ctx);
+  if (ncells > kNoAllocMaxCells) {
+    err = "chem_integrate_batched_noalloc holds at most 1048576 cells (fixed scratch); got " +
+          std::to_string(ncells) + ": split the batch or use chem_integrate_batched";
+    return CHEM_ERR_INVALID;
   }
   void *base = nullptr;
   cudaError_t e = noalloc_scratch(&base);
-  if (e != cudaSuccess) {
+  if (e != cudaSuccess || !base) {
     err = std::string("looking up the fixed scratch: ") + cudaGetErrorString(e);
     return CHEM_ERR_CUDA;
   }

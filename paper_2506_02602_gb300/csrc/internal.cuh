@@ -75,6 +75,13 @@ int32_t chem_ctx_max_steps(const chem_ctx *ctx);
 void *&chem_ctx_sur(chem_ctx *ctx);
 void surrogate_destroy(void *sur);
 
+// Argument checks of chem_integrate_batched and chem_integrate_batched_noalloc (api.cu):
+// state, tolerances, batch arrays and options; on CHEM_OK *o holds the options with the
+// defaults applied (opt may be NULL).  The message of a failure is set on ctx.
+int check_batched_call(chem_ctx *ctx, const chem_state *state, int64_t ncells,
+                       const chem_batch *batch, double rtol, double atol,
+                       const chem_batch_options *opt, chem_batch_options *o);
+
 cudaError_t launch_batched(int variant, const MechTables &mt, const BatchArgs &a,
                            const StepParams &p, const BatchScratch &s, int order_mode,
                            int ctas_per_sm, int shape, cudaStream_t st);

@@ -1,12 +1,13 @@
 """The allocation-free batched entry point (chem_integrate_batched_noalloc).
 
-It serves callers that cannot allocate device memory during the call.  Examples are
-code inside a CUDA graph capture, a host solver whose memory arena owns the GPU, or a
-latency-bound loop.  Its queue scratch is a fixed array in the library, so its results
-must match the allocating entry point (chem_integrate_batched) on the same inputs.
-They are checked here within the FP64 parity tolerance, on two calls in a row, because
-each call reuses the array the previous one left behind.  Requests beyond the fixed
-maximum are rejected before any launch.
+It serves callers that cannot allocate device memory during the call: a host solver
+whose memory arena owns the GPU, or a latency-bound loop that cannot pay for
+cudaMalloc's synchronisation.  Its queue scratch is a fixed array in the library, so
+its results must match the allocating entry point (chem_integrate_batched) on the same
+inputs.  They are checked here within the FP64 parity tolerance, on two calls in a row,
+because each call reuses the array the previous one left behind.  Requests beyond the
+fixed maximum are rejected before any launch, and the binding rejects tensors that are
+too short for the requested cell count.
 
 This file is named to be collected last.
 """
@@ -69,13 +70,21 @@ def test_noalloc_rejects_more_cells_than_its_scratch():
     from paper_2506_02602_gb300 import build, chem
     build.build()
     ctx = chem.Context(M.build(0), "fp64")
-    x = torch.zeros(16, dtype=torch.float64, device="cuda")
-    Y = torch.zeros((9, 16), dtype=torch.float64, device="cuda")
-    off = torch.tensor([0, 16], dtype=torch.int64, device="cuda")
+    n = (1 << 20) + 1  # one cell beyond the fixed scratch; the tensors really hold n cells
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    Y = torch.zeros((9, n), dtype=torch.float64, device="cuda")
+    off = torch.tensor([0, n], dtype=torch.int64, device="cuda")
     dt = torch.tensor([1e-7], dtype=torch.float64, device="cuda")
     nsub = torch.tensor([1], dtype=torch.int32, device="cuda")
-    # the size check comes before any pointer is used or anything is launched
+    # the size check comes before anything is launched
     with pytest.raises(chem.ChemError) as ei:
-        ctx.integrate_batched_noalloc(x, x, Y, x, off, dt, nsub, ncells=(1 << 20) + 1)
+        ctx.integrate_batched_noalloc(x, x, Y, x, off, dt, nsub)
     assert ei.value.code == chem.ERR_INVALID and "1048576" in str(ei.value)
+    # a cell count beyond the tensors' own size never reaches the library
+    small = torch.zeros(16, dtype=torch.float64, device="cuda")
+    with pytest.raises(chem.ChemError) as ei:
+        ctx.integrate_batched_noalloc(small, small, Y[:, :16], small, off, dt, nsub, ncells=17)
+    assert ei.value.code == chem.ERR_INVALID
+    with pytest.raises(chem.ChemError):  # fp32 state is refused as in integrate_batched
+        ctx.integrate_batched_noalloc(small.float(), small, Y[:, :16], small, off, dt, nsub)
     ctx.close()
