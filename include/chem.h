@@ -423,6 +423,49 @@ int chem_surrogate_grad(chem_ctx *ctx, const float *d_X, const float *d_T, int64
                         float *h_grad, float *h_loss, void *stream);
 
 /*
+ * chem_surrogate_grad keeping every intermediate of the pass, for layer-by-layer checks
+ * of the GEMMs and elementwise kernels (not a call of the paper's method).  With
+ * H_-1 = bf16(X), hidden layers l = 0, 1, 2 and the output layer 3 (W_l [N x K] of the
+ * flat parameters, G_l the loss gradient with respect to layer l's output), the device
+ * outputs (each nullable) are:
+ *   d_Z  fp32 [3][B][256]: Z_l = H_{l-1} W_l^T + b_l (FP32 accumulation);
+ *   d_H  bf16 bit patterns [3][B][256]: H_l = bf16(GELU(Z_l));
+ *   d_G  bf16 bit patterns [4][B][256]: G_3 = bf16(2 (Y - T) / (9 B)) over the 9 live
+ *        outputs as B x 16 (stride 16) at the start of slab 3; G_l = bf16(dH_l GELU'(Z_l))
+ *        for l < 3;
+ *   d_dH fp32 [3][B][256]: dH_l = G_{l+1} W_{l+1}, the gradient with respect to H_l.
+ * The weight gradients (h_grad) are G_l^T H_{l-1} and the bias gradients the column sums
+ * of G_l.  Other arguments, results and errors as chem_surrogate_grad.  Synchronous.
+ */
+int chem_surrogate_trace(chem_ctx *ctx, const float *d_X, const float *d_T, int64_t B, float *d_Y,
+                         float *d_Z, uint16_t *d_H, uint16_t *d_G, float *d_dH, float *h_grad,
+                         float *h_loss, void *stream);
+
+/*
+ * One Adam step of the network's parameters with a given gradient, for checks of the
+ * optimizer kernel that training runs (not a call of the paper's method): h_grad (host,
+ * flat like the parameters, n = chem_surrogate_param_count()), learning rate lr >= 0,
+ * b1 = 0.9, b2 = 0.999, eps = 1e-8 (Kingma & Ba 2015, with bias correction; the step
+ * count starts at 1 after chem_surrogate_params uploads parameters and advances by one
+ * per call).  The bf16 copies of the weights are refreshed.  Synchronous.  Errors:
+ * wrong n, NULL h_grad or invalid lr -> CHEM_ERR_INVALID.
+ */
+int chem_surrogate_adam(chem_ctx *ctx, const float *h_grad, int64_t n, float lr);
+
+/*
+ * The fp64 element projection of chem_surrogate_infer alone, for checks (not a call of
+ * the paper's method): for n cells (device planes with stride ldY), d_Yout receives the
+ * weighted least-squares projection of the prediction d_Yp onto the element (H, O, N)
+ * mass fractions of d_Y0: Y'' = Y' - W E^T (E W E^T)^-1 E (Y' - Y0), W = diag(max(Y'_k,
+ * 1e-12)), E the element mass fraction per unit species mass fraction.  A cell whose
+ * 3x3 system is singular gets d_Yp unchanged.  Needs no trained network.  Asynchronous
+ * on stream.  Errors: n < 0, NULL arrays with n > 0, ldY < n -> CHEM_ERR_INVALID.
+ */
+int chem_surrogate_project(chem_ctx *ctx, int64_t n, const double *d_Y0, const double *d_Yp,
+                           int64_t ldY, double *d_Yout, void *stream);
+
+/*
+ * The network alone on B rows/*
  * The network alone on B rows (a check of the kernels; not a call of the paper's
  * method): d_X [B x 16] normalised features (fp32 device), d_Y [B x 16] outputs (fp32
  * device, out; columns 9..15 zero).  impl: 0 = the kernel inference uses (tcgen05
@@ -484,6 +527,19 @@ int chem_integrate_batched_noalloc(chem_ctx *ctx, const chem_state *state, int64
  * CHEM_ERR_INVALID.  Asynchronous on stream.
  */
 int chem_diag_math(int op, int64_t n, const double *d_x, double *d_y, void *stream);
+
+/*
+ * Diagnostic: a throughput probe of the FMA pipe the integration kernels are bound by
+ * (the denominator of their compute roofline; the paper has no counterpart).  op 0:
+ * fp64, 1: fp32.  Launches blocks x threads threads; each runs iters rounds of 32 FMAs
+ * (8 independent dependent chains, 4 FMAs each per round), i.e. 64 flops per round, and
+ * writes one value to d_sink (device, blocks * threads elements of 8 bytes for op 0, 4
+ * for op 1).  The caller times the launch (CUDA events) to get flop/s.  Errors: unknown
+ * op, blocks < 1, threads not a multiple of 32 in [32, 1024], iters < 1 or NULL d_sink
+ * -> CHEM_ERR_INVALID.  Asynchronous on stream.
+ */
+int chem_diag_fma_peak(int op, int32_t blocks, int32_t threads, int64_t iters, void *d_sink,
+                       void *stream);
 
 /* Library version, as major * 10000 + minor * 100 + patch. */
 int chem_version(void);

@@ -131,6 +131,7 @@ def load() -> C.CDLL:
         "chem_integrate": (C.c_int, [vp, C.POINTER(State), i64, dbl, dbl, dbl, vp, vp]),
         "chem_integrate_host": (C.c_int, [vp, i64, vp, vp, vp, i64, vp, vp, vp, vp, dbl, dbl, dbl, vp]),
         "chem_diag_math": (C.c_int, [C.c_int, i64, vp, vp, vp]),
+        "chem_diag_fma_peak": (C.c_int, [C.c_int, C.c_int32, C.c_int32, i64, vp, vp]),
         "chem_integrate_batched": (C.c_int, [vp, C.POINTER(State), i64, C.POINTER(Batch), dbl, dbl,
                                              C.POINTER(BatchOptions), vp, vp]),
         "chem_batch_shape_info": (C.c_int, [vp, C.c_int32, vp, vp, vp]),
@@ -146,6 +147,9 @@ def load() -> C.CDLL:
         "chem_surrogate_params": (C.c_int, [vp, vp, vp, i64]),
         "chem_surrogate_grad": (C.c_int, [vp, vp, vp, i64, vp, vp, vp, vp]),
         "chem_surrogate_forward": (C.c_int, [vp, vp, i64, vp, C.c_int32, vp, vp]),
+        "chem_surrogate_adam": (C.c_int, [vp, vp, i64, C.c_float]),
+        "chem_surrogate_trace": (C.c_int, [vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "chem_surrogate_project": (C.c_int, [vp, i64, vp, vp, i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -167,6 +171,27 @@ def diag_math(op: int, x, stream=None):
     if rc != OK:
         raise ChemError(rc, "chem_diag_math failed")
     return y
+
+
+def fma_peak(op: int, blocks: int, threads: int, iters: int, reps: int = 5, stream=None):
+    """chem_diag_fma_peak timed with CUDA events: returns (best GFLOP/s over reps launches,
+    flops per launch).  op 0: fp64, 1: fp32."""
+    import torch
+    sink = torch.empty(blocks * threads, dtype=torch.float64 if op == 0 else torch.float32, device="cuda")
+    st = torch.cuda.current_stream() if stream is None else stream
+    flops = float(blocks) * threads * iters * 64
+    best = float("inf")
+    for r in range(reps + 1):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        rc = load().chem_diag_fma_peak(op, blocks, threads, iters, _ptr(sink), _stream(st))
+        b.record(st)
+        if rc != OK:
+            raise ChemError(rc, "chem_diag_fma_peak failed")
+        torch.cuda.synchronize()
+        if r:  # the first launch warms up
+            best = min(best, a.elapsed_time(b) * 1e-3)
+    return flops / best / 1e9, flops
 
 
 def make_mechanism(m: dict) -> Mechanism:
@@ -437,6 +462,47 @@ class Context:
                                                g.ctypes.data_as(C.c_void_p), loss.ctypes.data_as(C.c_void_p),
                                                _stream(stream)))
         return Y, g, float(loss[0])
+
+    def surrogate_trace(self, X, T, stream=None):
+        """chem_surrogate_trace on fp32 CUDA tensors X, T [B, 16]: returns a dict of
+        numpy arrays Y [B, 16], Z [3, B, 256], H [3, B, 256] (bf16 values as float32),
+        G [4, B, 256] (layer 3 in G3 [B, 16]), dH [3, B, 256], grad (flat) and loss."""
+        import torch
+        B = X.shape[0]
+        dev = X.device
+        Y = torch.empty((B, 16), dtype=torch.float32, device=dev)
+        Z = torch.empty((3, B, 256), dtype=torch.float32, device=dev)
+        H = torch.empty((3, B, 256), dtype=torch.bfloat16, device=dev)
+        G = torch.zeros((4, B, 256), dtype=torch.bfloat16, device=dev)
+        dH = torch.empty((3, B, 256), dtype=torch.float32, device=dev)
+        g = np.zeros(self.L.chem_surrogate_param_count(), dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        self._raise(self.L.chem_surrogate_trace(self.h, _ptr(X), _ptr(T), B, _ptr(Y), _ptr(Z), _ptr(H), _ptr(G),
+                                                _ptr(dH), g.ctypes.data_as(C.c_void_p),
+                                                loss.ctypes.data_as(C.c_void_p), _stream(stream)))
+        Gf = G.float()
+        return {"Y": Y.cpu().numpy(), "Z": Z.cpu().numpy(), "H": H.float().cpu().numpy(),
+                "G": Gf[:3].cpu().numpy(), "G3": Gf[3].reshape(-1)[: B * 16].reshape(B, 16).cpu().numpy(),
+                "dH": dH.cpu().numpy(), "grad": g, "loss": float(loss[0])}
+
+    def surrogate_adam(self, grad, lr):
+        """chem_surrogate_adam: one Adam step of the parameters with the flat gradient
+        `grad` (numpy fp32) and learning rate lr."""
+        g = np.ascontiguousarray(grad, dtype=np.float32)
+        self._raise(self.L.chem_surrogate_adam(self.h, g.ctypes.data_as(C.c_void_p), g.size, float(lr)))
+
+    def surrogate_project(self, Y0, Yp, out=None, stream=None):
+        """chem_surrogate_project on float64 CUDA planes Y0, Yp [S, ld]: the element
+        projection of Yp onto the element mass fractions of Y0 (returns out)."""
+        import torch
+        _check_f64_cuda("Y0", Y0)
+        _check_f64_cuda("Yp", Yp)
+        if Y0.shape != Yp.shape or Y0.stride() != Yp.stride() or Y0.stride(1) != 1:
+            raise ChemError(ERR_INVALID, "Y0 and Yp must be planes of one shape and stride")
+        out = torch.empty_like(Yp) if out is None else out
+        self._raise(self.L.chem_surrogate_project(self.h, Yp.shape[1], _ptr(Y0), _ptr(Yp), Yp.stride(0),
+                                                  _ptr(out), _stream(stream)))
+        return out
 
     FWD_TC, FWD_FUSED, FWD_LAYERS = 0, 1, 2
 

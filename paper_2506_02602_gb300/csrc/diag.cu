@@ -1,5 +1,7 @@
-// diag.cu -- chem_diag_math: the kernels' device math routines on caller arrays, for
-// accuracy tests against the CUDA library and the IEEE-754 definitions.
+// diag.cu -- diagnostics: chem_diag_math (the kernels' device math routines on caller
+// arrays, for accuracy tests against the CUDA library and the IEEE-754 definitions) and
+// chem_diag_fma_peak (an FMA-throughput probe of the fp64 and fp32 pipes, the
+// denominators of the integrators' compute roofline).
 #include <cuda_runtime.h>
 
 #include "fastmath.cuh"
@@ -30,7 +32,43 @@ __global__ void k_diag_math(int op, int64_t n, const double *__restrict__ x, dou
   y[i] = r;
 }
 
+// FMA-pipe throughput probe: 8 independent dependent chains per thread, x <- x a + b,
+// iters rounds; one store per thread keeps the chains live.  2 flops per FMA.
+template <typename R>
+__global__ void k_fma_peak(int64_t iters, R a, R b, R *__restrict__ sink) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  R x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = (R)(threadIdx.x & 15) + (R)j;
+#pragma unroll 1
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[j] = fma(x[j], a, b);
+  }
+  R s = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += x[j];
+  sink[t] = s;
+}
+
 }  // namespace chem
+
+extern "C" int chem_diag_fma_peak(int op, int32_t blocks, int32_t threads, int64_t iters,
+                                  void *d_sink, void *stream) {
+  if ((op != 0 && op != 1) || blocks < 1 || threads < 32 || threads > 1024 || (threads & 31) ||
+      iters < 1 || !d_sink)
+    return CHEM_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (op == 0)
+    chem::k_fma_peak<double><<<(unsigned)blocks, threads, 0, s>>>(iters, 0.9999999, 1e-7,
+                                                                  static_cast<double *>(d_sink));
+  else
+    chem::k_fma_peak<float><<<(unsigned)blocks, threads, 0, s>>>(iters, 0.9999f, 1e-4f,
+                                                                 static_cast<float *>(d_sink));
+  return cudaGetLastError() == cudaSuccess ? CHEM_OK : CHEM_ERR_CUDA;
+}
 
 extern "C" int chem_diag_math(int op, int64_t n, const double *d_x, double *d_y, void *stream) {
   if (op < 0 || op > 10 || n < 0) return CHEM_ERR_INVALID;

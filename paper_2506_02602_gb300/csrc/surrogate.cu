@@ -243,15 +243,37 @@ struct TrainBufs {
   }
 };
 
+// Optional copies of a pass's intermediates (chem_surrogate_trace; every field nullable).
+struct Trace {
+  float *Z;                // [3][B][256] hidden pre-activations
+  __nv_bfloat16 *H;        // [3][B][256] hidden activations
+  __nv_bfloat16 *G;        // [4][B][256] output gradient per layer (layer 3: B x 16, stride 16)
+  float *dH;               // [3][B][256] gradient w.r.t. hidden activation l
+};
+
+static cudaError_t trace_copy(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+  return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st) : cudaSuccess;
+}
+
 // Forward with saved activations, MSE over the 9 outputs, backward into s->grad.
 // X: normalised features [B x 16] (fp32, also converted to bf16), T: normalised targets.
-static cudaError_t forward_backward(Surrogate *s, TrainBufs &b, int64_t B, cudaStream_t st) {
+// tr (nullable) receives copies of the intermediates.
+static cudaError_t forward_backward(Surrogate *s, TrainBufs &b, int64_t B, cudaStream_t st,
+                                    const Trace *tr = nullptr) {
   SCHK(launch_to_bf16(B * kSurIn, b.Xb, b.Xbf, st));
   SCHK(layer_forward(s, 0, B, b.Xbf, b.Z[0], b.H[0], nullptr, st));
   SCHK(layer_forward(s, 1, B, b.H[0], b.Z[1], b.H[1], nullptr, st));
   SCHK(layer_forward(s, 2, B, b.H[1], b.Z[2], b.H[2], nullptr, st));
   SCHK(layer_forward(s, 3, B, b.H[2], nullptr, nullptr, b.Y, st));
   SCHK(launch_mse(B, NSP, kSurOut, b.Y, b.Tb, kSurOut, b.dY, kSurOut, b.loss, st));
+  const size_t slab = (size_t)B * kSurHidden;
+  if (tr) {
+    for (int l = 0; l < 3; ++l) {
+      SCHK(trace_copy(tr->Z ? tr->Z + l * slab : nullptr, b.Z[l], slab * sizeof(float), st));
+      SCHK(trace_copy(tr->H ? tr->H + l * slab : nullptr, b.H[l], slab * sizeof(__nv_bfloat16), st));
+    }
+    SCHK(trace_copy(tr->G ? tr->G + 3 * slab : nullptr, b.dY, (size_t)B * kSurOut * sizeof(__nv_bfloat16), st));
+  }
   // layer l: input Hin [B x K], output gradient G [B x N] (bf16)
   const __nv_bfloat16 *Hin[kSurLayers] = {b.Xbf, b.H[0], b.H[1], b.H[2]};
   const __nv_bfloat16 *G = b.dY;
@@ -281,6 +303,10 @@ static cudaError_t forward_backward(Surrogate *s, TrainBufs &b, int64_t B, cudaS
     SCHK(launch_gemm(gx, st));
     // G for layer l-1: dZ = dHin * GELU'(Z_{l-1})
     SCHK(launch_gelu_backward(B, K, b.dH, K, b.Z[l - 1], K, b.dZ, K, st));
+    if (tr) {
+      SCHK(trace_copy(tr->dH ? tr->dH + (l - 1) * slab : nullptr, b.dH, slab * sizeof(float), st));
+      SCHK(trace_copy(tr->G ? tr->G + (l - 1) * slab : nullptr, b.dZ, slab * sizeof(__nv_bfloat16), st));
+    }
     G = b.dZ;
   }
   return cudaSuccess;
@@ -430,8 +456,8 @@ int chem_surrogate_params(chem_ctx *ctx, float *h_out, const float *h_in, int64_
   return CHEM_OK;
 }
 
-int chem_surrogate_grad(chem_ctx *ctx, const float *d_X, const float *d_T, int64_t B, float *d_Y,
-                        float *h_grad, float *h_loss, void *stream) {
+static int surrogate_pass(chem_ctx *ctx, const float *d_X, const float *d_T, int64_t B, float *d_Y,
+                          float *h_grad, float *h_loss, void *stream, const Trace *tr) {
   if (!ctx) return CHEM_ERR_INVALID;
   if (B <= 0 || !d_X || !d_T) return sur_fail(ctx, CHEM_ERR_INVALID, "B > 0, X and T required");
   cudaError_t e;
@@ -443,7 +469,7 @@ int chem_surrogate_grad(chem_ctx *ctx, const float *d_X, const float *d_T, int64
   if (e == cudaSuccess) e = cudaMemcpyAsync(b.Xb, d_X, B * kSurIn * sizeof(float), cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b.Tb, d_T, B * kSurOut * sizeof(float), cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b.loss, 0, sizeof(float), st);
-  if (e == cudaSuccess) e = forward_backward(s, b, B, st);
+  if (e == cudaSuccess) e = forward_backward(s, b, B, st, tr);
   if (e == cudaSuccess && d_Y) e = cudaMemcpyAsync(d_Y, b.Y, B * kSurOut * sizeof(float), cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess && h_grad)
     e = cudaMemcpyAsync(h_grad, s->grad, (size_t)kSurParams * sizeof(float), cudaMemcpyDeviceToHost, st);
@@ -451,6 +477,49 @@ int chem_surrogate_grad(chem_ctx *ctx, const float *d_X, const float *d_T, int64
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   b.release();
   return e == cudaSuccess ? CHEM_OK : sur_cuda(ctx, e, "surrogate forward/backward");
+}
+
+int chem_surrogate_grad(chem_ctx *ctx, const float *d_X, const float *d_T, int64_t B, float *d_Y,
+                        float *h_grad, float *h_loss, void *stream) {
+  return surrogate_pass(ctx, d_X, d_T, B, d_Y, h_grad, h_loss, stream, nullptr);
+}
+
+int chem_surrogate_trace(chem_ctx *ctx, const float *d_X, const float *d_T, int64_t B, float *d_Y,
+                         float *d_Z, uint16_t *d_H, uint16_t *d_G, float *d_dH, float *h_grad,
+                         float *h_loss, void *stream) {
+  const Trace tr{d_Z, reinterpret_cast<__nv_bfloat16 *>(d_H), reinterpret_cast<__nv_bfloat16 *>(d_G), d_dH};
+  return surrogate_pass(ctx, d_X, d_T, B, d_Y, h_grad, h_loss, stream, &tr);
+}
+
+int chem_surrogate_adam(chem_ctx *ctx, const float *h_grad, int64_t n, float lr) {
+  if (!ctx) return CHEM_ERR_INVALID;
+  if (n != kSurParams || !h_grad) return sur_fail(ctx, CHEM_ERR_INVALID, "n must equal the parameter count");
+  if (!(lr >= 0.0f) || !std::isfinite(lr)) return sur_fail(ctx, CHEM_ERR_INVALID, "lr must be >= 0");
+  cudaError_t e;
+  Surrogate *s = ensure_surrogate(ctx, &e);
+  if (!s) return sur_cuda(ctx, e, "allocating the surrogate");
+  e = cudaMemcpyAsync(s->grad, h_grad, (size_t)kSurParams * sizeof(float), cudaMemcpyHostToDevice, 0);
+  if (e == cudaSuccess) e = adam_all(s, lr, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+  return e == cudaSuccess ? CHEM_OK : sur_cuda(ctx, e, "Adam step");
+}
+
+int chem_surrogate_project(chem_ctx *ctx, int64_t n, const double *d_Y0, const double *d_Yp,
+                           int64_t ldY, double *d_Yout, void *stream) {
+  if (!ctx) return CHEM_ERR_INVALID;
+  if (n < 0) return sur_fail(ctx, CHEM_ERR_INVALID, "n < 0");
+  if (n == 0) return CHEM_OK;
+  if (!d_Y0 || !d_Yp || !d_Yout) return sur_fail(ctx, CHEM_ERR_INVALID, "Y0, Yp and Yout are required");
+  if (ldY < n) return sur_fail(ctx, CHEM_ERR_INVALID, "ldY < n");
+  const MechTables &mt = chem_ctx_tables(ctx);
+  SurrogateConsts c{};
+  for (int el = 0; el < 3; ++el)
+    for (int k = 0; k < NSP; ++k) {
+      c.E[el][k] = mt.Emat[el][k];
+      c.emask[el] |= (mt.Emat[el][k] != 0.0) << k;
+    }
+  const cudaError_t e = launch_project_check(c, n, d_Y0, d_Yp, ldY, d_Yout, (cudaStream_t)stream);
+  return e == cudaSuccess ? CHEM_OK : sur_cuda(ctx, e, "projection");
 }
 
 int chem_surrogate_forward(chem_ctx *ctx, const float *d_X, int64_t B, float *d_Y, int32_t impl,

@@ -85,6 +85,10 @@ cudaError_t launch_pack_weights(const __nv_bfloat16 *const (&W)[kSurLayers], uns
 size_t packed_weight_bytes();
 cudaError_t launch_mlp_tc(int64_t n, const float *X, const float *norm, const unsigned char *Wpk,
                           const float *const (&b)[kSurLayers], float *O, int *err, cudaStream_t s);
+// The fp64 element projection of the inference epilogue alone (only sc.E and sc.emask are
+// read): Yout = projection of Yp onto the element mass fractions of Y0 (planes, stride ld).
+cudaError_t launch_project_check(const SurrogateConsts &sc, int64_t n, const double *Y0,
+                                 const double *Yp, int64_t ld, double *Yout, cudaStream_t s);
 // box_off = {0, n}, box_dt = {dt}, box_nsub = {1}: the fallback's one-box batch.
 cudaError_t launch_one_box(int64_t *box_off, double *box_dt, int32_t *box_nsub, int64_t n, double dt,
                            cudaStream_t s);

@@ -222,6 +222,86 @@ __device__ __noinline__ bool posterior_error(const MechTables &mt, const double 
 // (z-scored BC increments), the raw features X (un-normalised: T, ln p, log10 dt,
 // BC(Y0)) and the state; writes accepted cells (Y'', T'', status OK, nsteps 0) and
 // appends rejected ones to the fallback list.
+// Weighted least-squares projection of the prediction y1 onto the element (H, O, N) mass
+// fractions of y0: Y'' = Y' - W E^T (E W E^T)^-1 r with W = diag(max(Y'_k, 1e-12)) and
+// r = E (Y' - Y0), in fp64 (terms with a zero element fraction skipped: uniform branches
+// on the masks).  rn and zn receive |r|^2 and |E Y0|^2 of the raw prediction (the
+// residual gate's inputs).  Returns false, with y1 unchanged, when the 3x3 system is
+// singular or not finite.
+__device__ __forceinline__ bool project_elements(const SurrogateConsts &sc, const double (&y0)[NSP],
+                                                 double (&y1)[NSP], double &rn, double &zn) {
+  double z0[3] = {0.0, 0.0, 0.0}, r[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int el = 0; el < 3; ++el)
+#pragma unroll
+    for (int k = 0; k < NSP; ++k)
+      if ((sc.emask[el] >> k) & 1) {
+        z0[el] = fma(sc.E[el][k], y0[k], z0[el]);
+        r[el] = fma(sc.E[el][k], y1[k] - y0[k], r[el]);
+      }
+  rn = 0.0;
+  zn = 0.0;
+#pragma unroll
+  for (int el = 0; el < 3; ++el) {
+    rn = fma(r[el], r[el], rn);
+    zn = fma(z0[el], z0[el], zn);
+  }
+  double w[NSP], M[3][3];
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) w[k] = max_pos(y1[k], 1e-12);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = a; b < 3; ++b) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < NSP; ++k)
+        if (((sc.emask[a] & sc.emask[b]) >> k) & 1) s = fma(sc.E[a][k] * w[k], sc.E[b][k], s);
+      M[a][b] = s;
+      M[b][a] = s;
+    }
+  // 3x3 solve by Cramer's rule (M is symmetric positive definite for the H, O, N rows)
+  const double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                     M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                     M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+  if (!(det != 0.0 && isfinite(det))) return false;
+  const double id = rcp2(det);
+  double lamv[3];
+  lamv[0] = (r[0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (r[1] * M[2][2] - M[1][2] * r[2]) +
+             M[0][2] * (r[1] * M[2][1] - M[1][1] * r[2])) * id;
+  lamv[1] = (M[0][0] * (r[1] * M[2][2] - M[1][2] * r[2]) - r[0] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+             M[0][2] * (M[1][0] * r[2] - r[1] * M[2][0])) * id;
+  lamv[2] = (M[0][0] * (M[1][1] * r[2] - r[1] * M[2][1]) - M[0][1] * (M[1][0] * r[2] - r[1] * M[2][0]) +
+             r[0] * (M[1][0] * M[2][1] - M[1][1] * M[2][0])) * id;
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) {
+    double corr = 0.0;
+#pragma unroll
+    for (int el = 0; el < 3; ++el)
+      if ((sc.emask[el] >> k) & 1) corr = fma(sc.E[el][k], lamv[el], corr);
+    y1[k] = fma(-w[k], corr, y1[k]);
+  }
+  return true;
+}
+
+// The projection alone on given predictions (a check entry; see project_elements).
+__global__ void k_project_check(const __grid_constant__ SurrogateConsts sc, int64_t n,
+                                const double *__restrict__ Y0, const double *__restrict__ Yp,
+                                int64_t ld, double *__restrict__ Yout) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double y0[NSP], y1[NSP];
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) {
+    y0[k] = Y0[k * ld + i];
+    y1[k] = Yp[k * ld + i];
+  }
+  double rn, zn;
+  project_elements(sc, y0, y1, rn, zn);
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) Yout[k * ld + i] = y1[k];
+}
+
 // 4 blocks of 128 per SM (16 warps): the register cap of 128 costs 4 bytes of spill
 // stores, against 8 warps at the uncapped 255 registers.
 template <int V>
@@ -256,66 +336,14 @@ __global__ void __launch_bounds__(128, 4)
     const float d = fmaf(o[k], sc.tstd[k], sc.tmean[k]) * unscale;
     y1[k] = boxcox_step(y0[k], x[3 + k], d, (float)sc.lam);
   }
-  // element mass fractions before projection and the residual (terms with a zero
-  // element fraction skipped: uniform branches on the masks)
-  double z0[3] = {0.0, 0.0, 0.0}, r[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-  for (int el = 0; el < 3; ++el)
-#pragma unroll
-    for (int k = 0; k < NSP; ++k)
-      if ((sc.emask[el] >> k) & 1) {
-        z0[el] = fma(sc.E[el][k], y0[k], z0[el]);
-        r[el] = fma(sc.E[el][k], y1[k] - y0[k], r[el]);
-      }
   double rn = 0.0, zn = 0.0;
-#pragma unroll
-  for (int el = 0; el < 3; ++el) {
-    rn = fma(r[el], r[el], rn);
-    zn = fma(z0[el], z0[el], zn);
-  }
+  const bool solved = project_elements(sc, y0, y1, rn, zn);
   if (!reason && !(rn <= (double)sc.resid_max * sc.resid_max * zn)) reason = kFbResidual;
-  // weighted least-squares projection onto E Y = E Y0: Y'' = Y' - W E^T (E W E^T)^-1 r
-  double w[NSP], M[3][3];
-#pragma unroll
-  for (int k = 0; k < NSP; ++k) w[k] = max_pos(y1[k], 1e-12);
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = a; b < 3; ++b) {
-      double s = 0.0;
-#pragma unroll
-      for (int k = 0; k < NSP; ++k)
-        if (((sc.emask[a] & sc.emask[b]) >> k) & 1) s = fma(sc.E[a][k] * w[k], sc.E[b][k], s);
-      M[a][b] = s;
-      M[b][a] = s;
-    }
-  // 3x3 solve by Cramer's rule (M is symmetric positive definite for the H, O, N rows)
-  const double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
-                     M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
-                     M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
-  double lamv[3] = {0.0, 0.0, 0.0};
-  if (det != 0.0 && isfinite(det)) {
-    const double id = rcp2(det);
-    lamv[0] = (r[0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (r[1] * M[2][2] - M[1][2] * r[2]) +
-               M[0][2] * (r[1] * M[2][1] - M[1][1] * r[2])) * id;
-    lamv[1] = (M[0][0] * (r[1] * M[2][2] - M[1][2] * r[2]) - r[0] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
-               M[0][2] * (M[1][0] * r[2] - r[1] * M[2][0])) * id;
-    lamv[2] = (M[0][0] * (M[1][1] * r[2] - r[1] * M[2][1]) - M[0][1] * (M[1][0] * r[2] - r[1] * M[2][0]) +
-               r[0] * (M[1][0] * M[2][1] - M[1][1] * M[2][0])) * id;
-  } else if (!reason) {
-    reason = kFbResidual;
-  }
-  // the correction, and the negativity test on the fp32-rounded result (a NaN fails it)
+  if (!reason && !solved) reason = kFbResidual;
+  // the negativity test on the fp32-rounded result (a NaN fails it)
   bool neg = false;
 #pragma unroll
-  for (int k = 0; k < NSP; ++k) {
-    double corr = 0.0;
-#pragma unroll
-    for (int el = 0; el < 3; ++el)
-      if ((sc.emask[el] >> k) & 1) corr = fma(sc.E[el][k], lamv[el], corr);
-    y1[k] = fma(-w[k], corr, y1[k]);
-    neg |= !(d2f(y1[k]) >= -sc.neg_tol);
-  }
+  for (int k = 0; k < NSP; ++k) neg |= !(d2f(y1[k]) >= -sc.neg_tol);
   if (!reason && neg) reason = kFbNegative;
   // temperature of the projected state (fp64 Newton from the input temperature)
   const double eR = e[i] * (1.0 / R_U);
@@ -417,6 +445,13 @@ cudaError_t launch_surrogate_finish(int variant, const MechTables &mt, const Sur
 cudaError_t launch_one_box(int64_t *box_off, double *box_dt, int32_t *box_nsub, int64_t n, double dt,
                            cudaStream_t s) {
   k_one_box<<<1, 32, 0, s>>>(box_off, box_dt, box_nsub, n, dt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project_check(const SurrogateConsts &sc, int64_t n, const double *Y0,
+                                 const double *Yp, int64_t ld, double *Yout, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_project_check<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sc, n, Y0, Yp, ld, Yout);
   return cudaGetLastError();
 }
 

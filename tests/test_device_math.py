@@ -128,3 +128,16 @@ def test_hilo_split(lib):
     s32 = (((h[:, 0].astype(np.float32) - h[:, 1].astype(np.float32)) + h[:, 2].astype(np.float32))
            - h[:, 3].astype(np.float32))
     assert np.array_equal(s32.astype(np.float64), h[:, 0] - h[:, 1] + h[:, 2] - h[:, 3])
+
+
+def test_fma_probe_is_plausible(lib):
+    """chem_diag_fma_peak (the roofline denominators' probe): the fp64 rate is below the
+    unit-count peak (152 SMs x 2 DFMA lanes x 2 flops x 2.07 GHz, a probe that did no work
+    would exceed it) and above half of it; fp32 runs tens of times faster than fp64."""
+    from paper_2506_02602_gb300 import roofline
+    f64, _ = lib.fma_peak(0, 152 * 8, 256, 200)
+    f32, _ = lib.fma_peak(1, 152 * 8, 256, 4000)
+    assert 0.5 * roofline.FP64_PEAK_GFLOPS < f64 <= 1.02 * roofline.FP64_PEAK_GFLOPS, f64
+    assert f32 > 20 * f64, (f32, f64)
+    with pytest.raises(lib.ChemError):
+        lib.fma_peak(2, 1, 32, 1)
