@@ -93,6 +93,13 @@ def lib():
             "oracle_chem_fixed": (C.c_int32, [mp, C.c_double, C.c_double, dp, C.c_double,
                                               C.c_double, C.c_int32, dp]),
             "oracle_struct_size": (C.c_int32, []),
+            "oracle_butcher": (None, [C.c_int32, ip, dp, dp, dp, dp]),
+            "oracle_linear_step_scheme": (None, [C.c_int32, C.c_int32, dp, C.c_double, dp, dp]),
+            "oracle_quadratic_fixed_scheme": (C.c_double, [C.c_int32, C.c_double, C.c_double,
+                                                           C.c_int32, C.c_int32]),
+            "oracle_integrate_scheme": (C.c_int32, [C.c_int32, mp, C.c_int64, dp, dp, dp, C.c_int64, dp,
+                                                    C.c_double, C.c_double, C.c_double, dp, C.c_int32,
+                                                    ip, ip, ip, dp, dp, C.c_int32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -226,9 +233,11 @@ class Oracle:
 
     # integrator -----------------------------------------------------------
     def integrate(self, rho, e, Y, T, dt, rtol=1e-6, atol=1e-10, h0=None, max_steps=100000,
-                  nthreads=0):
+                  nthreads=0, scheme=0):
         """Integrate every cell over dt.  Returns a dict with Y [S, n], T, status,
-        nsteps (attempted), naccept, margin (min |err - 1|) and h (next step)."""
+        nsteps (attempted), naccept, margin (min |err - 1|) and h (next step).
+        scheme: 0 the two-register method of Eq. 21, 1 its tableau with full k-storage,
+        2 RKF45 (SCHEMES)."""
         rho, e = _f64(rho), _f64(e)
         Y = np.array(Y, dtype=np.float64, order="C", copy=True)
         T = np.array(T, dtype=np.float64, copy=True)
@@ -240,9 +249,9 @@ class Oracle:
         hout = np.zeros(n)
         h0a = _f64(h0) if h0 is not None else None
         h0p = _dp(h0a) if h0 is not None else None
-        self.L.oracle_integrate(self._mp, n, _dp(rho), _dp(e), _dp(Y), Y.shape[1], _dp(T), dt, rtol,
-                                atol, h0p, max_steps, _ip(status), _ip(nsteps), _ip(nacc),
-                                _dp(margin), _dp(hout), nthreads)
+        self.L.oracle_integrate_scheme(int(scheme), self._mp, n, _dp(rho), _dp(e), _dp(Y), Y.shape[1],
+                                       _dp(T), dt, rtol, atol, h0p, max_steps, _ip(status), _ip(nsteps),
+                                       _ip(nacc), _dp(margin), _dp(hout), nthreads)
         return {"Y": Y, "T": T, "status": status, "nsteps": nsteps, "naccept": nacc,
                 "margin": margin, "h": hout}
 
@@ -285,3 +294,32 @@ def linear_integrate(M, y, dt, rtol, atol, h0=0.0, max_steps=100000, max_log=100
 
 def quadratic_fixed(y0, h, nsteps, embedded=False):
     return lib().oracle_quadratic_fixed(y0, h, nsteps, int(embedded))
+
+
+SCHEMES = {"lsrk2r": 0, "full": 1, "rkf45": 2}
+MAXSTAGE = 6
+
+
+def butcher(scheme):
+    """Butcher tableau of scheme 1 or 2 (scheme 0 has the same tableau as 1): returns
+    (stages, A [6, 6], b, bhat, controller exponent)."""
+    s = C.c_int32(0)
+    a = np.zeros(MAXSTAGE * MAXSTAGE)
+    b = np.zeros(MAXSTAGE)
+    bh = np.zeros(MAXSTAGE)
+    ex = C.c_double(0.0)
+    lib().oracle_butcher(int(scheme), C.byref(s), _dp(a), _dp(b), _dp(bh), C.byref(ex))
+    k = s.value
+    return k, a.reshape(MAXSTAGE, MAXSTAGE)[:k, :k].copy(), b[:k].copy(), bh[:k].copy(), ex.value
+
+
+def linear_step_scheme(scheme, M, h, y):
+    M = _f64(M)
+    y = np.array(y, dtype=np.float64, copy=True)
+    E = np.zeros_like(y)
+    lib().oracle_linear_step_scheme(int(scheme), y.size, _dp(M), h, _dp(y), _dp(E))
+    return y, E
+
+
+def quadratic_fixed_scheme(scheme, y0, h, nsteps, embedded=False):
+    return lib().oracle_quadratic_fixed_scheme(int(scheme), y0, h, nsteps, int(embedded))

@@ -293,6 +293,110 @@ static int lsrk_step(int n, rhs_fn f, void *ctx, double h, double *X, double *E)
   return 0;
 }
 
+/* ------------------------------------ conventional (full-storage) explicit RK */
+
+/* An explicit Runge-Kutta tableau in Butcher form: stage i evaluates k_i = f(U_i) at
+ * U_i = y_n + h sum_{j<i} a_ij k_j; the step keeps every k_i and ends with
+ * y_n+1 = y_n + h sum_i b_i k_i and the embedded error estimate h sum_i (b_i - bhat_i) k_i.
+ * expo is the controller exponent 1/(q+1), q the order of the error estimate's leading
+ * term minus one. */
+#define OR_MAXSTAGE 6
+typedef struct {
+  int s;
+  double a[OR_MAXSTAGE][OR_MAXSTAGE], b[OR_MAXSTAGE], bh[OR_MAXSTAGE];
+  double expo;
+} butcher;
+
+/* The method of Eq. 21 written in Butcher form: the two-register recursion
+ * U = X + a_{i+1,i} h F, X = U + (b_i - a_{i+1,i}) h F leaves every earlier stage in X
+ * with its weight b_j, so a_ij = b_j for j < i-1 and a_{i,i-1} is the sub-diagonal
+ * coefficient (Sec. 2.2.3; ref. [37]). */
+static butcher lsrk_full_tableau(void) {
+  butcher t;
+  memset(&t, 0, sizeof t);
+  t.s = 5;
+  for (int i = 1; i < 5; ++i) {
+    for (int j = 0; j < i - 1; ++j) t.a[i][j] = LS_B[j];
+    t.a[i][i - 1] = LS_A[i - 1];
+  }
+  for (int i = 0; i < 5; ++i) { t.b[i] = LS_B[i]; t.bh[i] = LS_BH[i]; }
+  t.expo = 0.25;
+  return t;
+}
+
+/* Fehlberg's embedded 4(5) pair (RKF45, the paper's ref. [36]; Fehlberg, NASA TR R-315,
+ * 1969): six stages, the fourth-order solution is propagated (b) and the fifth-order one
+ * (bhat) estimates its error, whose leading term is O(h^5): exponent 1/5. */
+static butcher rkf45_tableau(void) {
+  butcher t;
+  memset(&t, 0, sizeof t);
+  t.s = 6;
+  t.a[1][0] = 1.0 / 4.0;
+  t.a[2][0] = 3.0 / 32.0; t.a[2][1] = 9.0 / 32.0;
+  t.a[3][0] = 1932.0 / 2197.0; t.a[3][1] = -7200.0 / 2197.0; t.a[3][2] = 7296.0 / 2197.0;
+  t.a[4][0] = 439.0 / 216.0; t.a[4][1] = -8.0; t.a[4][2] = 3680.0 / 513.0; t.a[4][3] = -845.0 / 4104.0;
+  t.a[5][0] = -8.0 / 27.0; t.a[5][1] = 2.0; t.a[5][2] = -3544.0 / 2565.0; t.a[5][3] = 1859.0 / 4104.0;
+  t.a[5][4] = -11.0 / 40.0;
+  const double b4[6] = {25.0 / 216.0, 0.0, 1408.0 / 2565.0, 2197.0 / 4104.0, -1.0 / 5.0, 0.0};
+  const double b5[6] = {16.0 / 135.0, 0.0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0, 2.0 / 55.0};
+  for (int i = 0; i < 6; ++i) { t.b[i] = b4[i]; t.bh[i] = b5[i]; }
+  t.expo = 0.2;
+  return t;
+}
+
+/* The integration schemes: 0 the two-register method of Eq. 21, 1 the same tableau with
+ * full k-storage, 2 RKF45 with full k-storage. */
+static butcher scheme_tableau(int scheme) {
+  return scheme == 2 ? rkf45_tableau() : lsrk_full_tableau();
+}
+
+void oracle_butcher(int32_t scheme, int32_t *s, double *a, double *b, double *bh, double *expo) {
+  butcher t = scheme_tableau(scheme);
+  *s = t.s;
+  for (int i = 0; i < OR_MAXSTAGE; ++i) {
+    for (int j = 0; j < OR_MAXSTAGE; ++j) a[i * OR_MAXSTAGE + j] = t.a[i][j];
+    b[i] = t.b[i];
+    bh[i] = t.bh[i];
+  }
+  *expo = t.expo;
+}
+
+/* One step of tableau t from X (overwritten with y_n+1), every stage derivative kept.
+ * Returns 0, or the 1-based stage whose RHS failed. */
+static int butcher_step(int n, rhs_fn f, void *ctx, const butcher *t, double h, double *X, double *E) {
+  double K[OR_MAXSTAGE][OR_MAXN], U[OR_MAXN];
+  for (int i = 0; i < t->s; ++i) {
+    for (int k = 0; k < n; ++k) {
+      double acc = 0.0;
+      for (int j = 0; j < i; ++j) acc += t->a[i][j] * K[j][k];
+      U[k] = X[k] + h * acc;
+    }
+    if (f(ctx, U, K[i])) return i + 1;
+  }
+  for (int k = 0; k < n; ++k) {
+    double sb = 0.0, se = 0.0;
+    for (int i = 0; i < t->s; ++i) {
+      sb += t->b[i] * K[i][k];
+      se += (t->b[i] - t->bh[i]) * K[i][k];
+    }
+    X[k] += h * sb;
+    E[k] = h * se;
+  }
+  return 0;
+}
+
+/* One step of scheme 0, 1 or 2; exponent of its controller in *expo. */
+static int scheme_step(int scheme, int n, rhs_fn f, void *ctx, double h, double *X, double *E,
+                       double *expo) {
+  if (scheme == 0) {
+    *expo = 0.25;
+    return lsrk_step(n, f, ctx, h, X, E);
+  }
+  butcher t = scheme_tableau(scheme);
+  *expo = t.expo;
+  return butcher_step(n, f, ctx, &t, h, X, E);
+}
+
 /* WRMS error of Eq. 22 over n components, |u_i| = max(|y_n,i|, |y_n+1,i|). */
 static double wrms(int n, const double *E, const double *Xold, const double *Xnew, double rtol,
                    double atol) {
@@ -316,8 +420,8 @@ typedef struct {
 /* on_event (nullable) is told when an attempt begins (0) and when one is rejected (1),
  * so that a right-hand side with state of its own (the temperature warm start of a
  * chemistry cell) can return it to the accepted state together with X. */
-static void integrate_adaptive(int n, rhs_fn f, void *ctx, double dt, double rtol, double atol,
-                               double h0, int32_t max_steps, double *X, adapt_out *out,
+static void integrate_adaptive(int scheme, int n, rhs_fn f, void *ctx, double dt, double rtol,
+                               double atol, double h0, int32_t max_steps, double *X, adapt_out *out,
                                double *log_h, double *log_err, int32_t *log_acc, int32_t max_log,
                                void (*on_event)(void *ctx, int ev)) {
   double t = 0.0, h = (h0 > 0.0) ? h0 : dt;
@@ -333,7 +437,8 @@ static void integrate_adaptive(int n, rhs_fn f, void *ctx, double dt, double rto
     /* A trial stage (2..5) whose RHS fails (no temperature root) or an error estimate
      * that is not finite rejects the attempt with the smallest factor 1/5; a failure
      * at stage 1, the accepted state itself, ends the cell with status 3. */
-    int failed = lsrk_step(n, f, ctx, h, X, E);
+    double expo = 0.25;
+    int failed = scheme_step(scheme, n, f, ctx, h, X, E, &expo);
     if (failed == 1) {
       for (int i = 0; i < n; ++i) X[i] = Xs[i];
       out->status = 3;
@@ -348,7 +453,7 @@ static void integrate_adaptive(int n, rhs_fn f, void *ctx, double dt, double rto
       h = h * 0.2;
       continue;
     }
-    double fac = (err == 0.0) ? 5.0 : fmin(5.0, fmax(0.2, 0.9 * pow(1.0 / err, 0.25)));
+    double fac = (err == 0.0) ? 5.0 : fmin(5.0, fmax(0.2, 0.9 * pow(1.0 / err, expo)));
     if (k < max_log) { log_h[k] = h; log_err[k] = err; log_acc[k] = err <= 1.0; }
     if (fabs(err - 1.0) < out->margin) out->margin = fabs(err - 1.0);
     if (err <= 1.0) {
@@ -385,6 +490,14 @@ void oracle_linear_step(int32_t n, const double *M, double h, double *y, double 
   lsrk_step(n, linear_rhs, &c, h, y, E);
 }
 
+/* The same step with scheme 0, 1 or 2. */
+void oracle_linear_step_scheme(int32_t scheme, int32_t n, const double *M, double h, double *y,
+                               double *E) {
+  linear_ctx c = {n, M};
+  double expo;
+  scheme_step(scheme, n, linear_rhs, &c, h, y, E, &expo);
+}
+
 /* Adaptive integration of y' = M y over [0, dt]; logs every attempted step.
  * out4 = {status, accepted, rejected}; returns the number of attempts. */
 int32_t oracle_linear_integrate(int32_t n, const double *M, double *y, double dt, double rtol,
@@ -392,7 +505,7 @@ int32_t oracle_linear_integrate(int32_t n, const double *M, double *y, double dt
                                 double *log_err, int32_t *log_acc, int32_t max_log, int32_t *out3) {
   linear_ctx c = {n, M};
   adapt_out o;
-  integrate_adaptive(n, linear_rhs, &c, dt, rtol, atol, h0, max_steps, y, &o, log_h, log_err,
+  integrate_adaptive(0, n, linear_rhs, &c, dt, rtol, atol, h0, max_steps, y, &o, log_h, log_err,
                      log_acc, max_log, NULL);
   out3[0] = o.status; out3[1] = o.nacc; out3[2] = o.nrej;
   return o.nacc + o.nrej;
@@ -410,6 +523,18 @@ double oracle_quadratic_fixed(double y0, double h, int32_t nsteps, int32_t embed
   double X[1] = {y0}, E[1];
   for (int s = 0; s < nsteps; ++s) {
     lsrk_step(1, quadratic_rhs, NULL, h, X, E);
+    if (embedded) X[0] -= E[0];
+  }
+  return X[0];
+}
+
+/* The same with scheme 0, 1 or 2 (embedded: propagate y_n+1 - E, the solution of the
+ * bhat weights). */
+double oracle_quadratic_fixed_scheme(int32_t scheme, double y0, double h, int32_t nsteps,
+                                     int32_t embedded) {
+  double X[1] = {y0}, E[1], expo;
+  for (int s = 0; s < nsteps; ++s) {
+    scheme_step(scheme, 1, quadratic_rhs, NULL, h, X, E, &expo);
     if (embedded) X[0] -= E[0];
   }
   return X[0];
@@ -460,10 +585,11 @@ double oracle_chem_rhs(const omech *m, double rho, double e, const double *Y, do
  * 4 non-finite), attempted steps, accepted steps, the smallest |err - 1| seen
  * (used to classify cells whose accept/reject decisions sit on a rounding knife-edge)
  * and the controller's next step h_out (to carry into a following call). */
-int32_t oracle_integrate(const omech *m, int64_t n, const double *rho, const double *e, double *Y,
-                         int64_t ldY, double *T, double dt, double rtol, double atol,
-                         const double *h0, int32_t max_steps, int32_t *status, int32_t *nsteps,
-                         int32_t *naccept, double *margin, double *h_out, int32_t nthreads) {
+int32_t oracle_integrate_scheme(int32_t scheme, const omech *m, int64_t n, const double *rho,
+                                const double *e, double *Y, int64_t ldY, double *T, double dt,
+                                double rtol, double atol, const double *h0, int32_t max_steps,
+                                int32_t *status, int32_t *nsteps, int32_t *naccept, double *margin,
+                                double *h_out, int32_t nthreads) {
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 8)
@@ -480,7 +606,7 @@ int32_t oracle_integrate(const omech *m, int64_t n, const double *rho, const dou
       o.h_next = (h0 && isfinite(h0[i]) && h0[i] > 0.0) ? h0[i] : dt;
     } else {
       double hi = (h0 && isfinite(h0[i]) && h0[i] > 0.0) ? h0[i] : 0.0;
-      integrate_adaptive(m->nsp, chem_rhs, &cc, dt, rtol, atol, hi, max_steps, X,
+      integrate_adaptive(scheme, m->nsp, chem_rhs, &cc, dt, rtol, atol, hi, max_steps, X,
                          &o, NULL, NULL, NULL, 0, chem_event);
     }
     double Tout = NAN;
@@ -497,6 +623,15 @@ int32_t oracle_integrate(const omech *m, int64_t n, const double *rho, const dou
     if (h_out) h_out[i] = o.h_next;
   }
   return 0;
+}
+
+/* The integration of the two-register method of Eq. 21 (scheme 0). */
+int32_t oracle_integrate(const omech *m, int64_t n, const double *rho, const double *e, double *Y,
+                         int64_t ldY, double *T, double dt, double rtol, double atol,
+                         const double *h0, int32_t max_steps, int32_t *status, int32_t *nsteps,
+                         int32_t *naccept, double *margin, double *h_out, int32_t nthreads) {
+  return oracle_integrate_scheme(0, m, n, rho, e, Y, ldY, T, dt, rtol, atol, h0, max_steps, status,
+                                 nsteps, naccept, margin, h_out, nthreads);
 }
 
 /* Fixed-step integration of one cell (nsteps steps of h, no error control), recording
