@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--sur-cells", type=int, default=1 << 24)
     ap.add_argument("--no-bubble", action="store_true", help="skip the shock-bubble hybrid leg")
     ap.add_argument("--no-eq27", action="store_true", help="skip the Eq. 27 divergence benchmark leg")
+    ap.add_argument("--no-comparators", action="store_true",
+                    help="skip the full-storage / RKF45 comparator leg")
     ap.add_argument("--bubble-n", type=int, default=256)
     ap.add_argument("--cpu-sample", type=int, default=131072)
     ap.add_argument("--ref-sample", type=int, default=32768)
@@ -276,14 +278,76 @@ def fallback_reasons(mask):
     return {name: float(counts[i + 1]) / n for i, name in enumerate(FALLBACK_REASONS)}
 
 
+# The conventional explicit comparators (full k-storage) and the one-pass block shape
+# each runs fastest in on GB300 (measured over 64 / 128 / 256 threads per block).
+COMPARATORS = {"fp64": (("lsrk", 128), ("full", 128), ("rkf45", 128)),
+               "mixed": (("lsrk", 64), ("full", 64), ("rkf45", 64))}
+
+
+def comparators_leg(mech, rho, e, Y0, T0, Y, T, nsteps, flush, steps, stream):
+    """The paper's comparison of its two-register scheme with standard explicit RK that
+    keeps every stage derivative (Sec. 2.2.3, Sec. 4.2.2), on the benchmark slice: the
+    same RK4(3)5 tableau with full k-storage and Fehlberg's RKF45, one-pass launches,
+    each the median of `steps` CUDA-event-timed launches from the pristine state (L2
+    flushed), with the compiled kernel's registers and spills."""
+    import torch
+    from paper_2506_02602_gb300 import build, chem
+    n = T0.numel()
+    out = {}
+    for variant, cfgs in COMPARATORS.items():
+        base = None
+        for scheme, block in cfgs:
+            ctx = chem.Context(mech, variant, scheme=scheme, block_size=block)
+            ts = []
+            for k in range(steps + 1):
+                Y.copy_(Y0)
+                T.copy_(T0)
+                flush.fill_(1.0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ctx.integrate(rho, e, Y, T, DT, RTOL, ATOL, nsteps=nsteps, stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                if k:
+                    ts.append(a.elapsed_time(b))
+            ms = float(np.median(ts))
+            if base is None:
+                base = ms
+            out[f"{variant} {scheme}"] = {"block": block, "ms": ms, "cells_per_s": n / (ms * 1e-3),
+                                          "attempted_steps": int(nsteps.sum()),
+                                          "time_vs_lsrk": ms / base}
+            ctx.close()
+    out["registers"] = build.kernel_resources("4chem6k_lsrkI")
+    return out
+
+
 def eq27_leg(mech, dev, stream):
     """The Eq. 27 thread-divergence benchmark (module docstring)."""
     import torch
     from chem_inputs import workloads
     from paper_2506_02602_gb300 import chem
     out = {"cells": 65536, "steps": 100, "dt": 1e-5,
-           "paper_v100_s": {"alpha=1": 4.4032, "alpha=0.1": 5.1225}}
+           "paper_v100_s": {"alpha=1": 4.4032, "alpha=0.1": 5.1225},
+           "paper_note": "the paper's V100 runs: LSRK about 3x faster than RKF45 and 6x than CVODE"}
     for variant in ("fp64", "mixed"):
+        # the comparators on the same field: 100 one-pass calls each
+        for scheme, block in COMPARATORS[variant][1:]:
+            ctx = chem.Context(mech, variant, scheme=scheme, block_size=block)
+            for alpha in (1.0, 0.1):
+                w = workloads.eq27_profile(alpha)
+                f64 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+                T0, Y0 = f64(w["T"]), f64(w["Y"])
+                rho, e = ctx.state_from_TPY(T0, f64(w["p"]), Y0)
+                Y, T = Y0.clone(), T0.clone()
+                h = torch.empty(T0.numel(), dtype=torch.float64, device=dev)
+
+                def calls():
+                    Y.copy_(Y0); T.copy_(T0); h.fill_(float("nan"))
+                    for _ in range(100):
+                        ctx.integrate(rho, e, Y, T, 1e-5, RTOL, ATOL, h=h, stream=stream)
+
+                out[f"{variant} {scheme} alpha={alpha:g}"] = {"calls_s": timed(calls, 1, stream) * 1e-3}
+            ctx.close()
         ctx = chem.Context(mech, variant)
         for alpha in (1.0, 0.1):
             w = workloads.eq27_profile(alpha)
@@ -311,6 +375,9 @@ def eq27_leg(mech, dev, stream):
             t_calls = timed(calls, 1, stream)
             Tc, ok_c = T.clone(), bool((st == 0).all())
             t_pers = timed(persistent, 1, stream)
+            for scheme, _ in COMPARATORS[variant][1:]:
+                r = out[f"{variant} {scheme} alpha={alpha:g}"]
+                r["time_vs_lsrk_calls"] = r["calls_s"] / (t_calls * 1e-3)
             out[f"{variant} alpha={alpha:g}"] = {
                 "calls_s": t_calls * 1e-3, "persistent_s": t_pers * 1e-3,
                 "cell_substeps_per_s": n * 100 / (min(t_calls, t_pers) * 1e-3),
@@ -713,6 +780,11 @@ def run_ours(args, rank, world, local):
     e2e_el, = max_over_ranks([e2e_el], world, dev)
     e2e_match = bool(np.array_equal(hY, res[head]["Y"]) and np.array_equal(hT, res[head]["T"]))
 
+    comparators = None
+    if not args.no_comparators:
+        comparators = comparators_leg(mech, rho, e, Y0, T0, Y, T, nsteps, flush, max(3, min(args.steps, 5)),
+                                      stream)
+
     eq27 = None
     if not args.no_eq27:
         eq27 = eq27_leg(mech, dev, stream)
@@ -754,6 +826,7 @@ def run_ours(args, rank, world, local):
             "surrogate": sur,
             "shock_bubble": bubble,
             "eq27": eq27,
+            "comparators": comparators,
             "clocks": clk,
             "cpu_baseline": cpu,
             "parity_vs_oracle_sample": parity,

@@ -106,15 +106,33 @@ typedef struct {
   int32_t reversible[CHEM_MAX_REACTIONS];
 } chem_mechanism;
 
+/*
+ * Integration scheme.  The paper's method is the two-register low-storage scheme of
+ * Eq. 21; the others are the conventional explicit comparators the paper measures it
+ * against (Sec. 2.2.3, Sec. 4.2.2), keeping every stage derivative: the same RK4(3)5
+ * tableau in Butcher form, and Fehlberg's RKF45 (six stages, fourth-order solution,
+ * fifth-order error estimate, controller exponent 1/5).  Only chem_integrate and
+ * chem_integrate_host run the comparators.
+ */
+typedef enum {
+  CHEM_SCHEME_LSRK = 0,          /* RK4(3)5[2R+]C, two registers plus the error register */
+  CHEM_SCHEME_FULL_STORAGE = 1,  /* the same tableau with all five k_i kept */
+  CHEM_SCHEME_RKF45 = 2          /* Fehlberg 4(5), all six k_i kept */
+} chem_scheme;
+
 /* Options fixed at setup.  Zero-initialised fields take the defaults in brackets. */
 typedef struct {
   int32_t variant;     /* chem_variant [CHEM_VARIANT_FP64] */
   int32_t max_steps;   /* attempted-step limit per cell and call [100000] */
   int32_t block_size;  /* threads per block of the one-pass integration kernel: 32 or 64
-                          (16 warps per SM, 128 registers a thread) or 128 (12 warps,
-                          170 registers); other values take 128 [0: 64 for the mixed
-                          variant, 128 for fp64] */
-  int32_t reserved[5]; /* must be zero */
+                          (16 warps per SM, 128 registers a thread), 128 (12 warps,
+                          170 registers) or 256 (8 warps, 255 registers); other values
+                          take 128 [0: 64 for the mixed variant, 128 for fp64] */
+  int32_t scheme;      /* chem_scheme [CHEM_SCHEME_LSRK]; the comparators serve
+                          chem_integrate and chem_integrate_host only: the batched and
+                          surrogate calls of a context with another scheme return
+                          CHEM_ERR_UNSUPPORTED */
+  int32_t reserved[4]; /* must be zero */
 } chem_options;
 
 /*

@@ -74,6 +74,26 @@ def ptxas_report() -> str:
     return "\n".join(out)
 
 
+def kernel_resources(pattern: str = "") -> list:
+    """Registers, stack frame and spill bytes per compiled kernel of the last build (from
+    ptxas -v), for kernels whose mangled name contains `pattern`."""
+    import re
+    out = []
+    for f in sorted(glob.glob(os.path.join(BUILD, "*.ptxas.txt"))):
+        with open(f) as fh:
+            txt = fh.read()
+        for blk in re.split(r"Compiling entry function '", txt)[1:]:
+            name = blk.split("'")[0]
+            if pattern not in name:
+                continue
+            st = re.search(r"(\d+) bytes stack frame, (\d+) bytes spill stores, (\d+) bytes spill loads", blk)
+            rg = re.search(r"Used (\d+) registers", blk)
+            if st and rg:
+                out.append({"kernel": name, "registers": int(rg.group(1)), "stack": int(st.group(1)),
+                            "spill_stores": int(st.group(2)), "spill_loads": int(st.group(3))})
+    return out
+
+
 if __name__ == "__main__":
     print(build(force=True))
     print(ptxas_report())

@@ -26,6 +26,7 @@ NUM_ELEMENTS = 3
 OK, ERR_INVALID, ERR_CUDA, ERR_UNSUPPORTED, ERR_NOMEM, ERR_TIMEOUT, ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 CELL_OK, CELL_MAX_STEPS, CELL_H_UNDERFLOW, CELL_NEWTON_FAIL, CELL_NONFINITE, CELL_SURROGATE = range(6)
 VARIANTS = {"fp64": 0, "mixed": 1}
+SCHEMES = {"lsrk": 0, "full": 1, "rkf45": 2}
 
 
 class ChemError(RuntimeError):
@@ -58,7 +59,7 @@ class Mechanism(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("variant", C.c_int32), ("max_steps", C.c_int32), ("block_size", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("scheme", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class State(C.Structure):
@@ -266,19 +267,22 @@ def _check_cells(n, rho, e, Y, T, h=None, status=None, nsteps=None, cost_hint=No
 class Context:
     """A chem_ctx bound to one mechanism and precision variant."""
 
-    def __init__(self, mech: dict, variant: str = "fp64", max_steps: int = 0, block_size: int = 0):
+    def __init__(self, mech: dict, variant: str = "fp64", max_steps: int = 0, block_size: int = 0,
+                 scheme: str = "lsrk"):
         self.L = load()
         self._mech = make_mechanism(mech)
         opt = Options()
         opt.variant = VARIANTS[variant]
         opt.max_steps = max_steps
         opt.block_size = block_size
+        opt.scheme = SCHEMES[scheme]
         h = C.c_void_p()
         rc = self.L.chem_setup(C.byref(self._mech), C.byref(opt), C.byref(h))
         if rc != OK:
             raise ChemError(rc, self.L.chem_last_error(None).decode())
         self.h = h
         self.variant = variant
+        self.scheme = scheme
         self.n_species = len(mech["W"])
 
     def close(self):

@@ -270,6 +270,8 @@ int check_batched_call(chem_ctx *ctx, const chem_state *state, int64_t ncells,
   rc = check_step(ctx, 1.0, rtol, atol);
   if (rc) return rc;
   if (ncells > INT32_MAX) return fail(ctx, CHEM_ERR_INVALID, "batched calls hold at most 2^31-1 cells");
+  if (ctx->opt.scheme != CHEM_SCHEME_LSRK)
+    return fail(ctx, CHEM_ERR_UNSUPPORTED, "the batched integrator runs the two-register scheme only");
   *o = chem_batch_options{};
   if (opt) *o = *opt;
   if (o->order != CHEM_ORDER_STIFFNESS && o->order != CHEM_ORDER_NATURAL)
@@ -306,7 +308,9 @@ int chem_setup(const chem_mechanism *mech, const chem_options *opt, chem_ctx **o
   // mixed variant (measured 1.7 % faster than 12 warps), 12 at 170 for fp64 (whose 128-
   // register build spills)
   if (o.block_size == 0) o.block_size = o.variant == CHEM_VARIANT_MIXED ? 64 : 128;
-  for (int i = 0; i < 5; ++i)
+  if (o.scheme != CHEM_SCHEME_LSRK && o.scheme != CHEM_SCHEME_FULL_STORAGE && o.scheme != CHEM_SCHEME_RKF45)
+    return fail(nullptr, CHEM_ERR_INVALID, "unknown scheme %d", o.scheme);
+  for (int i = 0; i < 4; ++i)
     if (o.reserved[i]) return fail(nullptr, CHEM_ERR_INVALID, "reserved options must be zero");
   MechTables t;
   int rc = build_tables(mech, &t);
@@ -369,7 +373,7 @@ int chem_integrate(chem_ctx *ctx, const chem_state *state, int64_t ncells, doubl
   CellArgs a{state->d_rho, state->d_e, state->d_Y, state->ldY, state->d_T, state->d_h,
              state->d_status, state->d_nsteps, ncells, d_stats};
   StepParams p{dt, rtol, atol, ctx->opt.max_steps};
-  cudaError_t e = launch_lsrk(ctx->opt.variant, ctx->tables, a, p, ctx->opt.block_size, s);
+  cudaError_t e = launch_lsrk(ctx->opt.variant, ctx->opt.scheme, ctx->tables, a, p, ctx->opt.block_size, s);
   return e == cudaSuccess ? CHEM_OK : cuda_fail(ctx, e, "integration launch");
 }
 
@@ -563,7 +567,7 @@ int chem_integrate_host(chem_ctx *ctx, int64_t n, const double *h_rho, const dou
       CellArgs a{d_rho + c0, d_e + c0, d_Y + c0, (int64_t)nd, d_T + c0, h_h ? d_h + c0 : nullptr,
                  d_status + c0, d_nsteps + c0, (int64_t)m, nullptr};
       StepParams p{dt, rtol, atol, ctx->opt.max_steps};
-      CK(launch_lsrk(ctx->opt.variant, ctx->tables, a, p, ctx->opt.block_size, cs), "integration launch");
+      CK(launch_lsrk(ctx->opt.variant, ctx->opt.scheme, ctx->tables, a, p, ctx->opt.block_size, cs), "integration launch");
       CK(cudaEventRecord(ev_comp, cs), "event");
       CK(cudaStreamWaitEvent(out, ev_comp, 0), "event wait");
       CK(cudaMemcpy2DAsync(h_Y + c0, (size_t)ldY * sizeof(double), d_Y + c0, bytes, mb, NSP,
@@ -590,7 +594,7 @@ int chem_integrate_host(chem_ctx *ctx, int64_t n, const double *h_rho, const dou
                        cudaMemcpyHostToDevice, s), "copy Y");
   CellArgs a{d_rho, d_e, d_Y, (int64_t)nd, d_T, h_h ? d_h : nullptr, d_status, d_nsteps, n, nullptr};
   StepParams p{dt, rtol, atol, ctx->opt.max_steps};
-  CK(launch_lsrk(ctx->opt.variant, ctx->tables, a, p, ctx->opt.block_size, s), "integration launch");
+  CK(launch_lsrk(ctx->opt.variant, ctx->opt.scheme, ctx->tables, a, p, ctx->opt.block_size, s), "integration launch");
   CK(cudaMemcpy2DAsync(h_Y, (size_t)ldY * sizeof(double), d_Y, bytes, bytes, NSP,
                        cudaMemcpyDeviceToHost, s), "copy Y back");
   CK(cudaMemcpyAsync(h_T, d_T, bytes, cudaMemcpyDeviceToHost, s), "copy T back");
@@ -613,6 +617,7 @@ namespace chem {
 std::string &chem_ctx_error(chem_ctx *ctx) { return ctx->err; }
 const MechTables &chem_ctx_tables(const chem_ctx *ctx) { return ctx->tables; }
 int chem_ctx_variant(const chem_ctx *ctx) { return ctx->opt.variant; }
+int chem_ctx_scheme(const chem_ctx *ctx) { return ctx->opt.scheme; }
 int32_t chem_ctx_max_steps(const chem_ctx *ctx) { return ctx->opt.max_steps; }
 void *&chem_ctx_sur(chem_ctx *ctx) { return ctx->sur; }
 }  // namespace chem

@@ -114,6 +114,8 @@ int chem_autotune_batched(chem_ctx *ctx, const chem_state *state, int64_t ncells
     return tune_fail(ctx, CHEM_ERR_INVALID, "rho, e, Y and T are required and ldY >= ncells");
   if (max_results < 0 || (max_results > 0 && !h_results))
     return tune_fail(ctx, CHEM_ERR_INVALID, "h_results is required when max_results > 0");
+  if (chem_ctx_scheme(ctx) != CHEM_SCHEME_LSRK)
+    return tune_fail(ctx, CHEM_ERR_UNSUPPORTED, "the batched integrator runs the two-register scheme only");
   chem_batch_options b0{};
   if (base) b0 = *base;
   const std::string key = tune_key(ctx, rtol, atol, ncells, batch->nboxes);

@@ -48,6 +48,42 @@ static __constant__ double c_ls_e[5] = {
     2114624349019.0 / 3568978502595.0 - 606302364029.0 / 971179775848.0,
     5198255086312.0 / 14908931495163.0 - 1097981568119.0 / 3980877426909.0};
 
+// Conventional explicit RK with full k-storage, the comparators of the two-register
+// scheme (the paper's "standard explicit" methods, Sec. 2.2.3 and Sec. 4.2.2): stage i
+// evaluates k_i = f(y_n + h sum_{j<i} a_ij k_j) and every k_i is kept until
+// y_n+1 = y_n + h sum_i b_i k_i and the error h sum_i (b_i - bhat_i) k_i are formed.
+// Table 0: the RK4(3)5[2R+]C tableau above in Butcher form (the two-register recursion
+// leaves a_ij = b_j for j < i-1); table 1: Fehlberg's RKF45 (NASA TR R-315, 1969), the
+// fourth-order solution propagated and the fifth-order one estimating its error.
+static __constant__ double c_fs_a[2][6][6] = {
+    {{0.0},
+     {970286171893.0 / 4311952581923.0},
+     {1153189308089.0 / 22510343858157.0, 6584761158862.0 / 12103376702013.0},
+     {1153189308089.0 / 22510343858157.0, 1772645290293.0 / 4653164025191.0,
+      2251764453980.0 / 15575788980749.0},
+     {1153189308089.0 / 22510343858157.0, 1772645290293.0 / 4653164025191.0,
+      -1672844663538.0 / 4480602732383.0, 26877169314380.0 / 34165994151039.0},
+     {0.0}},
+    {{0.0},
+     {1.0 / 4.0},
+     {3.0 / 32.0, 9.0 / 32.0},
+     {1932.0 / 2197.0, -7200.0 / 2197.0, 7296.0 / 2197.0},
+     {439.0 / 216.0, -8.0, 3680.0 / 513.0, -845.0 / 4104.0},
+     {-8.0 / 27.0, 2.0, -3544.0 / 2565.0, 1859.0 / 4104.0, -11.0 / 40.0}}};
+static __constant__ double c_fs_b[2][6] = {
+    {1153189308089.0 / 22510343858157.0, 1772645290293.0 / 4653164025191.0,
+     -1672844663538.0 / 4480602732383.0, 2114624349019.0 / 3568978502595.0,
+     5198255086312.0 / 14908931495163.0, 0.0},
+    {25.0 / 216.0, 0.0, 1408.0 / 2565.0, 2197.0 / 4104.0, -1.0 / 5.0, 0.0}};
+static __constant__ double c_fs_e[2][6] = {
+    {1153189308089.0 / 22510343858157.0 - 1016888040809.0 / 7410784769900.0,
+     1772645290293.0 / 4653164025191.0 - 11231460423587.0 / 58533540763752.0,
+     -1672844663538.0 / 4480602732383.0 - -1563879915014.0 / 6823010717585.0,
+     2114624349019.0 / 3568978502595.0 - 606302364029.0 / 971179775848.0,
+     5198255086312.0 / 14908931495163.0 - 1097981568119.0 / 3980877426909.0, 0.0},
+    {25.0 / 216.0 - 16.0 / 135.0, 0.0, 1408.0 / 2565.0 - 6656.0 / 12825.0,
+     2197.0 / 4104.0 - 28561.0 / 56430.0, -1.0 / 5.0 - -9.0 / 50.0, 0.0 - 2.0 / 55.0}};
+
 struct CellState {
   double X[NSP];
   double T, h, t, dt;
@@ -172,6 +208,112 @@ __device__ __forceinline__ void cell_attempt(const MechTables &mt, CellState &c,
   } else {
 #pragma unroll
     for (int k = 0; k < NSP; ++k) c.X[k] = Xs[k];
+    c.T = Tacc;
+    ++c.nrej;
+  }
+  c.h = h * fac;
+}
+
+// One attempted step of a full-storage scheme (CHEM_SCHEME_FULL_STORAGE: table 0, five
+// stages; CHEM_SCHEME_RKF45: table 1, six stages).  The same controller as cell_attempt
+// with the table's exponent (1/4 and 1/5).  The stage loop stays rolled (the right-hand
+// side is inlined once); the stage derivatives live in a register array indexed by
+// compile-time constants, written through predicated moves, so the k-storage costs
+// registers (and spills), not local-memory indexing.
+template <int V, int SCH>
+__device__ __forceinline__ void cell_attempt_full(const MechTables &mt, CellState &c,
+                                                  const StepParams &p) {
+  constexpr bool kMixed = V == CHEM_VARIANT_MIXED;
+  constexpr int TB = SCH == CHEM_SCHEME_RKF45 ? 1 : 0;
+  constexpr int S = SCH == CHEM_SCHEME_RKF45 ? 6 : 5;
+  using SReal = std::conditional_t<kMixed, float, double>;
+  const double dt = c.dt;
+  if (!(dt - c.t > 1e-12 * dt)) { c.done = true; return; }
+  if (c.nacc + c.nrej >= p.max_steps) { c.status = CHEM_CELL_MAX_STEPS; c.done = true; return; }
+  if (c.h < 1e-15 * dt) { c.status = CHEM_CELL_H_UNDERFLOW; c.done = true; return; }
+  double h = c.h;
+  if (h > dt - c.t) h = dt - c.t;
+  SReal K[S][NSP];
+#pragma unroll
+  for (int j = 0; j < S; ++j)
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) K[j][k] = SReal(0);
+  int failed = 0;
+  double Tacc = c.T;
+#pragma unroll 1
+  for (int s = 0; s < S; ++s) {
+    SReal U[NSP], F[NSP];
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+      if constexpr (kMixed) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int j = 0; j < S - 1; ++j)
+          if (j < s) acc = fmaf(d2f(h * c_fs_a[TB][s][j]), K[j][k], acc);
+        U[k] = d2f(c.X[k]) + acc;
+      } else {
+        double acc = 0.0;
+#pragma unroll
+        for (int j = 0; j < S - 1; ++j)
+          if (j < s) acc = fma(c_fs_a[TB][s][j], K[j][k], acc);
+        U[k] = fma(h, acc, c.X[k]);
+      }
+    }
+    ++c.nrhs;
+    bool ok;
+    if constexpr (kMixed) ok = cell_rhs_mixed(mt, U, c.rho_f, c.invRho_f, c.eR, c.T, F);
+    else ok = cell_rhs(mt, U, c.rho, c.invRho, c.eR, c.T, F);
+    if (!ok) { failed = s + 1; break; }
+    if (s == 0) Tacc = c.T;
+#pragma unroll
+    for (int j = 0; j < S; ++j)
+      if (j == s) {
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) K[j][k] = F[k];
+      }
+  }
+  if (failed == 1) {
+    c.status = CHEM_CELL_NEWTON_FAIL;
+    c.done = true;
+    return;
+  }
+  double Xn[NSP], E[NSP];
+  double err = CUDART_NAN;
+  if (!failed) {
+    double sum = 0.0;
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+      double sb = 0.0, se = 0.0;
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        const double Kj = kMixed ? f2d((float)K[j][k]) : (double)K[j][k];
+        sb = fma(c_fs_b[TB][j], Kj, sb);
+        se = fma(c_fs_e[TB][j], Kj, se);
+      }
+      Xn[k] = fma(h, sb, c.X[k]);
+      E[k] = h * se;
+      const double den = fma(p.rtol, max_abs(c.X[k], Xn[k]), p.atol);
+      const double w = E[k] * (kMixed ? rcp1(den) : rcp2(den));
+      sum = fma(w, w, sum);
+    }
+    err = sqrt(sum * (1.0 / NSP));
+  }
+  if (!isfinite(err)) {
+    c.T = Tacc;
+    ++c.nrej;
+    c.h = h * 0.2;
+    return;
+  }
+  double fac;
+  if (err == 0.0) fac = 5.0;
+  else if constexpr (TB == 1) fac = fmin(5.0, fmax(0.2, 0.9 * pow(err, -0.2)));
+  else fac = fmin(5.0, fmax(0.2, 0.9 / sqrt(sqrt(err))));
+  if (err <= 1.0) {
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) c.X[k] = Xn[k];
+    c.t += h;
+    ++c.nacc;
+  } else {
     c.T = Tacc;
     ++c.nrej;
   }

@@ -9,8 +9,11 @@ namespace chem {
 
 // BLOCK threads per block, MINB resident blocks per SM.  The register file is split
 // between the SM's four sub-partitions, so 12 warps per SM allow 170 registers a thread
-// (128 x 3) and 16 warps 128 (64 x 8, 32 x 16); anything between rounds down to 128.
-template <int V, int BLOCK, int MINB>
+// (128 x 3) and 16 warps 128 (64 x 8, 32 x 16); anything between rounds down to 128;
+// 8 warps (256 x 1) leave the 255-register maximum.
+// SCH: CHEM_SCHEME_LSRK (the two-register scheme of Eq. 21) or one of the full-storage
+// comparators (cell_attempt_full).
+template <int V, int BLOCK, int MINB, int SCH = CHEM_SCHEME_LSRK>
 __global__ void __launch_bounds__(BLOCK, MINB) k_lsrk(const __grid_constant__ MechTables mt,
                                                       const CellArgs a, const StepParams p) {
   load_math_tables();
@@ -25,7 +28,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_lsrk(const __grid_constant__ Me
     c.T = a.T[i];
     c.h = a.h ? a.h[i] : CUDART_NAN;
     cell_begin(c, a.rho[i], a.e[i], p.dt);
-    while (!c.done) cell_attempt<V>(mt, c, p);
+    if constexpr (SCH == CHEM_SCHEME_LSRK) {
+      while (!c.done) cell_attempt<V>(mt, c, p);
+    } else {
+      while (!c.done) cell_attempt_full<V, SCH>(mt, c, p);
+    }
     cell_finish(mt, c);
 #pragma unroll
     for (int k = 0; k < NSP; ++k) a.Y[k * a.ld + i] = c.X[k];
@@ -61,21 +68,33 @@ __global__ void k_state_from_TPY(const __grid_constant__ MechTables mt, int64_t 
   e[i] = R_U * e_over_R(m, Ti);
 }
 
-template <int V>
+template <int V, int SCH>
 static void launch_shape(const MechTables &mt, const CellArgs &a, const StepParams &p, int block,
                          cudaStream_t s) {
   const unsigned grid = (unsigned)((a.n + block - 1) / block);
-  if (block == 32) k_lsrk<V, 32, 16><<<grid, 32, 0, s>>>(mt, a, p);
-  else if (block == 64) k_lsrk<V, 64, 8><<<grid, 64, 0, s>>>(mt, a, p);
-  else k_lsrk<V, 128, 3><<<grid, 128, 0, s>>>(mt, a, p);
+  if (block == 32) k_lsrk<V, 32, 16, SCH><<<grid, 32, 0, s>>>(mt, a, p);
+  else if (block == 64) k_lsrk<V, 64, 8, SCH><<<grid, 64, 0, s>>>(mt, a, p);
+  else if (block == 256) k_lsrk<V, 256, 1, SCH><<<grid, 256, 0, s>>>(mt, a, p);
+  else k_lsrk<V, 128, 3, SCH><<<grid, 128, 0, s>>>(mt, a, p);
 }
 
-cudaError_t launch_lsrk(int variant, const MechTables &mt, const CellArgs &a, const StepParams &p,
-                        int block, cudaStream_t s) {
+template <int SCH>
+static void launch_variant(int variant, const MechTables &mt, const CellArgs &a,
+                           const StepParams &p, int block, cudaStream_t s) {
+  if (variant == CHEM_VARIANT_MIXED) launch_shape<CHEM_VARIANT_MIXED, SCH>(mt, a, p, block, s);
+  else launch_shape<CHEM_VARIANT_FP64, SCH>(mt, a, p, block, s);
+}
+
+cudaError_t launch_lsrk(int variant, int scheme, const MechTables &mt, const CellArgs &a,
+                        const StepParams &p, int block, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  if (block != 32 && block != 64) block = 128;  // the compiled shapes
-  if (variant == CHEM_VARIANT_MIXED) launch_shape<CHEM_VARIANT_MIXED>(mt, a, p, block, s);
-  else launch_shape<CHEM_VARIANT_FP64>(mt, a, p, block, s);
+  if (block != 32 && block != 64 && block != 256) block = 128;  // the compiled shapes
+  if (scheme == CHEM_SCHEME_FULL_STORAGE)
+    launch_variant<CHEM_SCHEME_FULL_STORAGE>(variant, mt, a, p, block, s);
+  else if (scheme == CHEM_SCHEME_RKF45)
+    launch_variant<CHEM_SCHEME_RKF45>(variant, mt, a, p, block, s);
+  else
+    launch_variant<CHEM_SCHEME_LSRK>(variant, mt, a, p, block, s);
   return cudaGetLastError();
 }
 

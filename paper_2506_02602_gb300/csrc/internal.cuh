@@ -65,12 +65,13 @@ struct BatchScratch {
 };
 
 // Launchers (integrate.cu).  Return the cudaError_t of the launch.
-cudaError_t launch_lsrk(int variant, const MechTables &mt, const CellArgs &a, const StepParams &p,
-                        int block, cudaStream_t s);
+cudaError_t launch_lsrk(int variant, int scheme, const MechTables &mt, const CellArgs &a,
+                        const StepParams &p, int block, cudaStream_t s);
 // Context accessors (api.cu) for entry points defined in other translation units.
 std::string &chem_ctx_error(chem_ctx *ctx);
 const MechTables &chem_ctx_tables(const chem_ctx *ctx);
 int chem_ctx_variant(const chem_ctx *ctx);
+int chem_ctx_scheme(const chem_ctx *ctx);
 int32_t chem_ctx_max_steps(const chem_ctx *ctx);
 void *&chem_ctx_sur(chem_ctx *ctx);
 void surrogate_destroy(void *sur);

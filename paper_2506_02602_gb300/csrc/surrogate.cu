@@ -681,6 +681,8 @@ int chem_surrogate_infer(chem_ctx *ctx, const chem_state *state, int64_t n, doub
   if (!ctx) return CHEM_ERR_INVALID;
   Surrogate *s = static_cast<Surrogate *>(chem_ctx_sur(ctx));
   if (!s || !s->ready) return sur_fail(ctx, CHEM_ERR_STATE, "no trained or loaded surrogate");
+  if (chem_ctx_scheme(ctx) != CHEM_SCHEME_LSRK)
+    return sur_fail(ctx, CHEM_ERR_UNSUPPORTED, "the surrogate's fallback runs the two-register scheme only");
   if (!state || n < 0) return sur_fail(ctx, CHEM_ERR_INVALID, "state is NULL or ncells < 0");
   if (!(dt > 0.0) || !std::isfinite(dt) || !(rtol > 0.0) || !(atol >= 0.0))
     return sur_fail(ctx, CHEM_ERR_INVALID, "dt, rtol must be > 0 and atol >= 0");

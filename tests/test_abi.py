@@ -81,10 +81,11 @@ int main(void) {
                                           chem.TuneResult.ctas_per_sm.offset]
 
 
-def _setup_rc(lib, mech, variant=0):
+def _setup_rc(lib, mech, variant=0, scheme=0):
     m = chem.make_mechanism(mech)
     opt = chem.Options()
     opt.variant = variant
+    opt.scheme = scheme
     h = C.c_void_p()
     rc = lib.chem_setup(C.byref(m), C.byref(opt), C.byref(h))
     msg = lib.chem_last_error(None).decode()
@@ -126,6 +127,16 @@ def test_setup_rejects_discontinuous_thermo(lib):
 def test_setup_rejects_bad_options(lib):
     rc, msg = _setup_rc(lib, M.build(0), variant=7)
     assert rc == chem.ERR_INVALID
+    rc, msg = _setup_rc(lib, M.build(0), scheme=3)
+    assert rc == chem.ERR_INVALID and "scheme" in msg
+
+
+def test_fma_probe_validates_its_arguments(lib):
+    """chem_diag_fma_peak rejects an unknown pipe, empty grids, partial warps and a
+    missing sink before launching anything."""
+    for args in ((2, 1, 32, 1), (0, 0, 32, 1), (0, 1, 48, 1), (1, 1, 2048, 1), (0, 1, 32, 0)):
+        assert lib.chem_diag_fma_peak(*args, C.c_void_p(8), None) == chem.ERR_INVALID, args
+    assert lib.chem_diag_fma_peak(0, 1, 32, 1, None, None) == chem.ERR_INVALID
 
 
 def test_valid_mechanism_needs_a_device(lib):

@@ -63,9 +63,15 @@ def test_reactors_through_ignition(ctx):
               "T0 %.1f p %.3g" % (r["T"][i], r["p"][i]), "T1 %.1f" % ref["T"][i],
               "steps gpu/or", gpu["nsteps"][i], ref["nsteps"][i], "margin %.2e" % ref["margin"][i],
               "cond %.2e %.2e" % (cond[0][i], cond[1][i]))
-    res = compare(gpu, ref, cond=cond)
+    # rtol-level bound for the ill-conditioned class, tightened to 1e-6 (measured on
+    # GB300: 9.0e-8 on T, 1.5e-7 on Y)
+    res = compare(gpu, ref, cond=cond, loose_T=1e-6, loose_Y=1e-6)
     print(res)
-    assert res["strict"] > 0.25 * res["n"]
+    # the loose class (ill-conditioned plus knife-edge cells) is bounded at the measured
+    # share plus margin: 2797 of 4096 cells (68.3 %) on GB300
+    loose = res["edge"] + res["ill_conditioned"]
+    assert loose <= 0.72 * res["n"], res
+    assert res["strict"] + loose == res["n"]
 
 
 @pytest.mark.parametrize("n,ld", [(1, 1), (31, 40), (33, 33), (127, 200), (129, 129), (1000, 1003)])
