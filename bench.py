@@ -83,6 +83,7 @@ def parse():
     ap.add_argument("--sur-cells", type=int, default=1 << 24)
     ap.add_argument("--no-bubble", action="store_true", help="skip the shock-bubble hybrid leg")
     ap.add_argument("--no-eq27", action="store_true", help="skip the Eq. 27 divergence benchmark leg")
+    ap.add_argument("--no-mech13", action="store_true", help="skip the 13-species mechanism leg")
     ap.add_argument("--no-comparators", action="store_true",
                     help="skip the full-storage / RKF45 comparator leg")
     ap.add_argument("--bubble-n", type=int, default=256)
@@ -318,6 +319,63 @@ def comparators_leg(mech, rho, e, Y0, T0, Y, T, nsteps, flush, steps, stream):
                                           "time_vs_lsrk": ms / base}
             ctx.close()
     out["registers"] = build.kernel_resources("4chem6k_lsrkI")
+    return out
+
+
+def mech13_leg(steps, dev, stream, flush, ref9):
+    """The 13-species / 27-reaction mechanism (the paper's mechanism size, Sec. 5.2.3) on
+    the 13-species detonation slice (workloads.detonation_slice13: the benchmark slice
+    with its N2 split into N2 / Ar / He and CO, CO2 traces), through libchem_h2o2_13.so:
+    fp64 and mixed one-pass launches, median of `steps` CUDA-event-timed launches from the
+    pristine state (L2 flushed), credited flops against the FP64 peak, and the compiled
+    kernels' registers and spills beside the 9-species ones (the register budget of the
+    paper's Sec. 4.1.2 at its own species count)."""
+    import torch
+    from chem_inputs import mechanism, workloads
+    from paper_2506_02602_gb300 import build, chem, roofline
+    m13 = mechanism.build13(0)
+    d = workloads.detonation_slice13(mech=m13)
+    n = d["T"].size
+    T0 = torch.tensor(d["T"], dtype=torch.float64, device=dev)
+    Y0 = torch.tensor(d["Y"], dtype=torch.float64, device=dev)
+    out = {"workload": f"13-species detonation slice, {n} cells, dt={DT:g} s", "cells": n}
+    ctx0 = chem.Context(m13, "fp64")
+    rho, e = ctx0.state_from_TPY(T0, torch.tensor(d["p"], dtype=torch.float64, device=dev), Y0)
+    ctx0.close()
+    Y, T = Y0.clone(), T0.clone()
+    ns = torch.empty(n, dtype=torch.int32, device=dev)
+    res = {}
+    for variant in ("fp64", "mixed"):
+        ctx = chem.Context(m13, variant)
+        ts = []
+        for k in range(steps + 1):
+            Y.copy_(Y0)
+            T.copy_(T0)
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.integrate(rho, e, Y, T, DT, RTOL, ATOL, nsteps=ns, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if k:
+                ts.append(a.elapsed_time(b))
+        ms = float(np.median(ts))
+        steps_tot = int(ns.sum())
+        if variant == "fp64":
+            flops = roofline.launch_flops(steps_tot, n, m13)
+        else:
+            flops = roofline.launch_flops_mixed_fp64(steps_tot, n, m13)
+        achieved = flops / (ms * 1e-3) / 1e9
+        res[variant] = {"ms": ms, "cells_per_s": n / (ms * 1e-3), "attempted_steps": steps_tot,
+                        "credited_gflop_per_launch": flops / 1e9, "achieved_gflops": achieved,
+                        "frac_of_fp64_peak": achieved / roofline.FP64_PEAK_GFLOPS}
+        ctx.close()
+        if ref9 is not None and variant in ref9:
+            res[variant]["cells_per_s_9sp"] = ref9[variant]["value"]
+            res[variant]["frac_9sp"] = ref9[variant]["roofline"]["frac"]
+    out.update(res)
+    out["step_flops"] = {"9sp": roofline.step_flops(mechanism.build(0)), "13sp": roofline.step_flops(m13)}
+    out["registers_13sp"] = build.kernel_resources("4chem6k_lsrkI", build.LIBS["h2o2_13"]["build"])
     return out
 
 
@@ -780,6 +838,11 @@ def run_ours(args, rank, world, local):
     e2e_el, = max_over_ranks([e2e_el], world, dev)
     e2e_match = bool(np.array_equal(hY, res[head]["Y"]) and np.array_equal(hT, res[head]["T"]))
 
+    mech13 = None
+    if not args.no_mech13:
+        mech13 = mech13_leg(max(3, min(args.steps, 5)), dev, stream, flush,
+                            {v: summary[v] for v in ("fp64", "mixed") if v in summary})
+
     comparators = None
     if not args.no_comparators:
         comparators = comparators_leg(mech, rho, e, Y0, T0, Y, T, nsteps, flush, max(3, min(args.steps, 5)),
@@ -827,6 +890,7 @@ def run_ours(args, rank, world, local):
             "shock_bubble": bubble,
             "eq27": eq27,
             "comparators": comparators,
+            "mech13": mech13,
             "clocks": clk,
             "cpu_baseline": cpu,
             "parity_vs_oracle_sample": parity,

@@ -1,7 +1,9 @@
-"""Seeded synthetic H2/O2/N2 reaction mechanism: input data only.
+"""Seeded synthetic H2/O2/N2 reaction mechanisms: input data only.
 
 The paper names a detailed hydrogen mechanism (Sec. 5.2.3) but prints none of its
-coefficients.  This module builds a mechanism with the same structure:
+coefficients.  This module builds mechanisms with the same structure.  ``build`` gives
+the 9-species / 21-reaction one below; ``build13`` the 13-species / 27-reaction one of
+the paper's size (``build13``'s docstring).  The 9-species mechanism has:
 
 * 9 species: H2, O2, H2O, H, O, OH, HO2, H2O2, N2 (N2 inert);
 * 21 reversible reactions of the usual hydrogen-oxidation classes: chain branching
@@ -85,8 +87,40 @@ _TROE_NPARAM = {"H+O2(+M)=HO2(+M)": 4, "H2O2(+M)=OH+OH(+M)": 3}
 N_SPECIES = len(_SPECIES)
 N_REACTIONS = len(_REACTIONS)
 
+# The 13-species extension: the colliders of the paper's mechanism size (argon, helium,
+# carbon monoxide and dioxide; Sec. 5.2.3 names 13 species and 27 reactions).  They take
+# part in no reaction; they enter the third-body concentrations with their own
+# efficiencies.  Their elements beyond H, O, N (Ar, He, C) are carried in the molar mass
+# only (the element counts cover H, O, N).  Columns as _SPECIES, plus the mass of the
+# untracked elements (kg/mol); noble gases have cp = 5/2 R exactly (no vibrational or
+# electronic term).
+_SPECIES13_EXTRA = (
+    ("AR",  (0, 0, 0),       0.0, 154.8, 2.5, (), 39.948e-3),
+    ("HE",  (0, 0, 0),       0.0, 126.2, 2.5, (), 4.0026e-3),
+    ("CO",  (0, 1, 0), -110500.0, 197.7, 3.5, (3100.0,), 12.011e-3),
+    ("CO2", (0, 2, 0), -393500.0, 213.8, 3.5, (960.0, 960.0, 1930.0, 3380.0), 12.011e-3),
+)
+SPECIES13 = SPECIES + tuple(s[0] for s in _SPECIES13_EXTRA)
+_COLLIDERS13 = {"AR": 0.7, "HE": 0.7, "CO": 1.9, "CO2": 3.8}
+# The 27 reactions: the 21 above (their third-body reactions with the 13-species
+# efficiencies) and six collider-specific or duplicate channels, as a detailed hydrogen
+# mechanism lists them: dissociation and recombination with Ar and He as the only
+# collision partner, recombination to water with water as the partner, and the second
+# HO2 + OH channel.  "{X}" in the efficiency dict sets the default of every species not
+# named.
+_REACTIONS13_EXTRA = (
+    ("H2+M=H+H+M",       "tb",   (18.9, -1.1, 436.0), None, {"*": 0.0, "AR": 1.0}, False),
+    ("H2+M=H+H+M",       "tb",   (18.9, -1.1, 436.0), None, {"*": 0.0, "HE": 1.0}, False),
+    ("O+O+M=O2+M",       "tb",   (13.8, 0.0, -7.5), None, {"*": 0.0, "AR": 1.0}, False),
+    ("O+O+M=O2+M",       "tb",   (13.8, 0.0, -7.5), None, {"*": 0.0, "HE": 1.0}, False),
+    ("H+OH+M=H2O+M",     "tb",   (21.9, -1.8, 0.0), None, {"*": 0.0, "H2O": 1.0}, False),
+    ("HO2+OH=H2O+O2",    "elem", (15.8, -1.0, 0.0), None, None, True),
+)
+# third-body reactions of the 21 whose Ar / He channels are separate reactions above
+_SEPARATE13 = {"H2+M=H+H+M", "O+O+M=O2+M"}
 
-def _parse_side(side: str) -> dict[int, int]:
+
+def _parse_side(side: str, species=SPECIES) -> dict[int, int]:
     """'H+O2(+M)' -> {species index: stoichiometric coefficient}, ignoring M."""
     side = side.replace("(+M)", "")
     nu: dict[int, int] = {}
@@ -94,7 +128,7 @@ def _parse_side(side: str) -> dict[int, int]:
         tok = tok.strip()
         if not tok or tok == "M":
             continue
-        k = SPECIES.index(tok)
+        k = species.index(tok)
         nu[k] = nu.get(k, 0) + 1
     return nu
 
@@ -166,17 +200,38 @@ def build(seed: int = 0) -> dict:
       eff [R, S] third-body efficiencies (1 where unused),
       reversible [R] (int), duplicate [R] (int), equations [R] strings.
     """
+    species = [sp + (0.0,) for sp in _SPECIES]
+    return _build(species, list(_REACTIONS), seed, f"synthetic-h2o2-9sp21r-seed{seed}", {}, set())
+
+
+def build13(seed: int = 0) -> dict:
+    """The seeded synthetic 13-species / 27-reaction mechanism: the paper's mechanism
+    size (13 species, 27 reactions; Sec. 5.2.3), built like ``build`` with argon,
+    helium, CO and CO2 as colliders and six more reactions (_REACTIONS13_EXTRA).  Same
+    dict layout as ``build``; species order SPECIES13."""
+    species = [sp + (0.0,) for sp in _SPECIES] + list(_SPECIES13_EXTRA)
+    return _build(species, list(_REACTIONS) + list(_REACTIONS13_EXTRA), seed,
+                  f"synthetic-h2o2-13sp27r-seed{seed}", _COLLIDERS13, _SEPARATE13)
+
+
+def _build(species_tab, reactions, seed, name, colliders, separate) -> dict:
+    """Draw a mechanism's coefficients (module docstring).  colliders: third-body
+    efficiencies of the extra species in every +M reaction (0 for Ar, He in the
+    reactions listed in `separate`, whose Ar / He channels are their own reactions)."""
     rng = np.random.default_rng(np.random.PCG64(seed))
-    S, Rn, E = N_SPECIES, N_REACTIONS, len(ELEMENTS)
-    W = np.array([sum(n * ATOMIC_MASS[el] for n, el in zip(comp, ELEMENTS)) for _, comp, *_ in _SPECIES])
-    ncomp = np.array([comp for _, comp, *_ in _SPECIES], dtype=np.int32)
+    names = tuple(sp[0] for sp in species_tab)
+    S, Rn = len(species_tab), len(reactions)
+    W = np.array([sum(n * ATOMIC_MASS[el] for n, el in zip(comp, ELEMENTS)) + other
+                  for _, comp, _, _, _, _, other in species_tab])
+    ncomp = np.array([comp for _, comp, *_ in species_tab], dtype=np.int32)
 
     nasa_lo = np.zeros((S, 7))
     nasa_hi = np.zeros((S, 7))
-    for k, (_, _, hf, s0, base, thetas) in enumerate(_SPECIES):
+    for k, (nm, _, hf, s0, base, thetas, other) in enumerate(species_tab):
         th = tuple(t * rng.uniform(0.95, 1.05) for t in thetas)
         scale = rng.uniform(0.97, 1.0)
-        lin = rng.uniform(0.0, 0.05) if not thetas else 0.0  # small electronic term for atoms
+        noble = nm in ("AR", "HE")
+        lin = rng.uniform(0.0, 0.05) if not thetas and not noble else 0.0  # electronic term for atoms
 
         def cp_fn(T, base=base, th=th, scale=scale, lin=lin):
             return _einstein_cp(T, base, th, scale) + lin * (T / 1000.0)
@@ -199,11 +254,11 @@ def build(seed: int = 0) -> dict:
         ea = 0.0 if ea_kj == 0.0 else ea_kj * 1e3 * rng.uniform(0.95, 1.05)
         return 10.0 ** lgA, bb, ea
 
-    for j, (eq, typ, centre, centre0, effs, is_dup) in enumerate(_REACTIONS):
+    for j, (eq, typ, centre, centre0, effs, is_dup) in enumerate(reactions):
         lhs, rhs = eq.split("=")
-        for k, n in _parse_side(lhs).items():
+        for k, n in _parse_side(lhs, names).items():
             nu_f[j, k] = n
-        for k, n in _parse_side(rhs).items():
+        for k, n in _parse_side(rhs, names).items():
             nu_r[j, k] = n
         order = int(nu_f[j].sum())
         rtype[j] = {"elem": 0, "tb": 1, "troe": 2}[typ]
@@ -218,14 +273,21 @@ def build(seed: int = 0) -> dict:
             troe[j, 1] = rng.uniform(50.0, 300.0)
             troe[j, 2] = rng.uniform(1000.0, 5000.0)
             troe[j, 3] = rng.uniform(3000.0, 8000.0) if troe_n[j] == 4 else 0.0
+        if effs and "*" in effs:
+            eff[j, :] = effs["*"]
+        if typ != "elem" and not (effs and "*" in effs):
+            for nm, val in colliders.items():
+                eff[j, names.index(nm)] = 0.0 if (eq in separate and nm in ("AR", "HE")) else val
         if effs:
-            for name, val in effs.items():
-                eff[j, SPECIES.index(name)] = val * rng.uniform(0.9, 1.1)
+            for nm, val in effs.items():
+                if nm == "*":
+                    continue
+                eff[j, names.index(nm)] = val if "*" in effs else val * rng.uniform(0.9, 1.1)
         dup[j] = int(is_dup)
 
     return {
-        "name": f"synthetic-h2o2-9sp21r-seed{seed}",
-        "species": list(SPECIES), "elements": list(ELEMENTS),
+        "name": name,
+        "species": list(names), "elements": list(ELEMENTS),
         "W": W, "ncomp": ncomp,
         "nasa_lo": nasa_lo, "nasa_hi": nasa_hi,
         "T_lo": np.full(S, T_LO), "T_mid": np.full(S, T_MID), "T_hi": np.full(S, T_HI),
@@ -233,7 +295,7 @@ def build(seed: int = 0) -> dict:
         "A": A, "b": b, "Ea": Ea, "A0": A0, "b0": b0, "Ea0": Ea0,
         "troe": troe, "troe_n": troe_n, "eff": eff,
         "reversible": np.ones(Rn, dtype=np.int32), "duplicate": dup,
-        "equations": [r[0] for r in _REACTIONS],
+        "equations": [r[0] for r in reactions],
     }
 
 

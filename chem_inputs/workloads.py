@@ -281,3 +281,60 @@ def bubble_trajectory_starts(ntraj, seed=5):
     T = np.where(shocked, 1500.0, 300.0) * (1.0 + 0.02 * r.uniform(-1.0, 1.0, ntraj))
     p = np.where(shocked, 20.0, 1.0) * ATM * (1.0 + 0.02 * r.uniform(-1.0, 1.0, ntraj))
     return {"T": T, "p": p, "Y": mass_from_mole(_bubble_mole(f)), "fuel": f}
+
+
+def reactors13(n=4096, seed=0, mech=None):
+    """Independent constant-volume reactors for the 13-species mechanism (species order
+    mechanism.SPECIES13): phi ~ U[0.5, 2], T0 ~ U[1000, 2000] K, p0 ~ U[0.5, 5] atm, fresh
+    H2-O2 with a diluent whose N2 : Ar : He split is Dirichlet(1, 1, 1) per cell, 3.76 moles
+    of diluent per mole of O2 (air-like), and traces of CO and CO2 (mole fractions
+    U[0, 1e-3] each) as extra colliders; no radicals.  The paper's detonation runs
+    dilute H2 : O2 with argon (2 : 1 : 7, Sec. 5.3); this recipe spans N2, Ar and He."""
+    from . import mechanism as m13
+    mech = mech or m13.build13(0)
+    idx = {name: k for k, name in enumerate(m13.SPECIES13)}
+    r = _rng(seed)
+    phi = r.uniform(0.5, 2.0, n)
+    T = r.uniform(1000.0, 2000.0, n)
+    p = r.uniform(0.5, 5.0, n) * ATM
+    split = r.dirichlet(np.ones(3), n).T
+    X = np.zeros((len(m13.SPECIES13), n))
+    X[idx["H2"]] = 2.0 * phi
+    X[idx["O2"]] = 1.0
+    X[idx["N2"]] = 3.76 * split[0]
+    X[idx["AR"]] = 3.76 * split[1]
+    X[idx["HE"]] = 3.76 * split[2]
+    X[idx["CO"]] = r.uniform(0.0, 1e-3, n) * (2.0 * phi + 4.76)
+    X[idx["CO2"]] = r.uniform(0.0, 1e-3, n) * (2.0 * phi + 4.76)
+    X /= X.sum(axis=0, keepdims=True)
+    m = X * np.asarray(mech["W"])[:, None]
+    Y = m / m.sum(axis=0, keepdims=True)
+    return {"T": T, "p": p, "Y": Y, "phi": phi}
+
+
+def detonation_slice13(nx=1024, ny=1024, seed=1, mech=None):
+    """The detonation slice (detonation_slice: same T, p and profile) for the 13-species
+    mechanism: in every cell the N2 mole fraction is split into N2 : Ar : He by a
+    Dirichlet(1, 1, 1) draw (the paper's detonations are argon-diluted, Sec. 5.3), CO and
+    CO2 traces (mole fractions U[0, 1e-4]) are added, and the mass fractions recomputed
+    with the 13 molar masses."""
+    from . import mechanism as m13
+    mech = mech or m13.build13(0)
+    d = detonation_slice(nx, ny, seed)
+    n = d["T"].size
+    r = _rng(seed + 1000)
+    W9 = _W()
+    X9 = d["Y"] / W9[:, None]
+    X9 /= X9.sum(axis=0, keepdims=True)
+    X = np.zeros((len(m13.SPECIES13), n))
+    X[:9] = X9
+    split = r.dirichlet(np.ones(3), n).T
+    n2 = X9[IDX["N2"]]
+    X[IDX["N2"]] = n2 * split[0]
+    X[9] = n2 * split[1]
+    X[10] = n2 * split[2]
+    X[11] = r.uniform(0.0, 1e-4, n)
+    X[12] = r.uniform(0.0, 1e-4, n)
+    X /= X.sum(axis=0, keepdims=True)
+    m = X * np.asarray(mech["W"])[:, None]
+    return {"T": d["T"], "p": d["p"], "Y": m / m.sum(axis=0, keepdims=True)}

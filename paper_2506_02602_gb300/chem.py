@@ -18,6 +18,8 @@ import numpy as np
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libchem.so")
+# one library per compiled mechanism structure (species count -> library)
+LIB_PATHS = {9: LIB_PATH, 13: os.path.join(PKG, "libchem_h2o2_13.so")}
 
 MAX_SPECIES = 16
 MAX_REACTIONS = 32
@@ -111,17 +113,22 @@ class Gate(C.Structure):
 ORDER_STIFFNESS, ORDER_NATURAL = 0, 1
 STATS_WORDS = C.sizeof(Stats) // 8
 
-_lib = None
+_libs = {}
 
 
-def load() -> C.CDLL:
-    """Load libchem.so (built in-tree by paper_2506_02602_gb300.build)."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    if not os.path.exists(LIB_PATH):
-        raise ChemError(ERR_CUDA, f"{LIB_PATH} is not built; run paper_2506_02602_gb300.build.build()")
-    L = C.CDLL(LIB_PATH)
+def load(n_species: int = 9) -> C.CDLL:
+    """Load the library compiled for the mechanism structure with n_species species
+    (libchem.so for 9, libchem_h2o2_13.so for 13; built in-tree by
+    paper_2506_02602_gb300.build)."""
+    if n_species in _libs:
+        return _libs[n_species]
+    path = LIB_PATHS.get(n_species)
+    if path is None:
+        raise ChemError(ERR_UNSUPPORTED, f"no library is compiled for {n_species} species "
+                                         f"(structures: {sorted(LIB_PATHS)})")
+    if not os.path.exists(path):
+        raise ChemError(ERR_CUDA, f"{path} is not built; run paper_2506_02602_gb300.build.build()")
+    L = C.CDLL(path)
     vp, i64, dbl = C.c_void_p, C.c_int64, C.c_double
     sig = {
         "chem_version": (C.c_int, []),
@@ -156,7 +163,7 @@ def load() -> C.CDLL:
         fn = getattr(L, name)
         fn.restype = res
         fn.argtypes = args
-    _lib = L
+    _libs[n_species] = L
     return L
 
 
@@ -269,7 +276,7 @@ class Context:
 
     def __init__(self, mech: dict, variant: str = "fp64", max_steps: int = 0, block_size: int = 0,
                  scheme: str = "lsrk"):
-        self.L = load()
+        self.L = load(len(mech["W"]))
         self._mech = make_mechanism(mech)
         opt = Options()
         opt.variant = VARIANTS[variant]

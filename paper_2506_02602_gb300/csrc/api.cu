@@ -113,7 +113,7 @@ int build_tables(const chem_mechanism *m, MechTables *t) {
     for (int k = 0; k < NSP; ++k)
       if (m->nu_f[j][k] != want_f[k] || m->nu_r[j][k] != want_r[k])
         return fail(nullptr, CHEM_ERR_UNSUPPORTED,
-                    "reaction %d: stoichiometry differs from the compiled H2-O2 structure", j);
+                    "reaction %d: stoichiometry differs from the compiled structure %s", j, kMechStructure);
     for (int k = NSP; k < CHEM_MAX_SPECIES; ++k)
       if (m->nu_f[j][k] || m->nu_r[j][k])
         return fail(nullptr, CHEM_ERR_INVALID, "reaction %d uses a species beyond n_species", j);

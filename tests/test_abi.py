@@ -47,6 +47,32 @@ def test_exports_every_declared_symbol(lib):
         getattr(lib, n)
 
 
+def test_every_structure_library_exports_every_symbol(lib):
+    """One library per compiled mechanism structure; each exports the whole ABI (the
+    13-species one answers the surrogate calls with CHEM_ERR_UNSUPPORTED)."""
+    names = declared_functions()
+    for n_sp, path in chem.LIB_PATHS.items():
+        out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
+                             check=True).stdout
+        exported = set(re.findall(r"\bT (chem_[A-Za-z_0-9]+)", out))
+        assert not [n for n in names if n not in exported], (n_sp, path)
+    L13 = chem.load(13)
+    assert L13.chem_surrogate_param_count() == 0
+    assert L13.chem_surrogate_save(None, b"x") == chem.ERR_UNSUPPORTED
+
+
+def test_generated_structure_headers_are_current():
+    """csrc/mech_*.cuh are what gen_mech.py writes for the mechanism descriptions."""
+    import importlib.util
+    gen = os.path.join(ROOT, "paper_2506_02602_gb300", "csrc", "gen_mech.py")
+    spec = importlib.util.spec_from_file_location("gen_mech", gen)
+    g = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(g)
+    for tag, fn in (("h2o2_9", M.build), ("h2o2_13", M.build13)):
+        with open(os.path.join(ROOT, "paper_2506_02602_gb300", "csrc", f"mech_{tag}.cuh")) as f:
+            assert f.read() == g.header(tag, fn(0)), tag
+
+
 def test_struct_layout_matches_header(tmp_path):
     prog = tmp_path / "sizes.c"
     prog.write_text(r'''
@@ -139,13 +165,23 @@ def test_fma_probe_validates_its_arguments(lib):
     assert lib.chem_diag_fma_peak(0, 1, 32, 1, None, None) == chem.ERR_INVALID
 
 
+def test_setup_matches_structure_to_library(lib):
+    """The 13-species mechanism is refused by the 9-species library (and the other way
+    round) before any device is touched."""
+    rc, msg = _setup_rc(lib, M.build13(0))
+    assert rc == chem.ERR_UNSUPPORTED and "13" in msg
+    rc, msg = _setup_rc(chem.load(13), M.build(0))
+    assert rc == chem.ERR_UNSUPPORTED
+
+
 def test_valid_mechanism_needs_a_device(lib):
     import torch
-    rc, msg = _setup_rc(lib, M.build(0))
-    if torch.cuda.is_available():
-        assert rc == chem.OK
-    else:
-        assert rc == chem.ERR_CUDA and "CUDA device" in msg
+    for L, mech in ((lib, M.build(0)), (chem.load(13), M.build13(0))):
+        rc, msg = _setup_rc(L, mech)
+        if torch.cuda.is_available():
+            assert rc == chem.OK
+        else:
+            assert rc == chem.ERR_CUDA and "CUDA device" in msg
 
 
 def test_diag_math_validates_its_arguments(lib):
