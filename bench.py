@@ -67,6 +67,15 @@ METRIC = "chem cells/s per hydro dt at stated error vs FP64; learned+batched vs 
 WORKLOAD = "detonation slice 1024x1024 (1,048,576 cells), H2-air 9 sp / 21 rx, dt=2e-9 s, rtol 1e-6, atol 1e-10"
 
 
+def _jsonable(o):
+    """numpy scalars and arrays in the JSON line as plain numbers and lists."""
+    if isinstance(o, np.generic):
+        return o.item()
+    if isinstance(o, np.ndarray):
+        return o.tolist()
+    raise TypeError(f"not serialisable: {type(o).__name__}")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -229,7 +238,7 @@ def run_reference(args, rank, world):
             "cpu_baseline": res,
             "e2e": {"value": res["value"], "unit": "cells/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    print(json.dumps(line, default=_jsonable), flush=True)
 
 
 # ----------------------------------------------------------------- GPU leg
@@ -749,6 +758,14 @@ def run_ours(args, rank, world, local):
         if v == "hybrid":
             res[v]["fallback_frac"] = float((fbmask != 0).float().mean())
             res[v]["fallback_reasons"] = fallback_reasons(fbmask)
+    # the FMA-pipe probe (chem_diag_fma_peak) under the same clock sampling: measured fp64
+    # and fp32 FMA throughput beside the unit-count peak the roofline divides by
+    f64, _ = chem.fma_peak(0, 152 * 8, 256, 1000, stream=stream)
+    f32, _ = chem.fma_peak(1, 152 * 8, 256, 40000, stream=stream)
+    probe = {"fp64_gflops": f64, "fp32_gflops": f32, "fp64_unit_peak_gflops": roofline.FP64_PEAK_GFLOPS,
+             "fp32_unit_peak_gflops": roofline.FP32_PEAK_GFLOPS,
+             "fp64_probe_over_unit_peak": f64 / roofline.FP64_PEAK_GFLOPS,
+             "launch": "1216 blocks x 256 threads, 8 independent all-register FMA chains per thread"}
     clk = clocks.stop()
 
     ref = res["fp64"]
@@ -892,10 +909,11 @@ def run_ours(args, rank, world, local):
             "comparators": comparators,
             "mech13": mech13,
             "clocks": clk,
+            "fma_probe": probe,
             "cpu_baseline": cpu,
             "parity_vs_oracle_sample": parity,
         }
-        print(json.dumps(line), flush=True)
+        print(json.dumps(line, default=_jsonable), flush=True)
     for c in ctxs.values():
         c.close()
     if world > 1:

@@ -550,9 +550,11 @@ int chem_diag_math(int op, int64_t n, const double *d_x, double *d_y, void *stre
  * Diagnostic: a throughput probe of the FMA pipe the integration kernels are bound by
  * (the denominator of their compute roofline; the paper has no counterpart).  op 0:
  * fp64, 1: fp32.  Launches blocks x threads threads; each runs iters rounds of 32 FMAs
- * (8 independent dependent chains, 4 FMAs each per round), i.e. 64 flops per round, and
- * writes one value to d_sink (device, blocks * threads elements of 8 bytes for op 0, 4
- * for op 1).  The caller times the launch (CUDA events) to get flop/s.  Errors: unknown
+ * (8 independent dependent chains, 4 FMAs each per round, all operands in registers),
+ * i.e. 64 flops per round, and writes one value to d_sink (device, blocks * threads + 2
+ * elements of 8 bytes for op 0, 4 for op 1; the last two hold the chains' coefficients,
+ * written by a one-thread launch first).  The caller times the call (CUDA events around
+ * it) to get flop/s.  Errors: unknown
  * op, blocks < 1, threads not a multiple of 32 in [32, 1024], iters < 1 or NULL d_sink
  * -> CHEM_ERR_INVALID.  Asynchronous on stream.
  */

@@ -185,7 +185,7 @@ def fma_peak(op: int, blocks: int, threads: int, iters: int, reps: int = 5, stre
     """chem_diag_fma_peak timed with CUDA events: returns (best GFLOP/s over reps launches,
     flops per launch).  op 0: fp64, 1: fp32."""
     import torch
-    sink = torch.empty(blocks * threads, dtype=torch.float64 if op == 0 else torch.float32, device="cuda")
+    sink = torch.empty(blocks * threads + 2, dtype=torch.float64 if op == 0 else torch.float32, device="cuda")
     st = torch.cuda.current_stream() if stream is None else stream
     flops = float(blocks) * threads * iters * 64
     best = float("inf")

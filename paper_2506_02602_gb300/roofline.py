@@ -72,7 +72,7 @@ def rhs_flops(mech: dict | None = None) -> int:
         f += (nr - 1) + (1 if nr != npr else 0) + (npr - 1) + 2  # prod G, prod c/G, (RT/p)^dnu, FMA
         f += nr + npr                          # production-rate updates
         if typ != 0:                           # [M]: one FMA per efficiency != 1
-            f += 2 * (nsp if mech is None else sum(abs(x - 1.0) > 0 for x in mech["eff"][j]))
+            f += 2 * (nsp if mech is None else int(sum(abs(x - 1.0) > 0 for x in mech["eff"][j])))
         if typ == 1:
             f += 1
         if typ == 2:
