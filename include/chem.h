@@ -420,7 +420,29 @@ int chem_surrogate_infer(chem_ctx *ctx, const chem_state *state, int64_t ncells,
                          double rtol, double atol, const chem_surrogate_gate *gate, void *stream,
                          uint8_t *d_fallback_mask, chem_stats *d_stats);
 
-/* Write / read the trained network (parameters, Box-Cox lambda, normalisation and
+/*
+ * The surrogate on a ragged batch of boxes (chem_batch as in chem_integrate_batched:
+ * box b owns cells [offset[b], offset[b+1]) and advances them by nsub[b] substeps of
+ * dt[b]; an AMR hierarchy's levels subcycled per Alg. 1), in one call: substep round r
+ * runs the network, projection, temperature, gate and error test of chem_surrogate_infer
+ * on every box with more than r substeps (at its own dt), and all the cells the gate
+ * rejects in that round, from every box, form one queue that one persistent
+ * work-stealing launch integrates (each cell over its box's dt, the context's variant).
+ * Each cell's result equals what per-box, per-substep chem_surrogate_infer calls give.
+ * The call reads the box table to the host once (a synchronisation of stream); the
+ * rounds are then issued asynchronously.  status, nsteps and d_fallback_mask
+ * (nullable, as chem_surrogate_infer) hold each cell's last substep; d_stats
+ * (nullable) counts cell-substeps: cells, status_count[CHEM_CELL_OK] for accepted ones
+ * and the integrator's codes (CHEM_CELL_SURROGATE for its successes) for the rest.
+ * Errors: as chem_surrogate_infer; a box table whose offsets do not run from 0 to
+ * ncells without decreasing, or with dt <= 0 or nsub < 1 -> CHEM_ERR_INVALID.
+ */
+int chem_surrogate_infer_batched(chem_ctx *ctx, const chem_state *state, int64_t ncells,
+                                 const chem_batch *batch, double rtol, double atol,
+                                 const chem_surrogate_gate *gate, void *stream,
+                                 uint8_t *d_fallback_mask, chem_stats *d_stats);
+
+/* Write / read the trained network (parameters, Box-Cox lambda, normalisation and/* Write / read the trained network (parameters, Box-Cox lambda, normalisation and
  * feature ranges) to / from a binary file.  Synchronous.  Errors: I/O -> CHEM_ERR_INVALID;
  * save without a network -> CHEM_ERR_STATE. */
 int chem_surrogate_save(chem_ctx *ctx, const char *path);

@@ -150,6 +150,8 @@ def load(n_species: int = 9) -> C.CDLL:
         "chem_surrogate_train": (C.c_int, [vp, C.POINTER(Pairs), i64, C.POINTER(TrainCfg), vp, vp]),
         "chem_surrogate_infer": (C.c_int, [vp, C.POINTER(State), i64, dbl, dbl, dbl, C.POINTER(Gate),
                                            vp, vp, vp]),
+        "chem_surrogate_infer_batched": (C.c_int, [vp, C.POINTER(State), i64, C.POINTER(Batch), dbl, dbl,
+                                                   C.POINTER(Gate), vp, vp, vp]),
         "chem_surrogate_save": (C.c_int, [vp, C.c_char_p]),
         "chem_surrogate_load": (C.c_int, [vp, C.c_char_p]),
         "chem_surrogate_params": (C.c_int, [vp, vp, vp, i64]),
@@ -442,6 +444,24 @@ class Context:
         self._raise(self.L.chem_surrogate_infer(self.h, C.byref(st), n, float(dt), float(rtol),
                                                 float(atol), C.byref(g), _stream(stream), _ptr(mask),
                                                 _ptr(stats)))
+
+    def surrogate_infer_batched(self, rho, e, Y, T, box_offset, box_dt, box_nsub, rtol=1e-6, atol=1e-10,
+                                status=None, nsteps=None, mask=None, stats=None, gate=None, stream=None):
+        """chem_surrogate_infer_batched: every box's substeps with the surrogate in one call
+        (box arrays as integrate_batched, CUDA tensors); Y, T advanced in place."""
+        import torch
+        n = rho.numel()
+        _check_cells(n, rho, e, Y, T, None, status, nsteps)
+        if box_offset.dtype != torch.int64 or box_nsub.dtype != torch.int32 or box_dt.dtype != torch.float64:
+            raise ChemError(ERR_INVALID, "box_offset int64, box_dt float64, box_nsub int32 expected")
+        st = State(_ptr(rho).value, _ptr(e).value, _ptr(Y).value, Y.stride(0), _ptr(T).value, None,
+                   None if status is None else status.data_ptr(),
+                   None if nsteps is None else nsteps.data_ptr())
+        b = Batch(box_dt.numel(), box_offset.data_ptr(), box_dt.data_ptr(), box_nsub.data_ptr())
+        g = Gate(**(gate or {}))
+        self._raise(self.L.chem_surrogate_infer_batched(self.h, C.byref(st), n, C.byref(b), float(rtol),
+                                                        float(atol), C.byref(g), _stream(stream), _ptr(mask),
+                                                        _ptr(stats)))
 
     def surrogate_save(self, path):
         self._raise(self.L.chem_surrogate_save(self.h, os.fsencode(path)))

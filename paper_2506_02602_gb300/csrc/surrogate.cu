@@ -10,6 +10,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -53,6 +54,9 @@ struct Surrogate {
   int32_t *box_nsub = nullptr;
   unsigned long long *cursor = nullptr;
   int *tc_err = nullptr;  // error word of the tensor-core kernel (a wait ran out)
+  // per-box substep counts of one round of the batched inference (all 1)
+  int32_t *ones = nullptr;
+  int64_t ones_cap = 0;
 };
 
 static void free_surrogate(Surrogate *s) {
@@ -77,6 +81,7 @@ static void free_surrogate(Surrogate *s) {
   cudaFree(s->box_dt);
   cudaFree(s->box_nsub);
   cudaFree(s->cursor);
+  cudaFree(s->ones);
   delete s;
 }
 
@@ -675,25 +680,8 @@ int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
   return CHEM_OK;
 }
 
-int chem_surrogate_infer(chem_ctx *ctx, const chem_state *state, int64_t n, double dt, double rtol,
-                         double atol, const chem_surrogate_gate *gate_in, void *stream,
-                         uint8_t *d_mask, chem_stats *d_stats) {
-  if (!ctx) return CHEM_ERR_INVALID;
-  Surrogate *s = static_cast<Surrogate *>(chem_ctx_sur(ctx));
-  if (!s || !s->ready) return sur_fail(ctx, CHEM_ERR_STATE, "no trained or loaded surrogate");
-  if (chem_ctx_scheme(ctx) != CHEM_SCHEME_LSRK)
-    return sur_fail(ctx, CHEM_ERR_UNSUPPORTED, "the surrogate's fallback runs the two-register scheme only");
-  if (!state || n < 0) return sur_fail(ctx, CHEM_ERR_INVALID, "state is NULL or ncells < 0");
-  if (!(dt > 0.0) || !std::isfinite(dt) || !(rtol > 0.0) || !(atol >= 0.0))
-    return sur_fail(ctx, CHEM_ERR_INVALID, "dt, rtol must be > 0 and atol >= 0");
-  if (n > INT32_MAX) return sur_fail(ctx, CHEM_ERR_INVALID, "at most 2^31-1 cells per call");
-  cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaSuccess;
-  if (d_stats) e = cudaMemsetAsync(d_stats, 0, sizeof(chem_stats), st);
-  if (e != cudaSuccess) return sur_cuda(ctx, e, "clearing stats");
-  if (n == 0) return CHEM_OK;
-  if (!state->d_rho || !state->d_e || !state->d_Y || !state->d_T || state->ldY < n)
-    return sur_fail(ctx, CHEM_ERR_INVALID, "rho, e, Y, T required and ldY >= ncells");
+// Gate defaults of chem_surrogate_gate (zero fields take them).
+static chem_surrogate_gate gate_defaults(const chem_surrogate_gate *gate_in) {
   chem_surrogate_gate g{};
   if (gate_in) g = *gate_in;
   if (g.ood_margin == 0.0f) g.ood_margin = 0.05f;
@@ -702,14 +690,21 @@ int chem_surrogate_infer(chem_ctx *ctx, const chem_state *state, int64_t n, doub
   if (g.max_dT == 0.0f) g.max_dT = 200.0f;
   if (g.err_tol == 0.0f) g.err_tol = 6e-4f;
   if (g.rate_max == 0.0f) g.rate_max = 1.5f;
-  const int64_t chunk = n < kInferChunk ? n : kInferChunk;
-  e = ensure_infer_buffers(s, chunk, n);
-  if (e != cudaSuccess) return sur_cuda(ctx, e, "allocating inference buffers");
+  return g;
+}
+
+// Network, projection, temperature, gate and error test on the cells [first, first + n)
+// of the state over dt, in chunks; accepted cells are written, rejected ones appended to
+// the fallback list (global indices) without resetting its count.
+static cudaError_t infer_range(chem_ctx *ctx, Surrogate *s, const SurrogateConsts &sc,
+                               const chem_state *state, int64_t first, int64_t n, double dt,
+                               uint8_t *d_mask, cudaStream_t st) {
   const MechTables &mt = chem_ctx_tables(ctx);
-  const SurrogateConsts sc = make_consts(s, g, mt);
-  e = cudaMemsetAsync(s->fb_count, 0, sizeof(unsigned int), st);
-  for (int64_t base = 0; base < n && e == cudaSuccess; base += chunk) {
-    const int64_t m = (n - base) < chunk ? (n - base) : chunk;
+  const int64_t chunk = s->chunk_cap;
+  cudaError_t e = cudaSuccess;
+  for (int64_t off = 0; off < n && e == cudaSuccess; off += chunk) {
+    const int64_t base = first + off;
+    const int64_t m = (n - off) < chunk ? (n - off) : chunk;
     e = launch_features(mt, m, state->d_rho + base, state->d_e + base, state->d_Y + base, state->ldY,
                         state->d_T + base, nullptr, dt, nullptr, 0, s->lam, s->dt_power, s->Xraw, nullptr, nullptr,
                         s->Tok, st);
@@ -722,6 +717,47 @@ int chem_surrogate_infer(chem_ctx *ctx, const chem_state *state, int64_t n, doub
                                   state->d_nsteps ? state->d_nsteps + base : nullptr,
                                   d_mask ? d_mask + base : nullptr, s->fb_idx, s->fb_count, base, st);
   }
+  return e;
+}
+
+// Checks shared by the inference entry points; on CHEM_OK *sp is the trained surrogate.
+static int infer_checks(chem_ctx *ctx, const chem_state *state, int64_t n, double rtol, double atol,
+                        Surrogate **sp) {
+  Surrogate *s = static_cast<Surrogate *>(chem_ctx_sur(ctx));
+  if (!s || !s->ready) return sur_fail(ctx, CHEM_ERR_STATE, "no trained or loaded surrogate");
+  if (chem_ctx_scheme(ctx) != CHEM_SCHEME_LSRK)
+    return sur_fail(ctx, CHEM_ERR_UNSUPPORTED, "the surrogate's fallback runs the two-register scheme only");
+  if (!state || n < 0) return sur_fail(ctx, CHEM_ERR_INVALID, "state is NULL or ncells < 0");
+  if (!(rtol > 0.0) || !std::isfinite(rtol) || !(atol >= 0.0) || !std::isfinite(atol))
+    return sur_fail(ctx, CHEM_ERR_INVALID, "rtol must be > 0 and atol >= 0");
+  if (n > INT32_MAX) return sur_fail(ctx, CHEM_ERR_INVALID, "at most 2^31-1 cells per call");
+  if (n > 0 && (!state->d_rho || !state->d_e || !state->d_Y || !state->d_T || state->ldY < n))
+    return sur_fail(ctx, CHEM_ERR_INVALID, "rho, e, Y, T required and ldY >= ncells");
+  *sp = s;
+  return CHEM_OK;
+}
+
+int chem_surrogate_infer(chem_ctx *ctx, const chem_state *state, int64_t n, double dt, double rtol,
+                         double atol, const chem_surrogate_gate *gate_in, void *stream,
+                         uint8_t *d_mask, chem_stats *d_stats) {
+  if (!ctx) return CHEM_ERR_INVALID;
+  Surrogate *s = nullptr;
+  int rc = infer_checks(ctx, state, n, rtol, atol, &s);
+  if (rc) return rc;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return sur_fail(ctx, CHEM_ERR_INVALID, "dt must be > 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (d_stats) e = cudaMemsetAsync(d_stats, 0, sizeof(chem_stats), st);
+  if (e != cudaSuccess) return sur_cuda(ctx, e, "clearing stats");
+  if (n == 0) return CHEM_OK;
+  const chem_surrogate_gate g = gate_defaults(gate_in);
+  const int64_t chunk = n < kInferChunk ? n : kInferChunk;
+  e = ensure_infer_buffers(s, chunk, n);
+  if (e != cudaSuccess) return sur_cuda(ctx, e, "allocating inference buffers");
+  const MechTables &mt = chem_ctx_tables(ctx);
+  const SurrogateConsts sc = make_consts(s, g, mt);
+  e = cudaMemsetAsync(s->fb_count, 0, sizeof(unsigned int), st);
+  if (e == cudaSuccess) e = infer_range(ctx, s, sc, state, 0, n, dt, d_mask, st);
   if (e == cudaSuccess) e = launch_one_box(s->box_off, s->box_dt, s->box_nsub, n, dt, st);
   if (e == cudaSuccess) {
     // the rejected cells: a queue (the fallback list, its length on the device) for the
@@ -734,6 +770,79 @@ int chem_surrogate_infer(chem_ctx *ctx, const chem_state *state, int64_t n, doub
   }
   if (e == cudaSuccess && d_stats) e = launch_surrogate_stats(d_stats, n, s->fb_count, st);
   return e == cudaSuccess ? CHEM_OK : sur_cuda(ctx, e, "surrogate inference");
+}
+
+int chem_surrogate_infer_batched(chem_ctx *ctx, const chem_state *state, int64_t n,
+                                 const chem_batch *batch, double rtol, double atol,
+                                 const chem_surrogate_gate *gate_in, void *stream, uint8_t *d_mask,
+                                 chem_stats *d_stats) {
+  if (!ctx) return CHEM_ERR_INVALID;
+  Surrogate *s = nullptr;
+  int rc = infer_checks(ctx, state, n, rtol, atol, &s);
+  if (rc) return rc;
+  if (!batch || batch->nboxes < 1 || !batch->d_box_offset || !batch->d_box_dt || !batch->d_box_nsub)
+    return sur_fail(ctx, CHEM_ERR_INVALID, "batch needs nboxes >= 1 and its three device arrays");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nb = batch->nboxes;
+  // the box table on the host: the rounds and their cell ranges are sequenced here
+  std::vector<int64_t> off((size_t)nb + 1);
+  std::vector<double> bdt((size_t)nb);
+  std::vector<int32_t> nsub((size_t)nb);
+  cudaError_t e = cudaMemcpyAsync(off.data(), batch->d_box_offset, off.size() * sizeof(int64_t),
+                                  cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(bdt.data(), batch->d_box_dt, bdt.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(nsub.data(), batch->d_box_nsub, nsub.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return sur_cuda(ctx, e, "reading the box table");
+  if (off[0] != 0 || off[(size_t)nb] != n)
+    return sur_fail(ctx, CHEM_ERR_INVALID, "box offsets must start at 0 and end at ncells");
+  int32_t rounds = 0;
+  for (int b = 0; b < nb; ++b) {
+    if (off[(size_t)b + 1] < off[(size_t)b]) return sur_fail(ctx, CHEM_ERR_INVALID, "box offsets must not decrease");
+    if (!(bdt[(size_t)b] > 0.0) || !std::isfinite(bdt[(size_t)b]) || nsub[(size_t)b] < 1)
+      return sur_fail(ctx, CHEM_ERR_INVALID, "box dt must be > 0 and substeps >= 1");
+    rounds = std::max(rounds, nsub[(size_t)b]);
+  }
+  if (d_stats) e = cudaMemsetAsync(d_stats, 0, sizeof(chem_stats), st);
+  if (e != cudaSuccess) return sur_cuda(ctx, e, "clearing stats");
+  if (n == 0) return CHEM_OK;
+  const chem_surrogate_gate g = gate_defaults(gate_in);
+  const int64_t chunk = n < kInferChunk ? n : kInferChunk;
+  e = ensure_infer_buffers(s, chunk, n);
+  if (e == cudaSuccess && nb > s->ones_cap) {
+    cudaFree(s->ones);
+    s->ones = nullptr;
+    s->ones_cap = 0;
+    e = cudaMalloc(&s->ones, (size_t)nb * sizeof(int32_t));
+    if (e == cudaSuccess) s->ones_cap = nb;
+  }
+  if (e == cudaSuccess) e = launch_fill_i32(s->ones, nb, 1, st);
+  if (e != cudaSuccess) return sur_cuda(ctx, e, "allocating inference buffers");
+  const MechTables &mt = chem_ctx_tables(ctx);
+  const SurrogateConsts sc = make_consts(s, g, mt);
+  StepParams p{0.0, rtol, atol, chem_ctx_max_steps(ctx)};
+  for (int32_t r = 0; r < rounds && e == cudaSuccess; ++r) {
+    // round r: every box with more than r substeps advances one substep of its dt; the
+    // cells the gate rejects, from all boxes, form one queue for one persistent launch
+    e = cudaMemsetAsync(s->fb_count, 0, sizeof(unsigned int), st);
+    int64_t active = 0;
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+      const int64_t a0 = off[(size_t)b], m = off[(size_t)b + 1] - a0;
+      if (nsub[(size_t)b] <= r || m == 0) continue;
+      e = infer_range(ctx, s, sc, state, a0, m, bdt[(size_t)b], d_mask, st);
+      active += m;
+    }
+    if (e == cudaSuccess) {
+      BatchArgs a{state->d_rho, state->d_e, state->d_Y, state->ldY, state->d_T, nullptr,
+                  state->d_status, state->d_nsteps, n, batch->d_box_offset, batch->d_box_dt, s->ones, nb,
+                  nullptr, d_stats, s->fb_count, CHEM_CELL_SURROGATE};
+      e = launch_persistent_queue(chem_ctx_variant(ctx), mt, a, p, s->fb_idx, s->cursor, st);
+    }
+    if (e == cudaSuccess && d_stats) e = launch_surrogate_stats_add(d_stats, active, s->fb_count, st);
+  }
+  return e == cudaSuccess ? CHEM_OK : sur_cuda(ctx, e, "batched surrogate inference");
 }
 
 static const char kSurMagic[8] = {'C', 'H', 'E', 'M', 'S', 'U', 'R', '2'};

@@ -89,6 +89,10 @@ cudaError_t launch_mlp_tc(int64_t n, const float *X, const float *norm, const un
 // read): Yout = projection of Yp onto the element mass fractions of Y0 (planes, stride ld).
 cudaError_t launch_project_check(const SurrogateConsts &sc, int64_t n, const double *Y0,
                                  const double *Yp, int64_t ld, double *Yout, cudaStream_t s);
+// Statistics of one substep round of the batched inference (cells and accepted counts).
+cudaError_t launch_surrogate_stats_add(chem_stats *st, int64_t active, const unsigned int *fb_count,
+                                       cudaStream_t s);
+cudaError_t launch_fill_i32(int32_t *a, int64_t n, int32_t v, cudaStream_t s);
 // box_off = {0, n}, box_dt = {dt}, box_nsub = {1}: the fallback's one-box batch.
 cudaError_t launch_one_box(int64_t *box_off, double *box_dt, int32_t *box_nsub, int64_t n, double dt,
                            cudaStream_t s);

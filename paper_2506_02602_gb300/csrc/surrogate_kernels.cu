@@ -391,7 +391,34 @@ __global__ void k_surrogate_stats(chem_stats *st, int64_t n, const unsigned int 
   }
 }
 
+// One substep round of chem_surrogate_infer_batched: the `active` cells of the round not
+// in the fallback list were accepted (the fallback launch counts its own cells).
+__global__ void k_surrogate_stats_add(chem_stats *st, int64_t active, const unsigned int *fb_count) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const int64_t acc = active - (int64_t)*fb_count;
+    st->cells += acc;
+    st->status_count[CHEM_CELL_OK] += acc;
+  }
+}
+
+__global__ void k_fill_i32(int32_t *a, int64_t n, int32_t v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+
 static unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+cudaError_t launch_surrogate_stats_add(chem_stats *st, int64_t active, const unsigned int *fb_count,
+                                       cudaStream_t s) {
+  k_surrogate_stats_add<<<1, 32, 0, s>>>(st, active, fb_count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_i32(int32_t *a, int64_t n, int32_t v, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_fill_i32<<<nblk(n, 256), 256, 0, s>>>(a, n, v);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_surrogate_stats(chem_stats *st, int64_t n, const unsigned int *fb_count,
                                    cudaStream_t s) {

@@ -51,6 +51,10 @@ int chem_surrogate_infer(chem_ctx *ctx, const chem_state *, int64_t, double, dou
                          const chem_surrogate_gate *, void *, uint8_t *, chem_stats *) {
   return no_surrogate(ctx);
 }
+int chem_surrogate_infer_batched(chem_ctx *ctx, const chem_state *, int64_t, const chem_batch *, double,
+                                 double, const chem_surrogate_gate *, void *, uint8_t *, chem_stats *) {
+  return no_surrogate(ctx);
+}
 int chem_surrogate_save(chem_ctx *ctx, const char *) { return no_surrogate(ctx); }
 int chem_surrogate_load(chem_ctx *ctx, const char *) { return no_surrogate(ctx); }
 

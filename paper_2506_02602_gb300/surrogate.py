@@ -182,6 +182,39 @@ def evaluate(ctx_sur, ctx_ref, states, dt, rtol=1e-6, atol=1e-10, gate=None, rep
             "stats": stats.cpu().numpy().tolist()}
 
 
+ERR_TOL_GRID = (3e-4, 4e-4, 5e-4, 6e-4, 8e-4)
+RATE_MAX_GRID = (1.0, 1.5, 2.0)
+
+
+def tune_gate(ctx_sur, ctx_ref, states, dt, bound=1e-3, margin=1.5, rtol=1e-6, atol=1e-10,
+              err_grid=ERR_TOL_GRID, rate_grid=RATE_MAX_GRID):
+    """The error test's thresholds for step dt, chosen on validation states (trajectories
+    neither trained on nor reported): among (err_tol, rate_max) pairs whose largest
+    relative T error over all cells, against the reference integrator, stays within
+    bound / margin, the one with the fewest fallbacks (ties: the smaller err_tol).
+    Returns (gate dict, table of every candidate)."""
+    import torch
+    n = states["T"].numel()
+    dev = states["T"].device
+    Yr, Tr = states["Y"].clone(), states["T"].clone()
+    ctx_ref.integrate(states["rho"], states["e"], Yr, Tr, dt, rtol, atol)
+    mask = torch.empty(n, dtype=torch.uint8, device=dev)
+    table, best = [], None
+    for et in err_grid:
+        for rm in rate_grid:
+            gate = {"err_tol": et, "rate_max": rm}
+            Y, T = states["Y"].clone(), states["T"].clone()
+            ctx_sur.surrogate_infer(states["rho"], states["e"], Y, T, dt, rtol, atol, mask=mask, gate=gate)
+            rel = float(((T - Tr).abs() / Tr).max())
+            fb = float((mask != 0).float().mean())
+            table.append({"err_tol": et, "rate_max": rm, "max_rel_T": rel, "fallback_frac": fb})
+            if rel <= bound / margin and (best is None or fb < best[1] - 1e-12):
+                best = (gate, fb)
+    if best is None:  # nothing meets the bound: the strictest test
+        best = ({"err_tol": min(err_grid), "rate_max": min(rate_grid)}, None)
+    return best[0], table
+
+
 def hybrid_levels(ctx, rho, e, Y, T, box_offset, box_dt, box_nsub, rtol=1e-6, atol=1e-10, gate=None,
                   status=None, nsteps=None, mask=None, stream=None):
     """One hydro step of a level-ordered field with the surrogate: for each box (cells

@@ -2,7 +2,9 @@
 256^3 workload): AMR-like levels with 2^l substeps, the surrogate (trained here on the
 field's own state family) with its error test and the persistent work-stealing
 integrator for the cells it rejects, against plain FP64 batched integration, itself
-checked against the oracle on sampled cells."""
+checked against the oracle on sampled cells.  The one-call batched surrogate
+(chem_surrogate_infer_batched) gives the per-box, per-substep loop's results bit for bit,
+with consistent statistics."""
 import numpy as np
 import pytest
 
@@ -89,3 +91,38 @@ def test_hybrid_against_plain_fp64(setup):
                   for j, el in enumerate(M.ELEMENTS)])
     E = E / E.sum(axis=0, keepdims=True)
     np.testing.assert_allclose(E @ Yh, E @ b["Y"], rtol=0, atol=1e-12)
+
+
+def test_batched_surrogate_equals_per_box_loop(setup):
+    import torch
+    from paper_2506_02602_gb300 import chem, surrogate
+    b, hyb, _ = setup
+    n = b["T"].size
+    dev_rho, dev_e = to_dev(b["rho"]), to_dev(b["e"])
+    Y1, T1 = to_dev(b["Y"]), to_dev(b["T"])
+    st1 = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    m1 = torch.empty(n, dtype=torch.uint8, device="cuda")
+    surrogate.hybrid_levels(hyb, dev_rho, dev_e, Y1, T1, b["box_offset"], b["box_dt"], b["box_nsub"],
+                            status=st1, mask=m1)
+    Y2, T2 = to_dev(b["Y"]), to_dev(b["T"])
+    st2 = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    m2 = torch.empty(n, dtype=torch.uint8, device="cuda")
+    stats = torch.zeros(chem.STATS_WORDS, dtype=torch.int64, device="cuda")
+    hyb.surrogate_infer_batched(dev_rho, dev_e, Y2, T2, torch.tensor(b["box_offset"], device="cuda"),
+                                to_dev(b["box_dt"]), torch.tensor(b["box_nsub"], dtype=torch.int32, device="cuda"),
+                                status=st2, mask=m2, stats=stats)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(Y2.cpu().numpy(), Y1.cpu().numpy())
+    np.testing.assert_array_equal(T2.cpu().numpy(), T1.cpu().numpy())
+    np.testing.assert_array_equal(st2.cpu().numpy(), st1.cpu().numpy())
+    np.testing.assert_array_equal(m2.cpu().numpy(), m1.cpu().numpy())
+    sv = stats.cpu().numpy()
+    subs = int((np.diff(b["box_offset"]) * np.asarray(b["box_nsub"])).sum())
+    assert sv[0] == subs                           # cell-substeps
+    assert sv[5 + 0] + sv[5 + 5] + sv[5 + 1:5 + 5].sum() == subs
+    # a box table that does not cover the cells is refused before any launch
+    bad = torch.tensor(np.asarray(b["box_offset"]) - 1, device="cuda")
+    with pytest.raises(chem.ChemError) as ei:
+        hyb.surrogate_infer_batched(dev_rho, dev_e, Y2, T2, bad, to_dev(b["box_dt"]),
+                                    torch.tensor(b["box_nsub"], dtype=torch.int32, device="cuda"))
+    assert ei.value.code == chem.ERR_INVALID
