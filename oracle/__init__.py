@@ -94,6 +94,11 @@ def lib():
                                               C.c_double, C.c_int32, dp]),
             "oracle_struct_size": (C.c_int32, []),
             "oracle_butcher": (None, [C.c_int32, ip, dp, dp, dp, dp]),
+            "oracle_euler1d_step": (C.c_int32, [mp, C.c_int64, C.c_double, C.c_double, C.c_int32, C.c_int32,
+                                                dp, dp, dp, dp, C.c_int64, dp]),
+            "oracle_euler1d_max_speed": (C.c_double, [mp, C.c_int64, dp, dp, dp, dp, C.c_int64, dp]),
+            "oracle_strang_step": (C.c_int32, [mp, C.c_int64, C.c_double, C.c_double, C.c_int32, C.c_int32,
+                                               C.c_double, C.c_double, dp, dp, dp, dp, C.c_int64, dp, C.c_int32]),
             "oracle_linear_step_scheme": (None, [C.c_int32, C.c_int32, dp, C.c_double, dp, dp]),
             "oracle_quadratic_fixed_scheme": (C.c_double, [C.c_int32, C.c_double, C.c_double,
                                                            C.c_int32, C.c_int32]),
@@ -254,6 +259,38 @@ class Oracle:
                                        _ip(nacc), _dp(margin), _dp(hout), nthreads)
         return {"Y": Y, "T": T, "status": status, "nsteps": nsteps, "naccept": nacc,
                 "margin": margin, "h": hout}
+
+    # 1D reactive Euler (the operator either side of the chemistry) -----------
+    def euler1d_step(self, U, dx, dt, bc=(0, 0)):
+        """One SSP-RK2 MUSCL-HLL step of the 1D Euler equations on the conserved state
+        U = dict(rho, rhou, rhoE [n], rhoY [S, n], T [n]) (copied; returns (rc, new U))."""
+        V = {k: np.array(v, dtype=np.float64, order="C", copy=True) for k, v in U.items()}
+        n = V["rho"].size
+        rc = self.L.oracle_euler1d_step(self._mp, n, dx, dt, int(bc[0]), int(bc[1]), _dp(V["rho"]),
+                                        _dp(V["rhou"]), _dp(V["rhoE"]), _dp(V["rhoY"]), V["rhoY"].shape[1],
+                                        _dp(V["T"]))
+        return rc, V
+
+    def euler1d_max_speed(self, U):
+        V = {k: _f64(v) for k, v in U.items()}
+        return self.L.oracle_euler1d_max_speed(self._mp, V["rho"].size, _dp(V["rho"]), _dp(V["rhou"]),
+                                               _dp(V["rhoE"]), _dp(V["rhoY"]), V["rhoY"].shape[1], _dp(V["T"]))
+
+    def strang_step(self, U, dx, dt, bc=(0, 0), rtol=1e-6, atol=1e-10, nthreads=0):
+        """Chemistry dt/2, Euler dt, chemistry dt/2 (returns (rc, new U))."""
+        V = {k: np.array(v, dtype=np.float64, order="C", copy=True) for k, v in U.items()}
+        n = V["rho"].size
+        rc = self.L.oracle_strang_step(self._mp, n, dx, dt, int(bc[0]), int(bc[1]), rtol, atol, _dp(V["rho"]),
+                                       _dp(V["rhou"]), _dp(V["rhoE"]), _dp(V["rhoY"]), V["rhoY"].shape[1],
+                                       _dp(V["T"]), nthreads)
+        return rc, V
+
+    def conserved_from_prim(self, rho, u, T, Y):
+        """U dict from primitive (rho, u, T, Y [S, n]) with the oracle's thermo."""
+        rho, u, T, Y = _f64(rho), _f64(u), _f64(T), _f64(Y)
+        e = np.array([self.e_mix(Y[:, i], T[i]) for i in range(rho.size)])
+        return {"rho": rho.copy(), "rhou": rho * u, "rhoE": rho * (e + 0.5 * u * u), "rhoY": rho[None, :] * Y,
+                "T": T.copy()}
 
     def chem_fixed(self, rho, e, Y, T, h, nsteps):
         Y = np.array(Y, dtype=np.float64, copy=True)

@@ -33,6 +33,7 @@
  * Units are SI: kg/mol, J/mol, mol/m^3, Pa, s.
  */
 #include <math.h>
+#include <stdlib.h>
 #include <stdint.h>
 #include <string.h>
 #ifdef _OPENMP
@@ -647,6 +648,238 @@ int32_t oracle_chem_fixed(const omech *m, double rho, double e, double *Y, doubl
     T_trace[s] = T;
   }
   return 0;
+}
+
+/* ------------------------------------------- 1D reactive Euler and Strang splitting */
+
+/* The operator on either side of the chemistry in the paper's split scheme (Sec. 2.2.1,
+ * Strang splitting of the reactive Euler equations, Eq. 14 without transport): a
+ * minimal 1D finite-volume step for the conserved state U = (rho, rho u, rho E,
+ * rho Y_k) of n cells of width dx.  Second-order MUSCL reconstruction of the primitive
+ * variables (rho, u, p, Y_k) with minmod-limited slopes, the HLL flux with Davis wave
+ * speeds, and the two-stage SSP Runge-Kutta (Heun) step in time.  A face whose
+ * reconstructed density or pressure is not positive falls back to the cell averages.
+ * Boundaries: 0 transmissive (zero gradient), 1 reflecting wall.  Thermo of Eq. 10:
+ * p = rho R_u T sum_k Y_k / W_k with T from e = E - u^2/2 by Newton (oracle_T_from_e). */
+
+typedef struct { double rho, u, p, Y[OR_MAXSP], T; } prim1d;
+
+static double mix_inv_w(const omech *m, const double *Y) {
+  double s = 0.0;
+  for (int k = 0; k < m->nsp; ++k) s += Y[k] / m->W[k];
+  return s;
+}
+
+/* Sound speed squared gamma p / rho with gamma = cp / cv of the mixture at T. */
+static double sound2(const omech *m, const prim1d *w) {
+  double cv = oracle_cv_mix(m, w->Y, w->T);
+  double cp = cv + R_U * mix_inv_w(m, w->Y);
+  return cp / cv * w->p / w->rho;
+}
+
+/* Primitive state of cell i from the conserved planes; T starts from Tguess.  Returns 0
+ * or 3 when no temperature root exists. */
+static int cons_to_prim(const omech *m, const double *rho, const double *rhou, const double *rhoE,
+                        const double *rhoY, int64_t ld, int64_t i, double Tguess, prim1d *w) {
+  w->rho = rho[i];
+  w->u = rhou[i] / rho[i];
+  for (int k = 0; k < m->nsp; ++k) w->Y[k] = rhoY[k * ld + i] / rho[i];
+  double e = rhoE[i] / rho[i] - 0.5 * w->u * w->u;
+  if (oracle_T_from_e(m, w->Y, e, Tguess, &w->T, NULL)) return 3;
+  w->p = rho[i] * R_U * w->T * mix_inv_w(m, w->Y);
+  return 0;
+}
+
+/* Physical flux of a primitive state (T known from p, rho, Y). */
+static void euler_flux(const omech *m, const prim1d *w, double *F) {
+  double e = oracle_e_mix(m, w->Y, w->T);
+  double E = e + 0.5 * w->u * w->u;
+  F[0] = w->rho * w->u;
+  F[1] = w->rho * w->u * w->u + w->p;
+  F[2] = (w->rho * E + w->p) * w->u;
+  for (int k = 0; k < m->nsp; ++k) F[3 + k] = w->rho * w->Y[k] * w->u;
+}
+
+static void prim_to_cons(const omech *m, const prim1d *w, double *U) {
+  double e = oracle_e_mix(m, w->Y, w->T);
+  U[0] = w->rho;
+  U[1] = w->rho * w->u;
+  U[2] = w->rho * (e + 0.5 * w->u * w->u);
+  for (int k = 0; k < m->nsp; ++k) U[3 + k] = w->rho * w->Y[k];
+}
+
+static double minmod(double a, double b) {
+  if (a * b <= 0.0) return 0.0;
+  return fabs(a) < fabs(b) ? a : b;
+}
+
+/* Ghost or interior primitive state of index j in [-2, n+1]. */
+static prim1d ghost(const prim1d *W, int64_t n, int64_t j, int bcl, int bcr) {
+  prim1d g;
+  if (j < 0) {
+    g = W[-j - 1];                       /* mirror: -1 -> 0, -2 -> 1 */
+    if (bcl == 0) g = W[0];
+    else g.u = -g.u;
+  } else if (j >= n) {
+    g = W[2 * n - 1 - j];                /* n -> n-1, n+1 -> n-2 */
+    if (bcr == 0) g = W[n - 1];
+    else g.u = -g.u;
+  } else {
+    g = W[j];
+  }
+  return g;
+}
+
+/* HLL flux at the face between reconstructed states L and R (primitive; T set). */
+static void hll(const omech *m, const prim1d *L, const prim1d *R, double *F) {
+  int nv = 3 + m->nsp;
+  double FL[3 + OR_MAXSP], FR[3 + OR_MAXSP], UL[3 + OR_MAXSP], UR[3 + OR_MAXSP];
+  double cL = sqrt(sound2(m, L)), cR = sqrt(sound2(m, R));
+  double SL = fmin(L->u - cL, R->u - cR), SR = fmax(L->u + cL, R->u + cR);
+  euler_flux(m, L, FL);
+  euler_flux(m, R, FR);
+  if (SL >= 0.0) { for (int v = 0; v < nv; ++v) F[v] = FL[v]; return; }
+  if (SR <= 0.0) { for (int v = 0; v < nv; ++v) F[v] = FR[v]; return; }
+  prim_to_cons(m, L, UL);
+  prim_to_cons(m, R, UR);
+  for (int v = 0; v < nv; ++v)
+    F[v] = (SR * FL[v] - SL * FR[v] + SL * SR * (UR[v] - UL[v])) / (SR - SL);
+}
+
+/* Reconstructed face state from cell state c with slope s, offset +-1/2; T from p. */
+static prim1d face_state(const omech *m, const prim1d *c, const prim1d *s, double half) {
+  prim1d f;
+  f.rho = c->rho + half * s->rho;
+  f.u = c->u + half * s->u;
+  f.p = c->p + half * s->p;
+  for (int k = 0; k < m->nsp; ++k) f.Y[k] = c->Y[k] + half * s->Y[k];
+  f.T = f.p / (f.rho * R_U * mix_inv_w(m, f.Y));
+  return f;
+}
+
+static prim1d slope(const omech *m, const prim1d *a, const prim1d *b, const prim1d *c) {
+  prim1d s;
+  s.rho = minmod(b->rho - a->rho, c->rho - b->rho);
+  s.u = minmod(b->u - a->u, c->u - b->u);
+  s.p = minmod(b->p - a->p, c->p - b->p);
+  for (int k = 0; k < m->nsp; ++k) s.Y[k] = minmod(b->Y[k] - a->Y[k], c->Y[k] - b->Y[k]);
+  s.T = 0.0;
+  return s;
+}
+
+/* dU/dt of every cell (the flux divergence) from the primitive states W. */
+static void euler_rhs(const omech *m, int64_t n, double dx, int bcl, int bcr, const prim1d *W, double *dU) {
+  int nv = 3 + m->nsp;
+  double Fr[3 + OR_MAXSP];
+  for (int64_t f = 0; f <= n; ++f) {     /* face f between cells f-1 and f */
+    prim1d a = ghost(W, n, f - 2, bcl, bcr), b = ghost(W, n, f - 1, bcl, bcr);
+    prim1d c = ghost(W, n, f, bcl, bcr), d = ghost(W, n, f + 1, bcl, bcr);
+    prim1d sb = slope(m, &a, &b, &c), sc = slope(m, &b, &c, &d);
+    prim1d L = face_state(m, &b, &sb, 0.5), R = face_state(m, &c, &sc, -0.5);
+    if (!(L.rho > 0.0 && L.p > 0.0 && R.rho > 0.0 && R.p > 0.0)) { L = b; R = c; }
+    hll(m, &L, &R, Fr);
+    if (f > 0)
+      for (int v = 0; v < nv; ++v) dU[(f - 1) * nv + v] -= Fr[v] / dx;
+    if (f < n)
+      for (int v = 0; v < nv; ++v) dU[f * nv + v] = Fr[v] / dx;
+  }
+}
+
+/* One SSP-RK2 step of the 1D Euler equations over dt (planes updated in place; T: in =
+ * Newton start, out = temperature of the new state).  Returns 0, or 3 when a
+ * temperature solve failed (state unchanged). */
+int32_t oracle_euler1d_step(const omech *m, int64_t n, double dx, double dt, int32_t bcl, int32_t bcr,
+                            double *rho, double *rhou, double *rhoE, double *rhoY, int64_t ld, double *T) {
+  int nv = 3 + m->nsp;
+  prim1d *W = (prim1d *)malloc(sizeof(prim1d) * (size_t)n);
+  double *U0 = (double *)malloc(sizeof(double) * (size_t)(n * nv));
+  double *U1 = (double *)malloc(sizeof(double) * (size_t)(n * nv));
+  double *dU = (double *)malloc(sizeof(double) * (size_t)(n * nv));
+  int32_t rc = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    U0[i * nv + 0] = rho[i]; U0[i * nv + 1] = rhou[i]; U0[i * nv + 2] = rhoE[i];
+    for (int k = 0; k < m->nsp; ++k) U0[i * nv + 3 + k] = rhoY[k * ld + i];
+  }
+  double *Tw = (double *)malloc(sizeof(double) * (size_t)n);
+  for (int64_t i = 0; i < n; ++i) Tw[i] = T[i];
+  for (int stage = 0; stage < 2 && rc == 0; ++stage) {
+    const double *U = stage == 0 ? U0 : U1;
+    for (int64_t i = 0; i < n && rc == 0; ++i) {
+      double r = U[i * nv], ru = U[i * nv + 1], rE = U[i * nv + 2], rY[OR_MAXSP];
+      for (int k = 0; k < m->nsp; ++k) rY[k] = U[i * nv + 3 + k];
+      rc = cons_to_prim(m, &r, &ru, &rE, rY, 1, 0, Tw[i], &W[i]);
+      Tw[i] = W[i].T;
+    }
+    if (rc) break;
+    euler_rhs(m, n, dx, bcl, bcr, W, dU);
+    for (int64_t j = 0; j < n * nv; ++j) {
+      if (stage == 0) U1[j] = U0[j] + dt * dU[j];
+      else U1[j] = 0.5 * U0[j] + 0.5 * (U1[j] + dt * dU[j]);
+    }
+  }
+  if (rc == 0) {
+    for (int64_t i = 0; i < n && rc == 0; ++i) {
+      prim1d w;
+      double rY[OR_MAXSP];
+      for (int k = 0; k < m->nsp; ++k) rY[k] = U1[i * nv + 3 + k];
+      rc = cons_to_prim(m, &U1[i * nv], &U1[i * nv + 1], &U1[i * nv + 2], rY, 1, 0, Tw[i], &w);
+      Tw[i] = w.T;
+    }
+  }
+  if (rc == 0) {
+    for (int64_t i = 0; i < n; ++i) {
+      rho[i] = U1[i * nv]; rhou[i] = U1[i * nv + 1]; rhoE[i] = U1[i * nv + 2];
+      for (int k = 0; k < m->nsp; ++k) rhoY[k * ld + i] = U1[i * nv + 3 + k];
+      T[i] = Tw[i];
+    }
+  }
+  free(W); free(U0); free(U1); free(dU); free(Tw);
+  return rc;
+}
+
+/* Largest |u| + c over the cells (the CFL speed); T: Newton starts (not modified). */
+double oracle_euler1d_max_speed(const omech *m, int64_t n, const double *rho, const double *rhou,
+                                const double *rhoE, const double *rhoY, int64_t ld, const double *T) {
+  double smax = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    prim1d w;
+    if (cons_to_prim(m, rho, rhou, rhoE, rhoY, ld, i, T[i], &w)) return NAN;
+    smax = fmax(smax, fabs(w.u) + sqrt(sound2(m, &w)));
+  }
+  return smax;
+}
+
+/* One Strang-split step (Sec. 2.2.1): chemistry over dt/2 at fixed (rho, e) of every
+ * cell, the Euler step over dt, chemistry over dt/2 again.  The chemistry is
+ * oracle_integrate (Eq. 20-22) on Y = rho Y / rho with e = E - u^2/2; rho E and rho u do
+ * not change in a chemistry half-step.  Returns 0, or the first nonzero per-cell status
+ * / Euler code. */
+int32_t oracle_strang_step(const omech *m, int64_t n, double dx, double dt, int32_t bcl, int32_t bcr,
+                           double rtol, double atol, double *rho, double *rhou, double *rhoE,
+                           double *rhoY, int64_t ld, double *T, int32_t nthreads) {
+  double *e = (double *)malloc(sizeof(double) * (size_t)n);
+  double *Y = (double *)malloc(sizeof(double) * (size_t)(n * m->nsp));
+  int32_t *st = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t rc = 0;
+  for (int half = 0; half < 2 && rc == 0; ++half) {
+    if (half == 1) {
+      rc = oracle_euler1d_step(m, n, dx, dt, bcl, bcr, rho, rhou, rhoE, rhoY, ld, T);
+      if (rc) break;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+      double u = rhou[i] / rho[i];
+      e[i] = rhoE[i] / rho[i] - 0.5 * u * u;
+      for (int k = 0; k < m->nsp; ++k) Y[k * n + i] = rhoY[k * ld + i] / rho[i];
+    }
+    oracle_integrate(m, n, rho, e, Y, n, T, 0.5 * dt, rtol, atol, NULL, 100000, st, NULL, NULL, NULL, NULL,
+                     nthreads);
+    for (int64_t i = 0; i < n; ++i) {
+      if (st[i] && !rc) rc = st[i];
+      for (int k = 0; k < m->nsp; ++k) rhoY[k * ld + i] = rho[i] * Y[k * n + i];
+    }
+  }
+  free(e); free(Y); free(st);
+  return rc;
 }
 
 int32_t oracle_max_species(void) { return OR_MAXSP; }
