@@ -93,6 +93,7 @@ def parse():
     ap.add_argument("--no-bubble", action="store_true", help="skip the shock-bubble hybrid leg")
     ap.add_argument("--no-eq27", action="store_true", help="skip the Eq. 27 divergence benchmark leg")
     ap.add_argument("--no-mech13", action="store_true", help="skip the 13-species mechanism leg")
+    ap.add_argument("--no-znd", action="store_true", help="skip the 1D Strang-split detonation leg")
     ap.add_argument("--no-cpu-configs", action="store_true",
                     help="skip the oracle timings of configs 0, 2, 3 and 4")
     ap.add_argument("--no-comparators", action="store_true",
@@ -472,6 +473,64 @@ def mech13_leg(steps, dev, stream, flush, ref9):
     out["step_flops"] = {"9sp": roofline.step_flops(mechanism.build(0)), "13sp": roofline.step_flops(m13)}
     out["registers_13sp"] = build.kernel_resources("4chem6k_lsrkI", build.LIBS["h2o2_13"]["build"])
     return out
+
+
+def znd_leg(mech, dev, stream, n=2048, dx=25e-6, t_end=2e-5, cfl=0.45):
+    """The split scheme end to end (Sec. 2.2.1): a 1D detonation in stoichiometric H2-air
+    at 300 K and 1 atm, initiated by a driver of the same mixture at 3000 K and 30 atm in
+    the left 4 % of a closed tube (wall at the left, transmissive at the right), advanced
+    by chem_strang_step at the CFL limit (chem_euler1d_max_speed) for t_end.  Reported:
+    the front's speed (a linear fit of the position where T first exceeds 1500 K, from the
+    right, over the second half of the run), the peak pressure and temperature behind
+    it, the step count and the time split between the Strang steps and the CFL
+    reductions.  Qualitative context for the shape of the paper's Table 13 (its values
+    are for Burke's mechanism in a full solver)."""
+    import torch
+    from chem_inputs import workloads
+    from paper_2506_02602_gb300 import chem
+    ctx = chem.Context(mech, "fp64")
+    f64 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    x = (np.arange(n) + 0.5) * dx
+    drv = x < 0.04 * n * dx
+    Y = np.repeat(workloads.mass_from_mole(workloads.h2_air_mole(np.array([1.0]))), n, axis=1)
+    T0 = np.where(drv, 3000.0, 300.0)
+    p0 = np.where(drv, 30.0, 1.0) * workloads.ATM
+    Tg, Yg = f64(T0), f64(Y)
+    rho, e = ctx.state_from_TPY(Tg, f64(p0), Yg)
+    U = {"rho": rho, "rhou": torch.zeros_like(rho), "rhoE": rho * e, "rhoY": rho[None, :] * Yg,
+         "T": Tg.clone()}
+    st = torch.zeros(n, dtype=torch.int32, device=dev)
+    t, steps, hist = 0.0, 0, []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    t_cfl = 0.0
+    while t < t_end * (1 - 1e-12):
+        a = time.perf_counter()
+        dt = min(cfl * dx / ctx.euler1d_max_speed(U, stream=stream), t_end - t)
+        t_cfl += time.perf_counter() - a
+        ctx.strang_step(U, dx, dt, (1, 0), RTOL, ATOL, status=st, stream=stream)
+        t += dt
+        steps += 1
+        if steps % 50 == 0:
+            T = U["T"].cpu().numpy()
+            hot = np.flatnonzero(T > 1500.0)
+            hist.append((t, float(x[hot[-1]]) if hot.size else 0.0))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    T = U["T"].cpu().numpy()
+    rho_h = U["rho"].cpu().numpy()
+    Yh = (U["rhoY"] / U["rho"][None, :]).cpu().numpy()
+    p = rho_h * 8.31446261815324 * T * (Yh / np.asarray(mech["W"])[:, None]).sum(axis=0)
+    h = np.array(hist)
+    half = h[h[:, 0] >= 0.5 * t_end]
+    speed = float(np.polyfit(half[:, 0], half[:, 1], 1)[0]) if len(half) > 2 else None
+    ctx.close()
+    return {"cells": n, "dx_m": dx, "t_end_s": t_end, "steps": steps, "wall_s": wall,
+            "cfl_reduction_s": t_cfl, "cell_steps_per_s": n * steps / wall,
+            "front_speed_m_s": speed, "front_position_m": float(h[-1, 1]) if len(h) else None,
+            "peak_pressure_atm": float(p.max() / 101325.0), "peak_T_K": float(T.max()),
+            "all_status_ok": bool((st == 0).all()),
+            "note": "synthetic 9-species mechanism; H2-air CJ speed is about 1970 m/s for real kinetics"}
 
 
 def eq27_leg(mech, dev, stream):
@@ -1079,6 +1138,10 @@ def run_ours(args, rank, world, local):
     if not args.no_eq27:
         eq27 = eq27_leg(mech, dev, stream)
 
+    znd = None
+    if not args.no_znd:
+        znd = znd_leg(mech, dev, stream)
+
     bubble, bubble_sample = None, None
     if not args.no_bubble:
         bubble, bubble_sample = shock_bubble_leg(args, mech, dev, stream, flush)
@@ -1122,6 +1185,7 @@ def run_ours(args, rank, world, local):
             "shock_bubble": bubble,
             "eq27": eq27,
             "comparators": comparators,
+            "znd_1d_strang": znd,
             "mech13": mech13,
             "config0_reactors": config0,
             "clocks": clk,

@@ -554,6 +554,68 @@ int chem_integrate_batched_noalloc(chem_ctx *ctx, const chem_state *state, int64
                                    const chem_batch_options *opt, void *stream,
                                    chem_stats *d_stats);
 
+/* ------------------------------------------------------------- the split scheme
+ *
+ * The operator on either side of the chemistry in the paper's split solver (Sec. 2.2.1:
+ * Strang splitting of the reactive Euler equations): a minimal 1D finite-volume Euler
+ * step and the Strang step that couples it to the integrator.  It exists to run the
+ * split scheme end to end (a 1D detonation); the paper's multi-dimensional AMR hydro
+ * solver is not part of this library.
+ *
+ * A 1D flow of n cells of width dx, all device arrays, structure of arrays:
+ *   d_rho[n], d_rhou[n], d_rhoE[n]   in/out: density, momentum, total energy per volume
+ *                                    (E = e + u^2 / 2, e as in chem_state_from_TPY)
+ *   d_rhoY[k * ldY + i]              in/out: partial densities rho Y_k
+ *   d_T[n]                           in: Newton start (NaN or <= 0 -> 1500 K); out: the
+ *                                    temperature of the new state
+ *   d_status[n] (nullable)           out: the last operator's per-cell outcome
+ *                                    (chem_cell_status; the Euler step writes
+ *                                    CHEM_CELL_NEWTON_FAIL where a cell has no
+ *                                    temperature root)
+ */
+typedef struct {
+  double *d_rho;
+  double *d_rhou;
+  double *d_rhoE;
+  double *d_rhoY;
+  int64_t ldY;
+  double *d_T;
+  int32_t *d_status;
+} chem_flow1d;
+
+/*
+ * One step dt of the 1D Euler equations for a reacting mixture (no source term):
+ * second-order MUSCL reconstruction of (rho, u, p, Y_k) with minmod-limited slopes (a face
+ * whose reconstructed density or pressure is not positive takes the cell averages), the
+ * HLL flux with Davis wave speeds (sound speed from gamma = c_p / c_v of the mixture's
+ * NASA-7 thermo), and the two-stage SSP Runge-Kutta (Heun) update; p = rho R_u T
+ * sum_k Y_k / W_k with T from e by the integrator's Newton solve.  bc_left, bc_right:
+ * 0 transmissive (zero gradient), 1 reflecting wall.  The caller keeps dt within the
+ * CFL limit (chem_euler1d_max_speed).  The context owns the scratch (~(4 (3 + S) + S + 3)
+ * n doubles, grown on demand).  Errors: NULL arrays, n < 2, ldY < n, dx or dt <= 0, an
+ * unknown boundary -> CHEM_ERR_INVALID; allocation -> CHEM_ERR_NOMEM.  Asynchronous.
+ */
+int chem_euler1d_step(chem_ctx *ctx, const chem_flow1d *flow, int64_t n, double dx, double dt,
+                      int32_t bc_left, int32_t bc_right, void *stream);
+
+/* Largest |u| + c over the cells (for the CFL step dt = CFL dx / max), into *h_smax
+ * (host).  Synchronous.  The flow's temperatures are Newton starts and are not changed.
+ * Errors as chem_euler1d_step. */
+int chem_euler1d_max_speed(chem_ctx *ctx, const chem_flow1d *flow, int64_t n, double *h_smax,
+                           void *stream);
+
+/*
+ * One Strang-split step (Sec. 2.2.1): the chemistry over dt / 2 (chem_integrate on
+ * Y = rho Y / rho at fixed rho and e = E - u^2 / 2, in the context's variant and scheme;
+ * rho, rho u and rho E do not change), chem_euler1d_step over dt, the chemistry over
+ * dt / 2 again.  rtol, atol as chem_integrate; d_stats (nullable, device) counts both
+ * chemistry half-steps.  Errors as chem_euler1d_step, plus rtol <= 0 or atol < 0 ->
+ * CHEM_ERR_INVALID.  Asynchronous.
+ */
+int chem_strang_step(chem_ctx *ctx, const chem_flow1d *flow, int64_t n, double dx, double dt,
+                     int32_t bc_left, int32_t bc_right, double rtol, double atol, void *stream,
+                     chem_stats *d_stats);
+
 /*
  * Diagnostic: evaluate one of the device math routines the integration kernels use on
  * n fp64 arguments (device pointers d_x -> d_y), so tests can check them against the

@@ -70,6 +70,11 @@ class State(C.Structure):
                 ("d_status", C.c_void_p), ("d_nsteps", C.c_void_p)]
 
 
+class Flow1D(C.Structure):
+    _fields_ = [("d_rho", C.c_void_p), ("d_rhou", C.c_void_p), ("d_rhoE", C.c_void_p), ("d_rhoY", C.c_void_p),
+                ("ldY", C.c_int64), ("d_T", C.c_void_p), ("d_status", C.c_void_p)]
+
+
 class Stats(C.Structure):
     _fields_ = [("cells", C.c_int64), ("accepted", C.c_int64), ("rejected", C.c_int64),
                 ("rhs_evals", C.c_int64), ("max_steps_cell", C.c_int64),
@@ -158,6 +163,10 @@ def load(n_species: int = 9) -> C.CDLL:
         "chem_surrogate_grad": (C.c_int, [vp, vp, vp, i64, vp, vp, vp, vp]),
         "chem_surrogate_forward": (C.c_int, [vp, vp, i64, vp, C.c_int32, vp, vp]),
         "chem_surrogate_adam": (C.c_int, [vp, vp, i64, C.c_float]),
+        "chem_euler1d_step": (C.c_int, [vp, C.POINTER(Flow1D), i64, dbl, dbl, C.c_int32, C.c_int32, vp]),
+        "chem_euler1d_max_speed": (C.c_int, [vp, C.POINTER(Flow1D), i64, vp, vp]),
+        "chem_strang_step": (C.c_int, [vp, C.POINTER(Flow1D), i64, dbl, dbl, C.c_int32, C.c_int32, dbl, dbl,
+                                       vp, vp]),
         "chem_surrogate_trace": (C.c_int, [vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]),
         "chem_surrogate_project": (C.c_int, [vp, i64, vp, vp, i64, vp, vp]),
     }
@@ -515,6 +524,39 @@ class Context:
         return {"Y": Y.cpu().numpy(), "Z": Z.cpu().numpy(), "H": H.float().cpu().numpy(),
                 "G": Gf[:3].cpu().numpy(), "G3": Gf[3].reshape(-1)[: B * 16].reshape(B, 16).cpu().numpy(),
                 "dH": dH.cpu().numpy(), "grad": g, "loss": float(loss[0])}
+
+    # the split scheme's 1D flow -------------------------------------------------
+    @staticmethod
+    def _flow(U, status=None):
+        """chem_flow1d of a dict of float64 CUDA tensors rho, rhou, rhoE [n], rhoY [S, ld], T [n]."""
+        for k in ("rho", "rhou", "rhoE", "rhoY", "T"):
+            _check_f64_cuda(k, U[k])
+        n = U["rho"].numel()
+        for k in ("rhou", "rhoE", "T"):
+            if U[k].numel() < n:
+                raise ChemError(ERR_INVALID, f"{k} has fewer than {n} cells")
+        if U["rhoY"].stride(1) != 1 or U["rhoY"].shape[1] < n:
+            raise ChemError(ERR_INVALID, "rhoY must be [S, ld] planes with ld >= n")
+        return Flow1D(U["rho"].data_ptr(), U["rhou"].data_ptr(), U["rhoE"].data_ptr(), U["rhoY"].data_ptr(),
+                      U["rhoY"].stride(0), U["T"].data_ptr(), None if status is None else status.data_ptr()), n
+
+    def euler1d_step(self, U, dx, dt, bc=(0, 0), status=None, stream=None):
+        """chem_euler1d_step on the flow U in place."""
+        f, n = self._flow(U, status)
+        self._raise(self.L.chem_euler1d_step(self.h, C.byref(f), n, float(dx), float(dt), int(bc[0]), int(bc[1]),
+                                             _stream(stream)))
+
+    def euler1d_max_speed(self, U, stream=None):
+        f, n = self._flow(U)
+        out = C.c_double(0.0)
+        self._raise(self.L.chem_euler1d_max_speed(self.h, C.byref(f), n, C.byref(out), _stream(stream)))
+        return out.value
+
+    def strang_step(self, U, dx, dt, bc=(0, 0), rtol=1e-6, atol=1e-10, status=None, stats=None, stream=None):
+        """chem_strang_step on the flow U in place."""
+        f, n = self._flow(U, status)
+        self._raise(self.L.chem_strang_step(self.h, C.byref(f), n, float(dx), float(dt), int(bc[0]), int(bc[1]),
+                                            float(rtol), float(atol), _stream(stream), _ptr(stats)))
 
     def surrogate_adam(self, grad, lr):
         """chem_surrogate_adam: one Adam step of the parameters with the flat gradient

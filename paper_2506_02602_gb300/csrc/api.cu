@@ -37,6 +37,9 @@ struct chem_ctx {
   // and per-chunk events (created on first use)
   cudaStream_t io[3] = {nullptr, nullptr, nullptr};
   cudaEvent_t ev[3 * 8 + 2] = {};
+  // device scratch of the 1D flow operators (euler1d.cu; grown on demand)
+  void *flow_scratch = nullptr;
+  size_t flow_bytes = 0;
 };
 
 namespace {
@@ -341,6 +344,7 @@ int chem_teardown(chem_ctx *ctx) {
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->sur) surrogate_destroy(ctx->sur);
+  if (ctx->flow_scratch) cudaFree(ctx->flow_scratch);
   delete ctx;
   return CHEM_OK;
 }
@@ -618,6 +622,19 @@ std::string &chem_ctx_error(chem_ctx *ctx) { return ctx->err; }
 const MechTables &chem_ctx_tables(const chem_ctx *ctx) { return ctx->tables; }
 int chem_ctx_variant(const chem_ctx *ctx) { return ctx->opt.variant; }
 int chem_ctx_scheme(const chem_ctx *ctx) { return ctx->opt.scheme; }
+int chem_ctx_block(const chem_ctx *ctx) { return ctx->opt.block_size; }
+cudaError_t chem_ctx_flow_scratch(chem_ctx *ctx, size_t bytes, void **out) {
+  if (bytes > ctx->flow_bytes) {
+    if (ctx->flow_scratch) cudaFree(ctx->flow_scratch);
+    ctx->flow_scratch = nullptr;
+    ctx->flow_bytes = 0;
+    cudaError_t e = cudaMalloc(&ctx->flow_scratch, bytes);
+    if (e != cudaSuccess) return e;
+    ctx->flow_bytes = bytes;
+  }
+  *out = ctx->flow_scratch;
+  return cudaSuccess;
+}
 int32_t chem_ctx_max_steps(const chem_ctx *ctx) { return ctx->opt.max_steps; }
 void *&chem_ctx_sur(chem_ctx *ctx) { return ctx->sur; }
 }  // namespace chem

@@ -72,6 +72,9 @@ std::string &chem_ctx_error(chem_ctx *ctx);
 const MechTables &chem_ctx_tables(const chem_ctx *ctx);
 int chem_ctx_variant(const chem_ctx *ctx);
 int chem_ctx_scheme(const chem_ctx *ctx);
+int chem_ctx_block(const chem_ctx *ctx);
+// Device scratch of the 1D flow operators, grown to at least `bytes` (freed at teardown).
+cudaError_t chem_ctx_flow_scratch(chem_ctx *ctx, size_t bytes, void **out);
 int32_t chem_ctx_max_steps(const chem_ctx *ctx);
 void *&chem_ctx_sur(chem_ctx *ctx);
 void surrogate_destroy(void *sur);
