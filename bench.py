@@ -482,8 +482,7 @@ def znd_leg(mech, dev, stream, n=2048, dx=25e-6, t_end=2e-5, cfl=0.45):
     by chem_strang_step at the CFL limit (chem_euler1d_max_speed) for t_end.  Reported:
     the front's speed (a linear fit of the position where T first exceeds 1500 K, from the
     right, over the second half of the run), the peak pressure and temperature behind
-    it, the step count and the time split between the Strang steps and the CFL
-    reductions.  Qualitative context for the shape of the paper's Table 13 (its values
+    it, the step count and the wall time.  Qualitative context for the shape of the paper's Table 13 (its values
     are for Burke's mechanism in a full solver)."""
     import torch
     from chem_inputs import workloads
