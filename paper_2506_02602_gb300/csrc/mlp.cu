@@ -1,15 +1,7 @@
-// mlp.cu -- tensor-core building blocks of the learned surrogate: a BF16 GEMM with
-// FP32 accumulation and a fused epilogue, and the elementwise kernels of training
-// (GELU backward, MSE gradient, bias-gradient reduction, Adam with FP32 master weights
-// and BF16 shadows, row gather).
-//
-// GEMM: C[m, n] = alpha * sum_k A(m, k) B(n, k) (+ bias[n]), with A(m, k) = A[m*sam + k*sak]
-// and B(n, k) = B[n*sbn + k*sbk] in BF16, so one kernel serves the forward layer
-// (X W^T), the input gradient (dZ W) and the weight gradient (X^T dZ) through strides.
-// A 128 x 128 CTA tile, 8 warps of 32 x 64, K in steps of 32 staged in shared memory
-// (k-contiguous rows, padded against bank conflicts), ldmatrix fragments and
-// mma.sync.m16n8k16 BF16 -> FP32.  Epilogue: alpha, optional bias, FP32 store and/or
-// BF16 store of the value or of GELU(value).
+// mlp.cu -- the elementwise kernels of the learned surrogate's training: GELU backward,
+// MSE gradient, split-K and bias-gradient reductions, Adam with FP32 master weights and
+// BF16 shadows, row gather, BF16 conversion.  The GEMMs run on the tensor cores
+// (mlp_gemm_tc.cu).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -20,99 +12,6 @@
 #include "mma.cuh"
 
 namespace chem {
-
-constexpr int GBM = 128, GBN = 128, GBK = 32, GPAD = 8;
-constexpr int GTHREADS = 256;
-
-__global__ void __launch_bounds__(GTHREADS) k_gemm_bf16(GemmArgs g) {
-  __shared__ __align__(16) __nv_bfloat16 As[GBM][GBK + GPAD];
-  __shared__ __align__(16) __nv_bfloat16 Bs[GBN][GBK + GPAD];
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
-  const int wm = (warp & 3) * 32;   // warp row offset in the CTA tile
-  const int wn = (warp >> 2) * 64;  // warp column offset
-  const int64_t m0 = (int64_t)blockIdx.y * GBM;
-  const int64_t n0 = (int64_t)blockIdx.x * GBN;
-  // this CTA's K slice (the whole K without split-K)
-  int64_t kbeg = 0, kend = g.K;
-  if (g.split > 1) {
-    const int64_t steps = (g.K + GBK - 1) / GBK, per = (steps + g.split - 1) / g.split;
-    kbeg = (int64_t)blockIdx.z * per * GBK;
-    kend = kbeg + per * GBK < g.K ? kbeg + per * GBK : g.K;
-  }
-  float acc[2][8][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
-  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-  for (int64_t k0 = kbeg; k0 < kend; k0 += GBK) {
-    // stage the A and B tiles (16 elements per thread each); across threads the index
-    // along the operand's unit-stride dimension runs fastest, so loads coalesce for
-    // k-contiguous operands (forward, input gradient) and row-contiguous ones (weight
-    // gradient) alike
-    for (int idx = tid; idx < GBM * GBK; idx += GTHREADS) {
-      const int r = g.sak == 1 ? idx / GBK : idx % GBM, c = g.sak == 1 ? idx % GBK : idx / GBM;
-      const int64_t m = m0 + r, k = k0 + c;
-      As[r][c] = (m < g.M && k < kend) ? g.A[m * g.sam + k * g.sak] : zero;
-    }
-    for (int idx = tid; idx < GBN * GBK; idx += GTHREADS) {
-      const int r = g.sbk == 1 ? idx / GBK : idx % GBN, c = g.sbk == 1 ? idx % GBK : idx / GBN;
-      const int64_t n = n0 + r, k = k0 + c;
-      Bs[r][c] = (n < g.N && k < kend) ? g.B[n * g.sbn + k * g.sbk] : zero;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GBK; kk += 16) {
-      uint32_t af[2][4];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int q = lane >> 3, rr = lane & 7;
-        ldmatrix_x4(af[i], &As[wm + i * 16 + (q & 1) * 8 + rr][kk + (q >> 1) * 8]);
-      }
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        uint32_t bf[2];
-        const int q = (lane >> 3) & 1, rr = lane & 7;
-        ldmatrix_x2(bf, &Bs[wn + j * 8 + rr][kk + q * 8]);
-#pragma unroll
-        for (int i = 0; i < 2; ++i) mma_bf16(acc[i][j], af[i], bf);
-      }
-    }
-    __syncthreads();
-  }
-  // epilogue: fragment (i, j) covers rows wm + 16i + {g, g+8}, cols wn + 8j + 2t + {0, 1}
-  const int gq = lane >> 2, tq = lane & 3;
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int64_t m = m0 + wm + i * 16 + gq + (q >> 1) * 8;
-        const int64_t n = n0 + wn + j * 8 + tq * 2 + (q & 1);
-        if (m < g.M && n < g.N && g.split > 1) {
-          g.Cf[(int64_t)blockIdx.z * g.split_ld + m * g.ldc + n] = acc[i][j][q] * g.alpha;
-        } else if (m < g.M && n < g.N) {
-          float v = acc[i][j][q] * g.alpha;
-          if (g.bias) v += g.bias[n];
-          if (g.accumulate) v += g.Cf[m * g.ldc + n];
-          if (g.Cf) g.Cf[m * g.ldc + n] = v;
-          if (g.Cb) g.Cb[m * g.ldcb + n] = __float2bfloat16(g.gelu ? gelu_f(v) : v);
-        }
-      }
-}
-
-cudaError_t launch_gemm(const GemmArgs &g, cudaStream_t s) {
-  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
-  if (g.split > 1 && (!g.Cf || g.Cb || g.bias || g.accumulate)) return cudaErrorInvalidValue;
-  dim3 grid((unsigned)((g.N + GBN - 1) / GBN), (unsigned)((g.M + GBM - 1) / GBM),
-            (unsigned)(g.split > 1 ? g.split : 1));
-  k_gemm_bf16<<<grid, GTHREADS, 0, s>>>(g);
-  return cudaGetLastError();
-}
 
 // dZ (bf16) = dH * GELU'(Z) with dH fp32 [M x N] (ld), Z fp32 (ld)
 __global__ void k_gelu_backward(int64_t M, int N, const float *__restrict__ dH, int ldh,
@@ -205,6 +104,49 @@ __global__ void k_adam(int64_t n, float *__restrict__ w, const float *__restrict
   }
 }
 
+// Adam with the step's learning rate and bias corrections read from a device schedule:
+// sched[3 t .. 3 t + 2] = {lr, 1 - b1^(t+1), 1 - b2^(t+1)} at t = *step (a CUDA graph of one
+// training step replays with the counter advancing on the device).
+__global__ void k_adam_sched(int64_t n, float *__restrict__ w, const float *__restrict__ g,
+                             float *__restrict__ m, float *__restrict__ v, const float *__restrict__ sched,
+                             const int64_t *__restrict__ step, float b1, float b2, float eps,
+                             __nv_bfloat16 *__restrict__ w_bf, __nv_bfloat16 *__restrict__ wT_bf, int rows,
+                             int cols) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float *sc = sched + 3 * *step;
+  const float lr = sc[0], bc1 = sc[1], bc2 = sc[2];
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.0f - b1) * gi;
+  const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float wi = w[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  w[i] = wi;
+  if (w_bf) w_bf[i] = __float2bfloat16(wi);
+  if (wT_bf) {
+    const int64_t r = i / cols, c = i % cols;
+    wT_bf[c * rows + r] = __float2bfloat16(wi);
+  }
+}
+
+// out[r, :] = in[idx[base + r], :] with base = (*step mod nbatch) * nrows: the batch of
+// the current step of an epoch's permutation
+__global__ void k_gather_rows_step(int64_t nrows, int ncol, const int32_t *__restrict__ idx,
+                                   const int64_t *__restrict__ step, int64_t nbatch, const float *__restrict__ in,
+                                   int ldin, float *__restrict__ out, int ldout) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nrows * ncol) return;
+  const int64_t r = t / ncol;
+  const int c = (int)(t % ncol);
+  const int64_t base = (*step % nbatch) * nrows;
+  out[r * ldout + c] = in[(int64_t)idx[base + r] * ldin + c];
+}
+
+__global__ void k_step_inc(int64_t *step) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *step += 1;
+}
+
 // out[r, :] = in[idx[r], :] for ncol columns (float)
 __global__ void k_gather_rows(int64_t nrows, int ncol, const int32_t *__restrict__ idx,
                               const float *__restrict__ in, int ldin, float *__restrict__ out,
@@ -256,6 +198,23 @@ cudaError_t launch_adam(int64_t n, float *w, const float *g, float *m, float *v,
 cudaError_t launch_gather_rows(int64_t nrows, int ncol, const int32_t *idx, const float *in, int ldin,
                                float *out, int ldout, cudaStream_t s) {
   k_gather_rows<<<blocks(nrows * ncol, 256), 256, 0, s>>>(nrows, ncol, idx, in, ldin, out, ldout);
+  return cudaGetLastError();
+}
+cudaError_t launch_adam_sched(int64_t n, float *w, const float *g, float *m, float *v, const float *sched,
+                              const int64_t *step, float b1, float b2, float eps, __nv_bfloat16 *w_bf,
+                              __nv_bfloat16 *wT_bf, int rows, int cols, cudaStream_t s) {
+  k_adam_sched<<<blocks(n, 256), 256, 0, s>>>(n, w, g, m, v, sched, step, b1, b2, eps, w_bf, wT_bf, rows, cols);
+  return cudaGetLastError();
+}
+cudaError_t launch_gather_rows_step(int64_t nrows, int ncol, const int32_t *idx, const int64_t *step,
+                                    int64_t nbatch, const float *in, int ldin, float *out, int ldout,
+                                    cudaStream_t s) {
+  k_gather_rows_step<<<blocks(nrows * ncol, 256), 256, 0, s>>>(nrows, ncol, idx, step, nbatch, in, ldin, out,
+                                                               ldout);
+  return cudaGetLastError();
+}
+cudaError_t launch_step_inc(int64_t *step, cudaStream_t s) {
+  k_step_inc<<<1, 32, 0, s>>>(step);
   return cudaGetLastError();
 }
 cudaError_t launch_to_bf16(int64_t n, const float *in, __nv_bfloat16 *out, cudaStream_t s) {

@@ -8,7 +8,8 @@
 
 namespace chem {
 
-// C[m, n] = alpha * sum_k A(m, k) B(n, k) (+ bias[n]) (+ Cf[m, n] if accumulate);
+// C[m, n] = alpha * sum_k A(m, k) B(n, k) (+ bias[n]) (+ Cf[m, n] if accumulate), on the
+// 5th-generation tensor cores (mlp_gemm_tc.cu);
 // A(m, k) = A[m*sam + k*sak], B(n, k) = B[n*sbn + k*sbk].  Outputs: Cf (fp32, ldc) and/or
 // Cb (bf16, ldcb) holding the value, or GELU(value) when gelu is set.
 // Split-K (split > 1): the K range is cut into `split` slices of whole 32-wide steps and
@@ -30,6 +31,7 @@ struct GemmArgs {
   int accumulate;
   int split;
   int64_t split_ld;
+  int *err;  // nullable device word: set to 1 if a bounded wait of the kernel ran out
 };
 
 cudaError_t launch_gemm(const GemmArgs &g, cudaStream_t s);
@@ -49,5 +51,17 @@ cudaError_t launch_adam(int64_t n, float *w, const float *g, float *m, float *v,
 cudaError_t launch_gather_rows(int64_t nrows, int ncol, const int32_t *idx, const float *in,
                                int ldin, float *out, int ldout, cudaStream_t s);
 cudaError_t launch_to_bf16(int64_t n, const float *in, __nv_bfloat16 *out, cudaStream_t s);
+// The device-scheduled pieces of a graph-captured training step: Adam with {lr, 1 - b1^t,
+// 1 - b2^t} read from sched[3 * (*step)], the batch gather of step *step, the counter.
+cudaError_t launch_adam_sched(int64_t n, float *w, const float *g, float *m, float *v, const float *sched,
+                              const int64_t *step, float b1, float b2, float eps, __nv_bfloat16 *w_bf,
+                              __nv_bfloat16 *wT_bf, int rows, int cols, cudaStream_t s);
+cudaError_t launch_gather_rows_step(int64_t nrows, int ncol, const int32_t *idx, const int64_t *step,
+                                    int64_t nbatch, const float *in, int ldin, float *out, int ldout,
+                                    cudaStream_t s);
+cudaError_t launch_step_inc(int64_t *step, cudaStream_t s);
+// Sets the tensor-core GEMM's shared-memory attribute on the current device (once), so
+// that GEMM launches can be captured in a CUDA graph.
+cudaError_t gemm_prepare();
 
 }  // namespace chem

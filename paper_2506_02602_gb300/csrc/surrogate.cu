@@ -213,6 +213,7 @@ static cudaError_t layer_forward(Surrogate *s, int l, int64_t M, const __nv_bflo
   g.Cb = last ? nullptr : Hout;
   g.ldcb = kSurN[l];
   g.gelu = !last;
+  g.err = s->tc_err;
   return launch_gemm(g, st);
 }
 
@@ -294,6 +295,7 @@ static cudaError_t forward_backward(Surrogate *s, TrainBufs &b, int64_t B, cudaS
     gw.Cf = b.part; gw.ldc = K;
     gw.split = kGradSplit;
     gw.split_ld = (int64_t)N * K;
+    gw.err = s->tc_err;
     SCHK(launch_gemm(gw, st));
     SCHK(launch_reduce_splits((int64_t)N * K, kGradSplit, b.part, (int64_t)N * K, s->grad + s->off_W[l], st));
     SCHK(launch_bias_grad(B, N, G, N, b.part, kGradSplit, s->grad + s->off_b[l], st));
@@ -305,6 +307,7 @@ static cudaError_t forward_backward(Surrogate *s, TrainBufs &b, int64_t B, cudaS
     gx.B = s->WT[l]; gx.sbn = N; gx.sbk = 1;
     gx.alpha = 1.0f;
     gx.Cf = b.dH; gx.ldc = K;
+    gx.err = s->tc_err;
     SCHK(launch_gemm(gx, st));
     // G for layer l-1: dZ = dHin * GELU'(Z_{l-1})
     SCHK(launch_gelu_backward(B, K, b.dH, K, b.Z[l - 1], K, b.dZ, K, st));
@@ -471,6 +474,7 @@ static int surrogate_pass(chem_ctx *ctx, const float *d_X, const float *d_T, int
   cudaStream_t st = (cudaStream_t)stream;
   TrainBufs b;
   e = b.alloc(B);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->tc_err, 0, sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b.Xb, d_X, B * kSurIn * sizeof(float), cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b.Tb, d_T, B * kSurOut * sizeof(float), cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b.loss, 0, sizeof(float), st);
@@ -479,8 +483,11 @@ static int surrogate_pass(chem_ctx *ctx, const float *d_X, const float *d_T, int
   if (e == cudaSuccess && h_grad)
     e = cudaMemcpyAsync(h_grad, s->grad, (size_t)kSurParams * sizeof(float), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && h_loss) e = cudaMemcpyAsync(h_loss, b.loss, sizeof(float), cudaMemcpyDeviceToHost, st);
+  int terr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&terr, s->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   b.release();
+  if (e == cudaSuccess && terr) return sur_fail(ctx, CHEM_ERR_TIMEOUT, "a bounded wait of the tensor-core GEMM ran out");
   return e == cudaSuccess ? CHEM_OK : sur_cuda(ctx, e, "surrogate forward/backward");
 }
 
@@ -590,6 +597,7 @@ int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
   std::vector<float> h;
   init_params(s, cfg.seed, h);
   e = set_params(s, h.data(), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->tc_err, 0, sizeof(int), st);
   if (e != cudaSuccess) return sur_cuda(ctx, e, "initialising parameters");
   const int64_t n = npairs, B = cfg.batch;
   float *X = nullptr, *Tg = nullptr;
@@ -650,32 +658,115 @@ int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
   if (e == cudaSuccess) e = launch_normalize(n, kSurFeat, kSurIn, X, s->dev_norm, s->dev_norm + 16, nullptr, st);
   if (e == cudaSuccess) e = launch_normalize(n, NSP, kSurOut, Tg, s->dev_norm + 32, s->dev_norm + 48, nullptr, st);
   if (e != cudaSuccess) { cleanup(); return sur_cuda(ctx, e, "normalising"); }
-  // epochs of shuffled batches
+  // epochs of shuffled batches.  One training step (the batch gather, forward, loss,
+  // backward, Adam) is captured once as a CUDA graph on a private stream and replayed
+  // for every batch: the batch offset, the learning rate of the cosine schedule and
+  // Adam's bias corrections come from a step counter on the device and a schedule table
+  // computed here, so the replays need no host arguments.
   const int64_t nb = n / B;
   const int64_t total = nb * cfg.epochs;
-  std::vector<int32_t> perm((size_t)n);
-  Rng r{cfg.seed ^ 0x5bd1e995ull};
-  int64_t it = 0;
-  for (int ep = 0; ep < cfg.epochs && e == cudaSuccess; ++ep) {
-    for (int64_t i = 0; i < n; ++i) perm[(size_t)i] = (int32_t)i;
-    for (int64_t i = n - 1; i > 0; --i) std::swap(perm[(size_t)i], perm[(size_t)(r.next() % (uint64_t)(i + 1))]);
-    e = cudaMemcpy(idx, perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b.loss, 0, sizeof(float), st);
-    for (int64_t bi = 0; bi < nb && e == cudaSuccess; ++bi, ++it) {
-      e = launch_gather_rows(B, kSurIn, idx + bi * B, X, kSurIn, b.Xb, kSurIn, st);
-      if (e == cudaSuccess) e = launch_gather_rows(B, kSurOut, idx + bi * B, Tg, kSurOut, b.Tb, kSurOut, st);
-      if (e == cudaSuccess) e = forward_backward(s, b, B, st);
-      const double frac = total > 1 ? (double)it / (double)(total - 1) : 1.0;
-      const float lr = (float)(cfg.lr_final + 0.5 * (cfg.lr - cfg.lr_final) * (1.0 + std::cos(3.141592653589793 * frac)));
-      if (e == cudaSuccess) e = adam_all(s, lr, st);
-    }
-    float lsum = 0.0f;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&lsum, b.loss, sizeof(float), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess && h_epoch_loss) h_epoch_loss[ep] = lsum / (float)nb;
+  std::vector<float> hsched((size_t)(3 * (total > 0 ? total : 1)));
+  for (int64_t it = 0; it < total; ++it) {
+    const double frac = total > 1 ? (double)it / (double)(total - 1) : 1.0;
+    hsched[(size_t)(3 * it)] =
+        (float)(cfg.lr_final + 0.5 * (cfg.lr - cfg.lr_final) * (1.0 + std::cos(3.141592653589793 * frac)));
+    hsched[(size_t)(3 * it + 1)] = 1.0f - powf(0.9f, (float)(it + 1));
+    hsched[(size_t)(3 * it + 2)] = 1.0f - powf(0.999f, (float)(it + 1));
   }
+  float *dsched = nullptr;
+  int64_t *dstep = nullptr;
+  int32_t *idx2 = nullptr;   // the second permutation buffer (epochs alternate)
+  int32_t *hperm = nullptr;  // pinned staging of the permutations, two slots
+  float *hloss = nullptr;    // pinned per-epoch loss sums
+  cudaStream_t ps = nullptr;
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaEvent_t up_done[2] = {nullptr, nullptr};
+  auto release_graph = [&]() {
+    for (int i = 0; i < 2; ++i) {
+      if (exec[i]) cudaGraphExecDestroy(exec[i]);
+      if (graph[i]) cudaGraphDestroy(graph[i]);
+      if (up_done[i]) cudaEventDestroy(up_done[i]);
+    }
+    if (ps) cudaStreamDestroy(ps);
+    cudaFree(dsched);
+    cudaFree(dstep);
+    cudaFree(idx2);
+    cudaFreeHost(hperm);
+    cudaFreeHost(hloss);
+  };
+  e = cudaMalloc(&dsched, hsched.size() * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&dstep, sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&idx2, n * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMallocHost(&hperm, 2 * n * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMallocHost(&hloss, (size_t)(cfg.epochs > 0 ? cfg.epochs : 1) * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(dsched, hsched.data(), hsched.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(dstep, 0, sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&up_done[i], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = gemm_prepare();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // features and statistics are done
+  int32_t *idxs[2] = {idx, idx2};
+  for (int gi = 0; gi < 2 && e == cudaSuccess && total > 0; ++gi) {
+    e = cudaStreamBeginCapture(ps, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) break;
+    cudaError_t ce = launch_gather_rows_step(B, kSurIn, idxs[gi], dstep, nb, X, kSurIn, b.Xb, kSurIn, ps);
+    if (ce == cudaSuccess) ce = launch_gather_rows_step(B, kSurOut, idxs[gi], dstep, nb, Tg, kSurOut, b.Tb, kSurOut, ps);
+    if (ce == cudaSuccess) ce = forward_backward(s, b, B, ps);
+    for (int l = 0; l < kSurLayers && ce == cudaSuccess; ++l) {
+      const int64_t nw = (int64_t)kSurN[l] * kSurK[l];
+      ce = launch_adam_sched(nw, s->param + s->off_W[l], s->grad + s->off_W[l], s->m + s->off_W[l],
+                             s->v + s->off_W[l], dsched, dstep, 0.9f, 0.999f, 1e-8f, s->W[l], s->WT[l], kSurN[l],
+                             kSurK[l], ps);
+      if (ce == cudaSuccess)
+        ce = launch_adam_sched(kSurN[l], s->param + s->off_b[l], s->grad + s->off_b[l], s->m + s->off_b[l],
+                               s->v + s->off_b[l], dsched, dstep, 0.9f, 0.999f, 1e-8f, nullptr, nullptr, 1,
+                               kSurN[l], ps);
+    }
+    if (ce == cudaSuccess) ce = launch_step_inc(dstep, ps);
+    e = cudaStreamEndCapture(ps, &graph[gi]);
+    if (e == cudaSuccess) e = ce;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec[gi], graph[gi], 0);
+  }
+  // the host shuffles epoch ep + 1 while the GPU replays epoch ep: permutations alternate
+  // between two device buffers (one graph each) and two pinned staging slots
+  Rng r{cfg.seed ^ 0x5bd1e995ull};
+  auto shuffle_into = [&](int32_t *dst) {
+    for (int64_t i = 0; i < n; ++i) dst[i] = (int32_t)i;
+    for (int64_t i = n - 1; i > 0; --i) std::swap(dst[i], dst[(size_t)(r.next() % (uint64_t)(i + 1))]);
+  };
+  if (e == cudaSuccess && cfg.epochs > 0) {
+    shuffle_into(hperm);
+    e = cudaMemcpyAsync(idx, hperm, n * sizeof(int32_t), cudaMemcpyHostToDevice, ps);
+    if (e == cudaSuccess) e = cudaEventRecord(up_done[0], ps);
+  }
+  for (int ep = 0; ep < cfg.epochs && e == cudaSuccess; ++ep) {
+    const int cur = ep & 1, nxt = cur ^ 1;
+    e = cudaMemsetAsync(b.loss, 0, sizeof(float), ps);
+    for (int64_t bi = 0; bi < nb && e == cudaSuccess; ++bi) e = cudaGraphLaunch(exec[cur], ps);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hloss + ep, b.loss, sizeof(float), cudaMemcpyDeviceToHost, ps);
+    if (e == cudaSuccess && ep + 1 < cfg.epochs) {
+      // the staging slot of epoch ep + 1 was last copied for epoch ep - 1
+      if (ep >= 1) e = cudaEventSynchronize(up_done[nxt]);
+      if (e == cudaSuccess) {
+        shuffle_into(hperm + (size_t)nxt * n);
+        e = cudaMemcpyAsync(idxs[nxt], hperm + (size_t)nxt * n, n * sizeof(int32_t), cudaMemcpyHostToDevice, ps);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(up_done[nxt], ps);
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ps);
+  if (e == cudaSuccess && h_epoch_loss)
+    for (int ep = 0; ep < cfg.epochs; ++ep) h_epoch_loss[ep] = hloss[ep] / (float)nb;
+  s->step = total;
+  s->packed = false;
+  release_graph();
   cleanup();
   if (e != cudaSuccess) return sur_cuda(ctx, e, "training");
+  int terr = 0;
+  e = cudaMemcpy(&terr, s->tc_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return sur_cuda(ctx, e, "training");
+  if (terr) return sur_fail(ctx, CHEM_ERR_TIMEOUT, "a bounded wait of the tensor-core GEMM ran out in training");
   s->ready = true;
   return CHEM_OK;
 }

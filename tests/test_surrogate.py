@@ -119,12 +119,13 @@ def test_forward_backward_elementwise_vs_fp64_oracle(lib):
         assert rW.max() <= 1.0 and rb.max() <= 1.0, (l, rW.max(), rb.max())
         pad = W.copy(); pad[: ref_W.shape[0], : ref_W.shape[1]] = 0.0
         assert np.all(pad == 0.0) and np.all(b[ref_b.size:] == 0.0)
-    # the one-kernel mma.sync forward: same fragments, K order and epilogue -> same numbers
-    Yf = ctx.surrogate_forward(Xb.cuda(), impl=ctx.FWD_FUSED).cpu().numpy()
-    np.testing.assert_array_equal(Yf, Yg)
-    Yf2 = ctx.surrogate_forward(Xb[:333].contiguous().cuda(), impl=ctx.FWD_FUSED).cpu().numpy()  # ragged tile
-    np.testing.assert_array_equal(Yf2, Yg[:333])
+    # the layer-by-layer forward is the training pass's own (the same tcgen05 GEMMs)
     np.testing.assert_array_equal(ctx.surrogate_forward(Xb.cuda(), impl=ctx.FWD_LAYERS).cpu().numpy(), Yg)
+    # the one-kernel mma.sync forward (the legacy tensor path, kept as a check): its own
+    # summation order, the same element bound against the oracle, full and ragged tiles
+    for rows in (B, 333):
+        Yf = ctx.surrogate_forward(Xb[:rows].contiguous().cuda(), impl=ctx.FWD_FUSED).cpu().numpy()
+        assert np.max(np.abs(Yf[:, :9] - Yo[:rows]) / Dy[:rows]) <= 1.0, rows
     # the tcgen05 kernel inference uses sums the K products in the tensor cores' own
     # order; its outputs meet the same element bound against the oracle, on full and
     # ragged tiles
