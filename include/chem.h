@@ -624,9 +624,10 @@ int chem_strang_step(chem_ctx *ctx, const chem_flow1d *flow, int64_t n, double d
  * 4 reciprocal with one Newton-Raphson step, 5 with two, 6 the hardware reciprocal
  * approximation alone, 7 the integer-pipe fp64 -> fp32 rounding (widened back exactly),
  * 8 the integer-pipe fp32 -> fp64 widening of the hardware-rounded fp32 of x,
- * 9 / 10 the hi / lo fp32 parts of the 2^-12-grid split of x.  Not part of the
- * integration path; the paper has no counterpart.  Errors: unknown op or n < 0 ->
- * CHEM_ERR_INVALID.  Asynchronous on stream.
+ * 9 / 10 the hi / lo fp32 parts of the 2^-12-grid split of x, 11 / 12 the network's fp32
+ * GELU and GELU' of (float)x (erf by Abramowitz & Stegun 7.1.26), 13 / 14 the same with
+ * the CUDA library's erff and expf.  Not part of the integration path; the paper has no
+ * counterpart.  Errors: unknown op or n < 0 -> CHEM_ERR_INVALID.  Asynchronous on stream.
  */
 int chem_diag_math(int op, int64_t n, const double *d_x, double *d_y, void *stream);
 

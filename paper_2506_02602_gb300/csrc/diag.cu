@@ -6,6 +6,7 @@
 
 #include "fastmath.cuh"
 #include "internal.cuh"
+#include "mma.cuh"
 
 namespace chem {
 
@@ -27,7 +28,19 @@ __global__ void k_diag_math(int op, int64_t n, const double *__restrict__ x, dou
     case 7: r = (double)d2f(v); break;          // widened exactly by the hardware
     case 8: r = f2d(__double2float_rn(v)); break;
     case 9: split_hilo(v, h, l); r = (double)h; break;
-    default: split_hilo(v, h, l); r = (double)l; break;
+    case 10: split_hilo(v, h, l); r = (double)l; break;
+    case 11: r = (double)gelu_f((float)v); break;
+    case 12: r = (double)gelu_grad_f((float)v); break;
+    case 13: {  // the same with the CUDA library's erff and expf
+      const float x = (float)v;
+      r = (double)(0.5f * x * (1.0f + erff(x * 0.70710678118654752f)));
+      break;
+    }
+    default: {
+      const float x = (float)v;
+      r = (double)(0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x));
+      break;
+    }
   }
   y[i] = r;
 }
@@ -87,7 +100,7 @@ extern "C" int chem_diag_fma_peak(int op, int32_t blocks, int32_t threads, int64
 }
 
 extern "C" int chem_diag_math(int op, int64_t n, const double *d_x, double *d_y, void *stream) {
-  if (op < 0 || op > 10 || n < 0) return CHEM_ERR_INVALID;
+  if (op < 0 || op > 14 || n < 0) return CHEM_ERR_INVALID;
   if (n == 0) return CHEM_OK;
   if (!d_x || !d_y) return CHEM_ERR_INVALID;
   const int block = 256;

@@ -1,6 +1,7 @@
 // mma.cuh -- warp-level tensor-core helpers shared by the surrogate's GEMM kernels:
 // ldmatrix fragment loads from shared memory, the m16n8k16 BF16 MMA with FP32
-// accumulation, 16-byte cp.async, and GELU with its derivative (erf form).
+// accumulation, 16-byte cp.async, and GELU with its derivative (erf form, by a published
+// rational-exponential approximation of erf).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -10,10 +11,35 @@
 
 namespace chem {
 
-__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// Phi(x) = (1 + erf(x / sqrt 2)) / 2 (the standard normal distribution function) and
+// exp(-x^2 / 2), from erf(u) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) e^(-u^2),
+// t = 1 / (1 + p u), u >= 0 (Abramowitz & Stegun 7.1.26, |error| <= 1.5e-7).  For x < 0
+// the tail 1 - erf(u) = poly e^(-u^2) is returned directly instead of cancelling 1 + erf,
+// so Phi keeps a relative accuracy below BF16's there (0.16 % at x = -5).  One reciprocal and one exponential
+// (the fast hardware approximations) and five FMAs.
+__device__ __forceinline__ float phi_cdf(float x, float &e) {
+  const float u = fabsf(x) * 0.70710678118654752f;
+  const float t = __fdividef(1.0f, fmaf(0.3275911f, u, 1.0f));
+  float p = fmaf(t, 1.061405429f, -1.453152027f);
+  p = fmaf(t, p, 1.421413741f);
+  p = fmaf(t, p, -0.284496736f);
+  p = fmaf(t, p, 0.254829592f);
+  p *= t;
+  e = __expf(-u * u);
+  const float tail = 0.5f * p * e;  // (1 - erf(u)) / 2
+  return x >= 0.0f ? 1.0f - tail : tail;
+}
 
+__device__ __forceinline__ float gelu_f(float x) {
+  float e;
+  return x * phi_cdf(x, e);
+}
+
+// GELU'(x) = Phi(x) + x phi(x), phi(x) = exp(-x^2 / 2) / sqrt(2 pi)
 __device__ __forceinline__ float gelu_grad_f(float x) {
-  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+  float e;
+  const float c = phi_cdf(x, e);
+  return fmaf(x * 0.39894228040143268f, e, c);
 }
 
 __device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const void *smem) {

@@ -185,12 +185,13 @@ def test_valid_mechanism_needs_a_device(lib):
 
 
 def test_diag_math_validates_its_arguments(lib):
-    """chem_diag_math's operations 0-10 (the kernels' exp / log, the refined reciprocals,
-    the integer-pipe conversions and the hi/lo split) are accepted and an empty call does
-    nothing; anything else is rejected before any device work."""
-    for op in range(11):
+    """chem_diag_math's operations 0-14 (the kernels' exp / log, the refined reciprocals,
+    the integer-pipe conversions, the hi/lo split, the network's GELU and GELU' and their
+    library-erff forms) are accepted and an empty call does nothing; anything else is
+    rejected before any device work."""
+    for op in range(15):
         assert lib.chem_diag_math(op, 0, None, None, None) == chem.OK, op
-    for op in (-1, 11, 99):
+    for op in (-1, 15, 99):
         assert lib.chem_diag_math(op, 0, None, None, None) == chem.ERR_INVALID, op
     assert lib.chem_diag_math(0, -1, None, None, None) == chem.ERR_INVALID
     assert lib.chem_diag_math(4, 8, None, None, None) == chem.ERR_INVALID

@@ -141,3 +141,30 @@ def test_fma_probe_is_plausible(lib):
     assert f32 > 20 * f64, (f32, f64)
     with pytest.raises(lib.ChemError):
         lib.fma_peak(2, 1, 32, 1)
+
+
+def test_gelu_approximation_against_library_erf(lib):
+    """The network's GELU and GELU' (erf by Abramowitz & Stegun 7.1.26, error <= 1.5e-7)
+    against the same formulas with the CUDA library's erff / expf and against the exact
+    values (math.erf, fp64): within 4e-7 absolute plus 4 fp32 ulps of the value, far
+    inside the BF16 rounding (2^-8 relative) that follows them; negative tails keep their
+    relative accuracy below BF16's (no cancellation of 1 + erf: 0.16 % at x = -5)."""
+    import math
+    x = np.concatenate([np.linspace(-9.0, 9.0, 200001), [0.0, -0.0, 1e-30, -1e-30]])
+    xf = x.astype(np.float32).astype(np.float64)
+    g = lib.diag_math(11, _dev(x)).cpu().numpy()
+    gd = lib.diag_math(12, _dev(x)).cpu().numpy()
+    g_lib = lib.diag_math(13, _dev(x)).cpu().numpy()
+    gd_lib = lib.diag_math(14, _dev(x)).cpu().numpy()
+    erf = np.vectorize(math.erf)
+    Phi = 0.5 * (1.0 + erf(xf / math.sqrt(2.0)))
+    g_ex = xf * Phi
+    gd_ex = Phi + xf * np.exp(-0.5 * xf * xf) / math.sqrt(2.0 * math.pi)
+    tol = lambda v: 4e-7 * np.maximum(1.0, np.abs(xf)) + 4 * np.spacing(np.abs(v).astype(np.float32)).astype(np.float64)
+    assert np.all(np.abs(g - g_ex) <= tol(g_ex)), np.max(np.abs(g - g_ex))
+    assert np.all(np.abs(gd - gd_ex) <= tol(gd_ex)), np.max(np.abs(gd - gd_ex))
+    assert np.all(np.abs(g - g_lib) <= tol(g_ex) + np.abs(g_lib - g_ex))
+    assert np.all(np.abs(gd - gd_lib) <= tol(gd_ex) + np.abs(gd_lib - gd_ex))
+    # the negative tail: relative accuracy of GELU(-5) ~ -1.4e-6 below BF16's 2^-8
+    i = np.argmin(np.abs(xf + 5.0))
+    assert abs(g[i] - g_ex[i]) <= 2e-3 * abs(g_ex[i])
