@@ -334,7 +334,9 @@ MLP_FLOPS_PER_ROW = 2 * (16 * 256 + 256 * 256 * 2 + 256 * 16)  # padded 16-256-2
 # DRAM bytes (read + write) per cell of one k_lsrk launch (dram__bytes_read.sum +
 # dram__bytes_write.sum), from an ncu capture of the 131,072-cell slice, scaled by the
 # cell count; to be set to None whenever the kernel changes until it is captured again.
-TRAFFIC_PER_CELL = {"fp64": 12.731904e6 / 131072, "mixed": 12.723200e6 / 131072}  # mean of 2 launches each
+# fp64: 12.73 MB per 131,072-cell launch (mean of 2); mixed: 12.73 MB (mean of 4 launches of
+# the current kernel)
+TRAFFIC_PER_CELL = {"fp64": 12.731904e6 / 131072, "mixed": 12.728064e6 / 131072}
 
 
 def _bf16_peak():
