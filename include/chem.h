@@ -646,6 +646,22 @@ int chem_diag_math(int op, int64_t n, const double *d_x, double *d_y, void *stre
 int chem_diag_fma_peak(int op, int32_t blocks, int32_t threads, int64_t iters, void *d_sink,
                        void *stream);
 
+/*
+ * Diagnostic: the equilibrium exponents ln(1 / K_c,j) = sum_k nu_jk g_k / (R_u T)
+ * + (sum_k nu_jk) ln(R_u T / p_ref) (Sec. 2.2.3: the reverse rates k_r = k_f / K_c of the
+ * law of mass action) of every reaction of the context's mechanism at n temperatures
+ * d_T (device, fp64, kelvin, > 0; non-positive values give NaN), written to d_out
+ * (device, n * n_reactions fp64, row i = temperature i, the fp32 results widened
+ * exactly), as the mixed-precision right-hand sides form them: form 0 the mixed
+ * variant's (fp64 Gibbs functions summed as fp32 hi/lo pairs), form 1 the all-fp32 one of
+ * the surrogate's error test.  The plain fp64 variant never forms ln K_c (it multiplies
+ * exp(-g_k / (R_u T)) factors) and has no form here.  Errors: NULL ctx, form not 0 or 1,
+ * n outside [0, 2^30] or NULL pointers with n > 0 -> CHEM_ERR_INVALID; a failed launch ->
+ * CHEM_ERR_CUDA.  Asynchronous on stream.
+ */
+int chem_diag_ln_inv_kc(chem_ctx *ctx, int form, int64_t n, const double *d_T, double *d_out,
+                        void *stream);
+
 /* Library version, as major * 10000 + minor * 100 + patch. */
 int chem_version(void);
 

@@ -145,6 +145,7 @@ def load(n_species: int = 9) -> C.CDLL:
         "chem_integrate_host": (C.c_int, [vp, i64, vp, vp, vp, i64, vp, vp, vp, vp, dbl, dbl, dbl, vp]),
         "chem_diag_math": (C.c_int, [C.c_int, i64, vp, vp, vp]),
         "chem_diag_fma_peak": (C.c_int, [C.c_int, C.c_int32, C.c_int32, i64, vp, vp]),
+        "chem_diag_ln_inv_kc": (C.c_int, [vp, C.c_int, i64, vp, vp, vp]),
         "chem_integrate_batched": (C.c_int, [vp, C.POINTER(State), i64, C.POINTER(Batch), dbl, dbl,
                                              C.POINTER(BatchOptions), vp, vp]),
         "chem_batch_shape_info": (C.c_int, [vp, C.c_int32, vp, vp, vp]),
@@ -589,6 +590,18 @@ class Context:
         self._raise(self.L.chem_surrogate_forward(self.h, _ptr(X), B, _ptr(Y), impl, _stream(stream),
                                                   C.byref(err) if check else None))
         return (Y, err.value) if check else Y
+
+    def ln_inv_kc(self, T, form=0, stream=None):
+        """chem_diag_ln_inv_kc: ln(1 / K_c) of every reaction at the temperatures T (a
+        float64 CUDA vector) as the mixed right-hand side (form 0) or the all-fp32 error
+        test (form 1) forms it; returns a float64 [n, n_reactions] tensor."""
+        import torch
+        _check_f64_cuda("T", T)
+        T = T.contiguous()
+        out = torch.empty((T.numel(), int(self._mech.n_reactions)), dtype=torch.float64, device=T.device)
+        self._raise(self.L.chem_diag_ln_inv_kc(self.h, int(form), T.numel(), _ptr(T), _ptr(out),
+                                               _stream(stream)))
+        return out
 
     def integrate_host(self, rho, e, Y, T, dt, rtol=1e-6, atol=1e-10, h=None, status=None,
                        nsteps=None, stream=None):

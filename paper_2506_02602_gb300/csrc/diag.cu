@@ -1,12 +1,17 @@
 // diag.cu -- diagnostics: chem_diag_math (the kernels' device math routines on caller
-// arrays, for accuracy tests against the CUDA library and the IEEE-754 definitions) and
+// arrays, for accuracy tests against the CUDA library and the IEEE-754 definitions),
 // chem_diag_fma_peak (an FMA-throughput probe of the fp64 and fp32 pipes, the
-// denominators of the integrators' compute roofline).
+// denominators of the integrators' compute roofline) and chem_diag_ln_inv_kc (the
+// equilibrium exponents as the mixed-precision right-hand sides form them).
 #include <cuda_runtime.h>
+
+#include <string>
+#include <utility>
 
 #include "fastmath.cuh"
 #include "internal.cuh"
 #include "mma.cuh"
+#include "rhs_mixed.cuh"
 
 namespace chem {
 
@@ -76,6 +81,34 @@ __global__ void k_fma_coefs(R *ab, R a, R b) {
   ab[1] = b;
 }
 
+template <typename Gibbs, int... J>
+__device__ __forceinline__ void store_ln_inv_kc(const Gibbs &g, double *o, std::integer_sequence<int, J...>) {
+  ((o[J] = (double)ln_inv_kc<J>(g)), ...);
+}
+
+// ln(1 / K_c,j) of every reaction at T[i] into out[i * NRX + j], through the same
+// helpers the right-hand sides call: form 0 the mixed variant's (fp64 Gibbs functions
+// summed as fp32 hi/lo pairs, after the fp64 ln T and 1 / T it takes from the
+// temperature solve), form 1 the error test's all-fp32 one.
+__global__ void k_ln_inv_kc(const __grid_constant__ MechTables mt, int form, int64_t n,
+                            const double *__restrict__ T, double *__restrict__ out) {
+  load_math_tables();  // log_t reads the per-block tables
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double t = T[i];
+  double *o = out + i * NRX;
+  if (form == 0) {
+    GibbsHL g;
+    gibbs_hl(mt, t, log_t(t), rcp1(t), g);
+    store_ln_inv_kc(g, o, std::make_integer_sequence<int, NRX>{});
+  } else {
+    const float tf = (float)t;
+    GibbsF g;
+    gibbs_f(mt, tf, logf(tf), 1.0f / tf, g);
+    store_ln_inv_kc(g, o, std::make_integer_sequence<int, NRX>{});
+  }
+}
+
 }  // namespace chem
 
 extern "C" int chem_diag_fma_peak(int op, int32_t blocks, int32_t threads, int64_t iters,
@@ -106,4 +139,29 @@ extern "C" int chem_diag_math(int op, int64_t n, const double *d_x, double *d_y,
   const int block = 256;
   chem::k_diag_math<<<(unsigned)((n + block - 1) / block), block, 0, (cudaStream_t)stream>>>(op, n, d_x, d_y);
   return cudaGetLastError() == cudaSuccess ? CHEM_OK : CHEM_ERR_CUDA;
+}
+
+extern "C" int chem_diag_ln_inv_kc(chem_ctx *ctx, int form, int64_t n, const double *d_T, double *d_out,
+                                   void *stream) {
+  if (!ctx) return CHEM_ERR_INVALID;
+  std::string &err = chem::chem_ctx_error(ctx);
+  if ((form != 0 && form != 1) || n < 0 || n > (int64_t(1) << 30)) {
+    err = "chem_diag_ln_inv_kc: form must be 0 or 1 and n in [0, 2^30], got form " + std::to_string(form) +
+          ", n " + std::to_string(n);
+    return CHEM_ERR_INVALID;
+  }
+  if (n == 0) return CHEM_OK;
+  if (!d_T || !d_out) {
+    err = "chem_diag_ln_inv_kc: NULL d_T or d_out";
+    return CHEM_ERR_INVALID;
+  }
+  const int block = 128;
+  chem::k_ln_inv_kc<<<(unsigned)((n + block - 1) / block), block, 0, (cudaStream_t)stream>>>(
+      chem::chem_ctx_tables(ctx), form, n, d_T, d_out);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    err = std::string("chem_diag_ln_inv_kc: ") + cudaGetErrorString(e);
+    return CHEM_ERR_CUDA;
+  }
+  return CHEM_OK;
 }

@@ -55,6 +55,34 @@ struct GibbsF {
   float r;
 };
 
+// g_k / RT = a1 (1 - ln T) - a2 T / 2 - ... - a5 T^4 / 20 + a6 / T - a7 (NASA-7, with the
+// coefficients pre-combined per range into gc) and ln(R_u T / p_ref), evaluated in fp64
+// and split into fp32 hi/lo pairs.
+__device__ __forceinline__ void gibbs_hl(const MechTables &mt, double T, double lnT, double invT, GibbsHL &g) {
+  const double oml = 1.0 - lnT;
+  const int range = ge_nonneg(T, mt.T_mid);
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) {
+    const double *gc = mt.gc[range][k];
+    const double gk = fma(T, fma(T, fma(T, fma(T, gc[4], gc[3]), gc[2]), gc[1]), fma(gc[5], invT, gc[6]));
+    split_hilo(fma(gc[0], oml, gk), g.h[k], g.l[k]);
+  }
+  split_hilo(lnT + mt.ln_R_over_Pref, g.rh, g.rl);
+}
+
+// The same functions evaluated entirely in fp32 (the error test's right-hand side).
+__device__ __forceinline__ void gibbs_f(const MechTables &mt, float T, float lnT, float invT, GibbsF &g) {
+  const float oml = 1.0f - lnT;
+  const int range = T >= mt.f.T_mid;
+#pragma unroll
+  for (int k = 0; k < NSP; ++k) {
+    const float *gc = mt.f.gc[range][k];
+    const float gk = fmaf(T, fmaf(T, fmaf(T, fmaf(T, gc[4], gc[3]), gc[2]), gc[1]), fmaf(gc[5], invT, gc[6]));
+    g.g[k] = fmaf(gc[0], oml, gk);
+  }
+  g.r = lnT + mt.f.ln_R_over_Pref;
+}
+
 template <int J>
 __device__ __forceinline__ float ln_inv_kc(const GibbsHL &g) {
   constexpr RxStruct R = kRx[J];
@@ -133,16 +161,8 @@ __device__ __forceinline__ bool cell_rhs_mixed(const MechTables &mt, const float
   if (!solve_T(mt, Y, eR, T)) return false;
   const double lnT = log_t(T);
   const double invT = rcp1(T);
-  const double oml = 1.0 - lnT;
-  const int range = ge_nonneg(T, mt.T_mid);
   GibbsHL g;
-#pragma unroll
-  for (int k = 0; k < NSP; ++k) {
-    const double *gc = mt.gc[range][k];
-    const double gk = fma(T, fma(T, fma(T, fma(T, gc[4], gc[3]), gc[2]), gc[1]), fma(gc[5], invT, gc[6]));
-    split_hilo(fma(gc[0], oml, gk), g.h[k], g.l[k]);
-  }
-  split_hilo(lnT + mt.ln_R_over_Pref, g.rh, g.rl);
+  gibbs_hl(mt, T, lnT, invT, g);
   RateInputsF in;
   in.lnT = d2f(lnT);
   in.invT = d2f(invT);
@@ -209,16 +229,8 @@ __device__ __forceinline__ bool cell_rhs_f32(const MechTables &mt, const float (
   if (!solve_T_f32(mt, yw, eR, T)) return false;
   const float lnT = logf(T);
   const float invT = 1.0f / T;
-  const float oml = 1.0f - lnT;
-  const int range = T >= mt.f.T_mid;
   GibbsF g;
-#pragma unroll
-  for (int k = 0; k < NSP; ++k) {
-    const float *gc = mt.f.gc[range][k];
-    const float gk = fmaf(T, fmaf(T, fmaf(T, fmaf(T, gc[4], gc[3]), gc[2]), gc[1]), fmaf(gc[5], invT, gc[6]));
-    g.g[k] = fmaf(gc[0], oml, gk);
-  }
-  g.r = lnT + mt.f.ln_R_over_Pref;
+  gibbs_f(mt, T, lnT, invT, g);
   RateInputsF in;
   in.lnT = lnT;
   in.invT = invT;

@@ -165,6 +165,12 @@ def test_fma_probe_validates_its_arguments(lib):
     assert lib.chem_diag_fma_peak(0, 1, 32, 1, None, None) == chem.ERR_INVALID
 
 
+def test_ln_inv_kc_diagnostic_rejects_a_missing_context(lib):
+    """chem_diag_ln_inv_kc needs a context (its mechanism tables) and refuses NULL
+    before launching anything."""
+    assert lib.chem_diag_ln_inv_kc(None, 0, 4, C.c_void_p(8), C.c_void_p(8), None) == chem.ERR_INVALID
+
+
 def test_setup_matches_structure_to_library(lib):
     """The 13-species mechanism is refused by the 9-species library (and the other way
     round) before any device is touched."""
