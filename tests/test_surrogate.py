@@ -139,6 +139,31 @@ def test_forward_backward_elementwise_vs_fp64_oracle(lib):
     ctx.close()
 
 
+def test_tcgen05_network_with_many_tiles_per_cta(lib):
+    """The inference kernel keeps two 128-row tiles in flight per CTA (one epilogue group
+    each) over a persistent grid: on 3 tiles per SM plus a ragged end (pairs, a lone last
+    tile, a partial tile) every output meets the element bound against the oracle, and a
+    row's result does not depend on which CTA, group or position processed it."""
+    import torch
+    ctx = lib.Context(MECH, "fp64")
+    params, _ = _bf16_network(ctx, seed=11)
+    big = 152 * 128 * 3 + 77
+    Xb, _ = _batch(big, seed=12)
+    Xd = Xb.cuda()
+    Y, err = ctx.surrogate_forward(Xd, check=True)
+    assert err == 0
+    Y = Y.cpu().numpy()
+    x64 = Xb.numpy().astype(np.float64)[:, :12]
+    Yo, Dy, _, _ = BB.e2e_reference(params, x64, np.zeros((big, 9)))
+    ratio = np.abs(Y[:, :9] - Yo) / Dy
+    assert ratio.max() <= 1.0, ratio.max()
+    assert np.all(Y[:, 9:] == 0.0)
+    for r0, r1 in ((0, 512), (300 * 128, 301 * 128), (big - 77 - 128, big)):
+        Ys = ctx.surrogate_forward(Xd[r0:r1].contiguous()).cpu().numpy()
+        np.testing.assert_array_equal(Ys, Y[r0:r1])
+    ctx.close()
+
+
 def test_every_network_stage_elementwise(lib):
     """chem_surrogate_trace: each stage against the oracle's arithmetic on the GPU's own
     inputs to that stage (rigorous FP32 / BF16 bounds, element by element)."""
