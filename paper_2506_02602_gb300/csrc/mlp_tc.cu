@@ -327,12 +327,16 @@ __global__ void __launch_bounds__(TTHREADS, 1) k_mlp_tc(const __grid_constant__ 
           auto emit = [&](const uint32_t(&r)[32], int c32) {
 #pragma unroll
             for (int g4 = 0; g4 < 4; ++g4) {
-              __align__(16) __nv_bfloat16 hb[8];
+              uint32_t pk[4];
 #pragma unroll
-              for (int i = 0; i < 8; ++i)
-                hb[i] = __float2bfloat16(gelu_f(__uint_as_float(r[g4 * 8 + i]) + bl[c32 + g4 * 8 + i]));
+              for (int i = 0; i < 4; ++i) {
+                const int j = g4 * 8 + 2 * i;
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(gelu_f(__uint_as_float(r[j]) + bl[c32 + j]),
+                                                                gelu_f(__uint_as_float(r[j + 1]) + bl[c32 + j + 1]));
+                pk[i] = *reinterpret_cast<const uint32_t *>(&h2);
+              }
               *reinterpret_cast<uint4 *>(sH + core_off(row, ch * COLS_PER_WARP + c32 + g4 * 8, kSurHidden)) =
-                  *reinterpret_cast<const uint4 *>(hb);
+                  make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
           };
           static_assert(COLS_PER_WARP == 128, "four 32-column chunks per warp");
