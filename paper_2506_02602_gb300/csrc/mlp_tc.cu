@@ -268,8 +268,8 @@ __global__ void __launch_bounds__(TTHREADS, 1) k_mlp_tc(const __grid_constant__ 
     const int gtid = tid - g * GWARPS * 32;
     const int row = q * 32 + lane;  // this thread's accumulator lane
     const uint32_t t_lane = tmem + (uint32_t)(g * kSurHidden) + ((uint32_t)(q * 32) << 16);
-    unsigned char *sX = sm + SM_X + (uint32_t)g * kXBytes;
-    unsigned char *sH = sm + SM_H + (uint32_t)g * kHBytes;
+    const uint32_t sX32 = sbase + SM_X + (uint32_t)g * kXBytes;
+    const uint32_t sH32 = sbase + SM_H + (uint32_t)g * kHBytes;
     const uint32_t b_mma = barrier_addr(BAR_MMA0 + g), b_ready = barrier_addr(BAR_HREADY0 + g);
     uint32_t mma_ph = 0;
     auto ready = [&]() {  // this warp's part of the next A operand is written
@@ -310,10 +310,13 @@ __global__ void __launch_bounds__(TTHREADS, 1) k_mlp_tc(const __grid_constant__ 
 #pragma unroll
           for (int i = 0; i < 8; ++i) v[i] = 0.0f;
         }
-        __align__(16) __nv_bfloat16 hb[8];
+        uint32_t pk[4];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) hb[i] = __float2bfloat16(v[i]);
-        *reinterpret_cast<uint4 *>(sX + core_off(r, c0, kSurIn)) = *reinterpret_cast<const uint4 *>(hb);
+        for (int i = 0; i < 4; ++i) {
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+          pk[i] = *reinterpret_cast<const uint32_t *>(&h2);
+        }
+        sts128(sX32 + core_off(r, c0, kSurIn), pk[0], pk[1], pk[2], pk[3]);
       }
       ready();
       for (int layer = 0; layer < kSurLayers; ++layer) {
@@ -322,21 +325,24 @@ __global__ void __launch_bounds__(TTHREADS, 1) k_mlp_tc(const __grid_constant__ 
           break;
         }
         if (layer < 3) {
-          const float *bl = sbias + layer * kSurHidden + ch * COLS_PER_WARP;
+          const uint32_t sB = sbase + SM_BIAS + (uint32_t)((layer * kSurHidden + ch * COLS_PER_WARP) * 4);
           const uint32_t tc = t_lane + (uint32_t)(ch * COLS_PER_WARP);
           auto emit = [&](const uint32_t(&r)[32], int c32) {
 #pragma unroll
             for (int g4 = 0; g4 < 4; ++g4) {
+              const float4 b0 = lds128(sB + (uint32_t)(c32 + g4 * 8) * 4);
+              const float4 b1 = lds128(sB + (uint32_t)(c32 + g4 * 8 + 4) * 4);
+              const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
               uint32_t pk[4];
 #pragma unroll
               for (int i = 0; i < 4; ++i) {
                 const int j = g4 * 8 + 2 * i;
-                const __nv_bfloat162 h2 = __floats2bfloat162_rn(gelu_f(__uint_as_float(r[j]) + bl[c32 + j]),
-                                                                gelu_f(__uint_as_float(r[j + 1]) + bl[c32 + j + 1]));
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(gelu_f(__uint_as_float(r[j]) + bv[2 * i]),
+                                                                gelu_f(__uint_as_float(r[j + 1]) + bv[2 * i + 1]));
                 pk[i] = *reinterpret_cast<const uint32_t *>(&h2);
               }
-              *reinterpret_cast<uint4 *>(sH + core_off(row, ch * COLS_PER_WARP + c32 + g4 * 8, kSurHidden)) =
-                  make_uint4(pk[0], pk[1], pk[2], pk[3]);
+              sts128(sH32 + core_off(row, ch * COLS_PER_WARP + c32 + g4 * 8, kSurHidden), pk[0], pk[1], pk[2],
+                     pk[3]);
             }
           };
           static_assert(COLS_PER_WARP == 128, "four 32-column chunks per warp");

@@ -23,21 +23,46 @@ struct RateInputsF {
   float c[NSP];
 };
 
-template <int J>
+// fp32 transcendentals and divisions of the rate expressions: the CUDA library's
+// accurate functions for the integrator, or its fast intrinsics (hardware base-2
+// exponential and logarithm, approximate division; relative errors ~1e-6 on these
+// arguments) for the error test's estimator, which compares with a tolerance of ~5e-4 T.
+template <bool FAST>
+__device__ __forceinline__ float exp_r(float x) {
+  if constexpr (FAST) return __expf(x); else return expf(x);
+}
+template <bool FAST>
+__device__ __forceinline__ float log_r(float x) {
+  if constexpr (FAST) return __logf(x); else return logf(x);
+}
+template <bool FAST>
+__device__ __forceinline__ float log10_r(float x) {
+  if constexpr (FAST) return __log10f(x); else return log10f(x);
+}
+template <bool FAST>
+__device__ __forceinline__ float exp10_r(float x) {
+  if constexpr (FAST) return __exp10f(x); else return exp10f(x);
+}
+template <bool FAST>
+__device__ __forceinline__ float div_r(float a, float b) {
+  if constexpr (FAST) return __fdividef(a, b); else return a / b;
+}
+
+template <int J, bool FAST>
 __device__ __forceinline__ float troe_F_f32(const MechTables &mt, float T, float invT, float Pr) {
   constexpr int n = kRx[J].troe_n;
   if constexpr (n == 0) {
     return 1.0f;
   } else {
     const float a = mt.f.troe_a[J];
-    float Fc = (1.0f - a) * expf(-T * mt.f.troe_i3[J]) + a * expf(-T * mt.f.troe_i1[J]);
-    if constexpr (n == 4) Fc += expf(-mt.f.troe_T2[J] * invT);
-    const float lFc = log10f(Fc);
+    float Fc = (1.0f - a) * exp_r<FAST>(-T * mt.f.troe_i3[J]) + a * exp_r<FAST>(-T * mt.f.troe_i1[J]);
+    if constexpr (n == 4) Fc += exp_r<FAST>(-mt.f.troe_T2[J] * invT);
+    const float lFc = log10_r<FAST>(Fc);
     const float cc = -0.4f - 0.67f * lFc;
     const float nn = 0.75f - 1.27f * lFc;
-    const float x = log10f(Pr) + cc;
-    const float f1 = x / (nn - 0.14f * x);
-    return exp10f(lFc / (1.0f + f1 * f1));
+    const float x = log10_r<FAST>(Pr) + cc;
+    const float f1 = div_r<FAST>(x, nn - 0.14f * x);
+    return exp10_r<FAST>(div_r<FAST>(lFc, 1.0f + f1 * f1));
   }
 }
 
@@ -107,12 +132,12 @@ __device__ __forceinline__ float ln_inv_kc(const GibbsF &g) {
   return q;
 }
 
-template <int J, typename Gibbs>
+template <int J, bool FAST, typename Gibbs>
 __device__ __forceinline__ void reaction_mixed(const MechTables &mt, const RateInputsF &in,
                                                const Gibbs &g, float (&wdot)[NSP]) {
   constexpr RxStruct R = kRx[J];
   float lnkf = fmaf(mt.f.beta[J], in.lnT, mt.f.lnA[J]) - mt.f.Ta[J] * in.invT;
-  float kf = mt.kconst[J] == 1 ? mt.f.A[J] : expf(lnkf);
+  float kf = mt.kconst[J] == 1 ? mt.f.A[J] : exp_r<FAST>(lnkf);
   float M = 0.0f;
   if constexpr (R.type != ELEM) {
     M = in.ctot;
@@ -122,16 +147,16 @@ __device__ __forceinline__ void reaction_mixed(const MechTables &mt, const RateI
     }
   }
   if constexpr (R.type == FALLOFF) {
-    const float k0 = expf(fmaf(mt.f.beta0[J], in.lnT, mt.f.lnA0[J]) - mt.f.Ta0[J] * in.invT);
-    const float Pr = k0 * M / kf;
-    kf = (Pr > 0.0f) ? kf * (Pr / (1.0f + Pr)) * troe_F_f32<J>(mt, in.T, in.invT, Pr) : 0.0f;
-    lnkf = logf(kf);
+    const float k0 = exp_r<FAST>(fmaf(mt.f.beta0[J], in.lnT, mt.f.lnA0[J]) - mt.f.Ta0[J] * in.invT);
+    const float Pr = div_r<FAST>(k0 * M, kf);
+    kf = (Pr > 0.0f) ? kf * div_r<FAST>(Pr, 1.0f + Pr) * troe_F_f32<J, FAST>(mt, in.T, in.invT, Pr) : 0.0f;
+    lnkf = log_r<FAST>(kf);
   }
   float qf = kf * in.c[R.r0];
   if constexpr (R.r1 >= 0) qf *= in.c[R.r1];
   float q = qf;
   if (mt.reversible[J]) {
-    const float kr = (kf > 0.0f) ? expf(lnkf + ln_inv_kc<J>(g)) : 0.0f;
+    const float kr = (kf > 0.0f) ? exp_r<FAST>(lnkf + ln_inv_kc<J>(g)) : 0.0f;
     float qr = kr * in.c[R.p0];
     if constexpr (R.p1 >= 0) qr *= in.c[R.p1];
     q = qf - qr;
@@ -143,11 +168,11 @@ __device__ __forceinline__ void reaction_mixed(const MechTables &mt, const RateI
   if constexpr (R.p1 >= 0) wdot[R.p1] += q;
 }
 
-template <typename Gibbs, int... J>
+template <bool FAST, typename Gibbs, int... J>
 __device__ __forceinline__ void all_reactions_mixed(const MechTables &mt, const RateInputsF &in,
                                                     const Gibbs &g, float (&wdot)[NSP],
                                                     std::integer_sequence<int, J...>) {
-  (reaction_mixed<J, Gibbs>(mt, in, g, wdot), ...);
+  (reaction_mixed<J, FAST, Gibbs>(mt, in, g, wdot), ...);
 }
 
 // dY/dt (fp32) of one cell at fixed (rho, e) from the fp32 stage state U.
@@ -175,7 +200,7 @@ __device__ __forceinline__ bool cell_rhs_mixed(const MechTables &mt, const float
     wdot[k] = 0.0f;
   }
   in.ctot = ctot;
-  all_reactions_mixed(mt, in, g, wdot, std::make_integer_sequence<int, NRX>{});
+  all_reactions_mixed<false>(mt, in, g, wdot, std::make_integer_sequence<int, NRX>{});
 #pragma unroll
   for (int k = 0; k < NSP; ++k) F[k] = wdot[k] * mt.f.W[k] * invRho_f;
   return true;
@@ -207,7 +232,7 @@ __device__ __forceinline__ bool solve_T_f32(const MechTables &mt, const float (&
     }
     const float eT = fmaf(Tn, fmaf(Tn, fmaf(Tn, fmaf(Tn, fmaf(Tn, m[4], m[3]), m[2]), m[1]), m[0]), m[5]);
     const float cv = fmaf(Tn, fmaf(Tn, fmaf(Tn, fmaf(Tn, d[4], d[3]), d[2]), d[1]), d[0]);
-    const float dT = (eT - eR) / cv;
+    const float dT = __fdividef(eT - eR, cv);
     Tn -= dT;
     if (!isfinite(Tn) || Tn <= 0.0f) return false;
     if (fabsf(dT) <= 2e-6f * Tn) {
@@ -219,16 +244,16 @@ __device__ __forceinline__ bool solve_T_f32(const MechTables &mt, const float (&
 }
 
 // dY/dt of one cell entirely in fp32 (temperature, Gibbs functions and ln(1/K_c)
-// included): the right-hand side of the surrogate's error test, an estimator that
-// needs relative accuracy far coarser than fp32's.  T: in = guess, out = solved T.
+// included) with the fast intrinsics: the right-hand side of the surrogate's error test,
+// an estimator that needs relative accuracy far coarser than fp32's.  T: in = guess, out = solved T.
 __device__ __forceinline__ bool cell_rhs_f32(const MechTables &mt, const float (&U)[NSP], float rho,
                                              float invRho, float eR, float &T, float (&F)[NSP]) {
   float yw[NSP];
 #pragma unroll
   for (int k = 0; k < NSP; ++k) yw[k] = U[k] * mt.f.invW[k];
   if (!solve_T_f32(mt, yw, eR, T)) return false;
-  const float lnT = logf(T);
-  const float invT = 1.0f / T;
+  const float lnT = __logf(T);
+  const float invT = __fdividef(1.0f, T);
   GibbsF g;
   gibbs_f(mt, T, lnT, invT, g);
   RateInputsF in;
@@ -243,7 +268,7 @@ __device__ __forceinline__ bool cell_rhs_f32(const MechTables &mt, const float (
     wdot[k] = 0.0f;
   }
   in.ctot = ctot;
-  all_reactions_mixed(mt, in, g, wdot, std::make_integer_sequence<int, NRX>{});
+  all_reactions_mixed<true>(mt, in, g, wdot, std::make_integer_sequence<int, NRX>{});
 #pragma unroll
   for (int k = 0; k < NSP; ++k) F[k] = wdot[k] * mt.f.W[k] * invRho;
   return true;

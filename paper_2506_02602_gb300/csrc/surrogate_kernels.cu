@@ -30,6 +30,7 @@
 // share of the mixture energy is under ~1 K).  A trapezoidal check (two right-hand
 // sides) was tried first: its O(dt^3) truncation can cancel a surrogate error of the
 // same size, which let a few cells through with twice the tolerated error.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -172,9 +173,10 @@ __global__ void k_normalize(int64_t n, int ncol, int ld, float *A, const float *
 
 // Temperature-error estimate of a surrogate result y1 (see the file comment): returns
 // false if a right-hand side fails, else sets dT = est (K) and rate = dt * the largest
-// relative rate of change at either end.  All in fp32 (cell_rhs_f32), whatever the
-// context's variant: an estimate compared with a tolerance of ~5e-4 T needs nothing
-// finer; y1 - y0 is formed in fp64 first, so the defect does not lose it to rounding.
+// relative rate of change at either end.  All in fp32 with the fast intrinsics
+// (cell_rhs_f32), whatever the context's variant: an estimate compared with a tolerance
+// of ~5e-4 T needs nothing finer; y1 - y0 is formed in fp64 first, so the defect does not
+// lose it to rounding.
 __device__ __noinline__ bool posterior_error(const MechTables &mt, const double (&y0)[NSP],
                                              const double (&y1)[NSP], float rho_f, float eR,
                                              float T0, float T1f, float dtf, float &dT, float &rate) {
@@ -184,7 +186,7 @@ __device__ __noinline__ bool posterior_error(const MechTables &mt, const double 
     u0[k] = d2f(y0[k]);
     u1[k] = d2f(y1[k]);
   }
-  const float invRho_f = 1.0f / rho_f;
+  const float invRho_f = __fdividef(1.0f, rho_f);
   float Ta = T0, Tb = T1f;
   if (!cell_rhs_f32(mt, u0, rho_f, invRho_f, eR, Ta, F0) || !cell_rhs_f32(mt, u1, rho_f, invRho_f, eR, Tb, F1))
     return false;
@@ -211,10 +213,10 @@ __device__ __noinline__ bool posterior_error(const MechTables &mt, const double 
         fmaf(T1f, fmaf(T1f, fmaf(T1f, fmaf(T1f, fmaf(T1f, c[4], c[3]), c[2]), c[1]), c[0]), c[5]) * mt.f.invW[k];
     const float defect = d2f(y1[k] - y0[k]) - sdt * (F0[k] + 4.0f * Fm[k] + F1[k]);
     sum = fmaf(fabsf(ukR - eR), fabsf(defect), sum);
-    r = fmaxf(r, fmaxf(fabsf(F0[k]) / (fabsf(u0[k]) + 1e-6f), fabsf(F1[k]) / (fabsf(u1[k]) + 1e-6f)));
+    r = fmaxf(r, fmaxf(__fdividef(fabsf(F0[k]), fabsf(u0[k]) + 1e-6f), __fdividef(fabsf(F1[k]), fabsf(u1[k]) + 1e-6f)));
   }
   rate = dtf * r;
-  dT = sum / cvR;
+  dT = __fdividef(sum, cvR);
   return isfinite(dT) && cvR > 0.0f;
 }
 
@@ -366,7 +368,11 @@ __global__ void __launch_bounds__(128, 4)
     if (mask) mask[i] = 0;
   } else {
     if (mask) mask[i] = (uint8_t)reason;
-    const unsigned slot = atomicAdd(fb_count, 1u);
+    // one atomic per group of rejecting lanes, each lane at its rank after the group's base
+    const cooperative_groups::coalesced_group grp = cooperative_groups::coalesced_threads();
+    unsigned slot = 0;
+    if (grp.thread_rank() == 0) slot = atomicAdd(fb_count, grp.size());
+    slot = grp.shfl(slot, 0) + grp.thread_rank();
     fb_idx[slot] = (int32_t)(base + i);
   }
 }
