@@ -7,7 +7,8 @@ its results must match the allocating entry point (chem_integrate_batched) on th
 inputs.  They are checked here within the FP64 parity tolerance, on two calls in a row,
 because each call reuses the array the previous one left behind.  Requests beyond the
 fixed maximum are rejected before any launch, and the binding rejects tensors that are
-too short for the requested cell count.
+too short for the requested cell count.  Both queue orders (stiffness key or index order)
+and a caller's cost hint give the same per-cell results.
 
 This file is named to be collected last.
 """
@@ -31,7 +32,7 @@ def _inputs(seed, nboxes):
     return b
 
 
-def _run(ctx, b, noalloc):
+def _run(ctx, b, noalloc, **opts):
     import torch
     dev = lambda a, dt=torch.float64: torch.tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
     n = b["T"].size
@@ -41,7 +42,7 @@ def _run(ctx, b, noalloc):
     args = (dev(b["rho"]), dev(b["e"]), Y, T, dev(b["box_offset"], torch.int64),
             dev(b["box_dt"]), dev(b["box_nsub"], torch.int32))
     if noalloc:
-        ctx.integrate_batched_noalloc(*args, status=st, nsteps=ns)
+        ctx.integrate_batched_noalloc(*args, status=st, nsteps=ns, **opts)
     else:
         ctx.integrate_batched(*args, status=st, nsteps=ns)
     torch.cuda.synchronize()
@@ -62,6 +63,30 @@ def test_noalloc_matches_batched_on_two_calls(variant):
         np.testing.assert_array_equal(nn, nr)
         assert np.max(np.abs(Tn - Tr) / Tr) <= TOL_T
         assert np.max(np.abs(Yn - Yr)) <= TOL_Y
+    ctx.close()
+
+
+@pytest.mark.parametrize("queue", ["natural", "cost_hint"])
+def test_noalloc_other_queue_orders(queue):
+    """The other queue orders of the allocation-free entry: cells in index order, and cells
+    ordered by a caller's per-cell cost (here the step counts of a previous call); only
+    the schedule changes, so the results match the allocating entry point's."""
+    import torch
+    from paper_2506_02602_gb300 import build, chem
+    build.build()
+    ctx = chem.Context(M.build(0), "fp64")
+    b = _inputs(33, 40)
+    Yr, Tr, sr, nr = _run(ctx, b, noalloc=False)
+    if queue == "natural":
+        opts = {"order": chem.ORDER_NATURAL}
+    else:
+        opts = {"cost_hint": torch.tensor(nr, dtype=torch.int32, device="cuda")}
+    Yn, Tn, sn, nn = _run(ctx, b, noalloc=True, **opts)
+    assert np.all(sr == 0)
+    np.testing.assert_array_equal(sn, sr)
+    np.testing.assert_array_equal(nn, nr)
+    assert np.max(np.abs(Tn - Tr) / Tr) <= TOL_T
+    assert np.max(np.abs(Yn - Yr)) <= TOL_Y
     ctx.close()
 
 
