@@ -334,9 +334,9 @@ MLP_FLOPS_PER_ROW = 2 * (16 * 256 + 256 * 256 * 2 + 256 * 16)  # padded 16-256-2
 # DRAM bytes (read + write) per cell of one k_lsrk launch (dram__bytes_read.sum +
 # dram__bytes_write.sum), from an ncu capture of the 131,072-cell slice, scaled by the
 # cell count; to be set to None whenever the kernel changes until it is captured again.
-# fp64: 12.73 MB per 131,072-cell launch (mean of 2); mixed: 12.73 MB (mean of 4 launches of
-# the current kernel)
-TRAFFIC_PER_CELL = {"fp64": 12.731904e6 / 131072, "mixed": 12.728064e6 / 131072}
+# fp64: 12.84 MB per 131,072-cell launch (mean of 4 launches of the current kernel);
+# mixed: 12.73 MB (mean of 4 launches of the current kernel)
+TRAFFIC_PER_CELL = {"fp64": 12.841984e6 / 131072, "mixed": 12.728064e6 / 131072}
 
 
 def _bf16_peak():
