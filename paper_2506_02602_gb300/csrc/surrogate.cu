@@ -618,7 +618,7 @@ int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
   if (e != cudaSuccess) { cleanup(); return sur_cuda(ctx, e, "allocating training buffers"); }
   // features and targets of every pair, then their statistics
   e = launch_features(mt, n, pairs->d_rho, pairs->d_e, pairs->d_Y0, pairs->ldY0, pairs->d_T0,
-                      pairs->d_dt, 0.0, pairs->d_Y1, pairs->ldY1, s->lam, s->dt_power, X, Tg, nullptr, nullptr, st);
+                      pairs->d_dt, 0.0, pairs->d_Y1, pairs->ldY1, s->lam, s->dt_power, X, Tg, nullptr, st);
   int hkeys[4 * 32];
   for (int i = 0; i < 32; ++i) {
     hkeys[i] = INT_MAX; hkeys[32 + i] = INT_MIN; hkeys[64 + i] = INT_MAX; hkeys[96 + i] = INT_MIN;
@@ -797,7 +797,7 @@ static cudaError_t infer_range(chem_ctx *ctx, Surrogate *s, const SurrogateConst
     const int64_t base = first + off;
     const int64_t m = (n - off) < chunk ? (n - off) : chunk;
     e = launch_features(mt, m, state->d_rho + base, state->d_e + base, state->d_Y + base, state->ldY,
-                        state->d_T + base, nullptr, dt, nullptr, 0, s->lam, s->dt_power, s->Xraw, nullptr, nullptr,
+                        state->d_T + base, nullptr, dt, nullptr, 0, s->lam, s->dt_power, s->Xraw, nullptr,
                         s->Tok, st);
     if (e == cudaSuccess) e = mlp_forward(s, m, s->Xraw, s->dev_norm, s->O, st);
     if (e == cudaSuccess)

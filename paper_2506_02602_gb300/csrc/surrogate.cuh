@@ -58,8 +58,7 @@ struct SurrogateConsts {
 cudaError_t launch_features(const MechTables &mt, int64_t n, const double *rho, const double *e,
                             const double *Y0, int64_t ld0, const double *T0, const double *dt_cell,
                             double dt, const double *Y1, int64_t ld1, double lam, double dt_power,
-                            float *X, float *Tg,
-                            double *Tout, uint8_t *ok, cudaStream_t s);
+                            float *X, float *Tg, uint8_t *ok, cudaStream_t s);
 cudaError_t launch_colstats(int64_t n, int ncol, int ld, const float *A, double *sum, double *sumsq,
                             int *mnkey, int *mxkey, cudaStream_t s);
 cudaError_t launch_normalize(int64_t n, int ncol, int ld, float *A, const float *mean,

@@ -70,30 +70,33 @@ __device__ __forceinline__ double boxcox_step(double y0, float bc0, float d, flo
 
 // Raw (un-normalised) features and, when Y1 is given, targets of n cells.
 // X[i, 0:12] = T, ln p, log10 dt, BC(Y0); Tg[i, 0:9] = BC(Y1) - BC(Y0).  Padding zero.
-// Tout (nullable) receives the solved temperature; ok (nullable) 1 where T solved.
+// ok (nullable) 1 where T solved.  The features are fp32 network inputs (rounded to BF16
+// in the first layer), so T is solved in fp32 (Newton to 2e-6 T from the cell's T), the
+// same way for training and inference.
 __global__ void k_features(const __grid_constant__ MechTables mt, int64_t n, const double *rho,
                            const double *e, const double *Y0, int64_t ld0, const double *Tg0,
                            const double *dt_cell, double dt_scalar, const double *Y1, int64_t ld1,
-                           double lam, double dt_power, float *X, float *Tg, double *Tout,
-                           uint8_t *ok) {
+                           double lam, double dt_power, float *X, float *Tg, uint8_t *ok) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double y[NSP];
-  double inv_w = 0.0;
+  float yw[NSP];
+  float inv_w = 0.0f;
 #pragma unroll
   for (int k = 0; k < NSP; ++k) {
     y[k] = Y0[k * ld0 + i];
-    inv_w = fma(y[k], mt.invW[k], inv_w);
+    yw[k] = d2f(y[k]) * mt.f.invW[k];
+    inv_w += yw[k];
   }
-  double T = Tg0 ? Tg0[i] : CUDART_NAN;
-  const bool good =
-      isfinite(rho[i]) && rho[i] > 0.0 && isfinite(e[i]) && solve_T(mt, y, e[i] * (1.0 / R_U), T);
-  if (!good) T = 1500.0;
-  const double p = rho[i] * R_U * T * inv_w;
+  float T = Tg0 ? d2f(Tg0[i]) : CUDART_NAN_F;
+  const bool good = isfinite(rho[i]) && rho[i] > 0.0 && isfinite(e[i]) &&
+                    solve_T_f32(mt, yw, d2f(e[i] * (1.0 / R_U)), T);
+  if (!good) T = 1500.0f;
+  const float p = d2f(rho[i]) * (float)R_U * T * inv_w;
   const double dt = dt_cell ? dt_cell[i] : dt_scalar;
   float *x = X + i * kSurIn;
-  x[0] = d2f(T);
-  x[1] = logf(fmaxf(d2f(p), 1e-30f));
+  x[0] = T;
+  x[1] = logf(fmaxf(p, 1e-30f));
   x[2] = log10f(d2f(dt));
 #pragma unroll
   for (int k = 0; k < NSP; ++k) x[3 + k] = boxcox_f(y[k], (float)lam);
@@ -108,7 +111,6 @@ __global__ void k_features(const __grid_constant__ MechTables mt, int64_t n, con
 #pragma unroll
     for (int c = NSP; c < kSurOut; ++c) t[c] = 0.0f;
   }
-  if (Tout) Tout[i] = T;
   if (ok) ok[i] = good;
 }
 
@@ -435,11 +437,10 @@ cudaError_t launch_surrogate_stats(chem_stats *st, int64_t n, const unsigned int
 cudaError_t launch_features(const MechTables &mt, int64_t n, const double *rho, const double *e,
                             const double *Y0, int64_t ld0, const double *T0, const double *dt_cell,
                             double dt, const double *Y1, int64_t ld1, double lam, double dt_power,
-                            float *X, float *Tg,
-                            double *Tout, uint8_t *ok, cudaStream_t s) {
+                            float *X, float *Tg, uint8_t *ok, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_features<<<nblk(n, 128), 128, 0, s>>>(mt, n, rho, e, Y0, ld0, T0, dt_cell, dt, Y1, ld1, lam, dt_power, X, Tg,
-                                          Tout, ok);
+                                          ok);
   return cudaGetLastError();
 }
 
