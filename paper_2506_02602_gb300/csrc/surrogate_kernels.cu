@@ -179,7 +179,7 @@ __global__ void k_normalize(int64_t n, int ncol, int ld, float *A, const float *
 // (cell_rhs_f32), whatever the context's variant: an estimate compared with a tolerance
 // of ~5e-4 T needs nothing finer; y1 - y0 is formed in fp64 first, so the defect does not
 // lose it to rounding.
-__device__ __noinline__ bool posterior_error(const MechTables &mt, const double (&y0)[NSP],
+__device__ __forceinline__ bool posterior_error(const MechTables &mt, const double (&y0)[NSP],
                                              const double (&y1)[NSP], float rho_f, float eR,
                                              float T0, float T1f, float dtf, float &dT, float &rate) {
   float u0[NSP], u1[NSP], F0[NSP], F1[NSP];
@@ -307,7 +307,9 @@ __global__ void k_project_check(const __grid_constant__ SurrogateConsts sc, int6
 }
 
 // 4 blocks of 128 per SM (16 warps): the register cap of 128 costs 4 bytes of spill
-// stores, against 8 warps at the uncapped 255 registers.
+// stores, against 8 warps at the uncapped 255 registers.  The error test is inlined: as a
+// called function it took its state arrays by reference through a ~580-byte local
+// stack frame, and the kernel ran 10-14 % slower.
 template <int V>
 __global__ void __launch_bounds__(128, 4)
     k_surrogate_finish(const __grid_constant__ MechTables mt, const __grid_constant__ SurrogateConsts sc,
