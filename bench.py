@@ -335,8 +335,9 @@ MLP_FLOPS_PER_ROW = 2 * (16 * 256 + 256 * 256 * 2 + 256 * 16)  # padded 16-256-2
 # dram__bytes_write.sum), from an ncu capture of the 131,072-cell slice, scaled by the
 # cell count; to be set to None whenever the kernel changes until it is captured again.
 # fp64: 12.84 MB per 131,072-cell launch (mean of 4 launches of the current kernel);
-# mixed: 12.73 MB (mean of 4 launches of the current kernel)
-TRAFFIC_PER_CELL = {"fp64": 12.841984e6 / 131072, "mixed": 12.728064e6 / 131072}
+# mixed (32 warps per SM, spilling): 12.75 MB read + 7.75 MB written (spill lines evicted
+# from L2), mean of 4 launches of the current kernel
+TRAFFIC_PER_CELL = {"fp64": 12.841984e6 / 131072, "mixed": 20.507712e6 / 131072}
 
 
 def _bf16_peak():

@@ -9,8 +9,8 @@ namespace chem {
 
 // BLOCK threads per block, MINB resident blocks per SM.  The register file is split
 // between the SM's four sub-partitions, so 12 warps per SM allow 170 registers a thread
-// (128 x 3) and 16 warps 128 (64 x 8, 32 x 16); anything between rounds down to 128;
-// 8 warps (256 x 1) leave the 255-register maximum.
+// (128 x 3), 16 warps 128 (64 x 8, 32 x 16) and 32 warps 64 (64 x 16, 32 x 32); anything
+// between rounds down; 8 warps (256 x 1) leave the 255-register maximum.
 // SCH: CHEM_SCHEME_LSRK (the two-register scheme of Eq. 21) or one of the full-storage
 // comparators (cell_attempt_full).
 template <int V, int BLOCK, int MINB, int SCH = CHEM_SCHEME_LSRK>
@@ -68,12 +68,21 @@ __global__ void k_state_from_TPY(const __grid_constant__ MechTables mt, int64_t 
   e[i] = R_U * e_over_R(m, Ti);
 }
 
+// Blocks per SM of the 32- and 64-thread shapes.  The mixed two-register kernel of the
+// 9-species structure runs them at 32 warps per SM (64 registers, spilling to L1): the
+// FP64 pipe's latency is hidden by more warps rather than by registers, and the 1M-cell
+// detonation slice ran 3.8 % faster than at 16 warps (128 registers).  The fp64 variant
+// (fp64 state and rates), the full-storage comparators and the 13-species structure keep
+// 16 warps: the fp64 kernel measured 7 % slower at 32.
+template <int V, int SCH>
+constexpr int kDense = (V == CHEM_VARIANT_MIXED && SCH == CHEM_SCHEME_LSRK && NSP <= 9) ? 2 : 1;
+
 template <int V, int SCH>
 static void launch_shape(const MechTables &mt, const CellArgs &a, const StepParams &p, int block,
                          cudaStream_t s) {
   const unsigned grid = (unsigned)((a.n + block - 1) / block);
-  if (block == 32) k_lsrk<V, 32, 16, SCH><<<grid, 32, 0, s>>>(mt, a, p);
-  else if (block == 64) k_lsrk<V, 64, 8, SCH><<<grid, 64, 0, s>>>(mt, a, p);
+  if (block == 32) k_lsrk<V, 32, 16 * kDense<V, SCH>, SCH><<<grid, 32, 0, s>>>(mt, a, p);
+  else if (block == 64) k_lsrk<V, 64, 8 * kDense<V, SCH>, SCH><<<grid, 64, 0, s>>>(mt, a, p);
   else if (block == 256) k_lsrk<V, 256, 1, SCH><<<grid, 256, 0, s>>>(mt, a, p);
   else k_lsrk<V, 128, 3, SCH><<<grid, 128, 0, s>>>(mt, a, p);
 }
