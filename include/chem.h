@@ -252,7 +252,8 @@ typedef struct {
 /* Compiled shapes of the persistent kernel: (threads per CTA, minimum resident CTAs
  * per SM, hence a register cap of min(255, 65536 / (threads * CTAs))):
  * 0 = (128, 2) [default, no cap in effect], 1 = (128, 3), 2 = (128, 4), 3 = (64, 6),
- * 4 = (64, 8), 5 = (256, 2).  All run the same algorithm; the compiler contracts
+ * 4 = (64, 8) [(64, 16) for the mixed variant of the 9-species library], 5 = (256, 2).
+ * All run the same algorithm; the compiler contracts
  * multiply-adds per compiled kernel, so results of different shapes agree to rounding
  * (to the integration tolerance in ill-conditioned cells), not bit for bit.  Shape 0
  * gives the results of chem_integrate. */

@@ -90,7 +90,8 @@ cudaError_t launch_batched(int variant, const MechTables &mt, const BatchArgs &a
                            const StepParams &p, const BatchScratch &s, int order_mode,
                            int ctas_per_sm, int shape, cudaStream_t st);
 // The persistent kernel over a given queue of cell indices (order[0 .. queue length))
-// with the default shape and all resident CTAs; resets the cursor first.
+// with the variant's fastest shape (0 for fp64, the 32-warp shape 4 for mixed) and all
+// resident CTAs; resets the cursor first.
 cudaError_t launch_persistent_queue(int variant, const MechTables &mt, const BatchArgs &a,
                                     const StepParams &p, const int32_t *order,
                                     unsigned long long *cursor, cudaStream_t st);
