@@ -266,28 +266,29 @@ def oracle_config(name, smp, carry_h, budget_s, gpu_T=None):
 
 
 def cpu_baselines(args, reactors_state, amr_sample, sur_sample, bubble_sample):
-    """The oracle on every configuration (rank 0, N = 1): config 0 whole, configs 2-4 on
-    seeded stratified samples (extrapolated); config 1 is the headline cpu_baseline."""
+    """The oracle on every workload (rank 0, N = 1): the 4096 reactors whole; the AMR
+    batch, the surrogate's held-out cells and the shock-bubble field on seeded stratified
+    samples (extrapolated); the detonation slice is the headline cpu_baseline."""
     from chem_inputs import mechanism, workloads
     out = {}
     if reactors_state is not None:
         r = reactors_state
         smp = {"rho": r["rho"], "e": r["e"], "Y": r["Y"], "T": r["T"],
                "strata": [{"idx": np.arange(r["T"].size), "dt": 1e-7, "nsub": 1, "weight": r["T"].size}]}
-        out["config0_reactors"] = oracle_config("4096 reactors, dt 1e-7 s", smp, True, 10.0,
-                                                {"fp64": r["gpu_T"]})
+        out["reactors_4096"] = oracle_config("4096 reactors, dt 1e-7 s", smp, True, 10.0,
+                                            {"fp64": r["gpu_T"]})
     if amr_sample:
-        out["config2_amr_batch"] = oracle_config("AMR-like batch, 256 boxes, 3 levels", amr_sample, True, 15.0,
-                                                 {amr_sample["variant"]: amr_sample["gpu_T"]})
+        out["amr_batch_256_boxes"] = oracle_config("AMR-like batch, 256 boxes, 3 levels", amr_sample, True, 15.0,
+                                                  {amr_sample["variant"]: amr_sample["gpu_T"]})
     if sur_sample is not None:
         for dt in SUR_DTS:
             smp = dict(sur_sample)
             n = smp["T"].size if dt < 1e-7 else min(smp["T"].size, 16384)
             smp["strata"] = [{"idx": np.arange(n), "dt": dt, "nsub": 1, "weight": args.sur_cells}]
-            out[f"config3_surrogate_cells_dt={dt:g}"] = oracle_config(
+            out[f"surrogate_heldout_cells_dt={dt:g}"] = oracle_config(
                 f"held-out surrogate cells, dt {dt:g} s (uniform sample)", smp, True, 10.0)
     if bubble_sample is not None:
-        out["config4_shock_bubble"] = oracle_config(
+        out["shock_bubble_256cubed"] = oracle_config(
             "256^3 shock-bubble field, 4 levels, dt 1e-8 s", bubble_sample, False, 15.0,
             {"plain_fp64": bubble_sample["gpu_T_plain"], "hybrid": bubble_sample["gpu_T_hybrid"]})
     return out
@@ -1101,8 +1102,8 @@ def run_ours(args, rank, world, local):
     e2e_el, = max_over_ranks([e2e_el], world, dev)
     e2e_match = bool(np.array_equal(hY, res[head]["Y"]) and np.array_equal(hT, res[head]["T"]))
 
-    # config 0: 4096 independent reactors, dt 1e-7 s (the parity configuration): plain fp64
-    # one-pass launches, median of K; its state is the oracle's config-0 sample
+    # 4096 independent reactors, dt 1e-7 s (the parity workload): plain fp64 one-pass
+    # launches, median of K; the same states are the oracle's sample of this workload
     r0 = workloads.reactors(4096, seed=0)
     T0r = torch.tensor(r0["T"], dtype=torch.float64, device=dev)
     Y0r = torch.tensor(r0["Y"], dtype=torch.float64, device=dev)
@@ -1119,7 +1120,7 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         if k:
             ts0.append(a.elapsed_time(b_))
-    config0 = {"workload": "4096 reactors, phi U[0.5,2], T0 U[1000,2000] K, p U[0.5,5] atm, dt 1e-7 s",
+    reactors = {"workload": "4096 reactors, phi U[0.5,2], T0 U[1000,2000] K, p U[0.5,5] atm, dt 1e-7 s",
                "variant": "fp64", "ms": float(np.median(ts0)), "cells_per_s": 4096 / (float(np.median(ts0)) * 1e-3),
                "note": "4096 cells fill 32 of 152 SMs' worth of 128-thread blocks: latency, not throughput"}
     reactors_state = {"rho": rho_r.cpu().numpy(), "e": e_r.cpu().numpy(), "Y": r0["Y"], "T": r0["T"],
@@ -1188,7 +1189,7 @@ def run_ours(args, rank, world, local):
             "comparators": comparators,
             "znd_1d_strang": znd,
             "mech13": mech13,
-            "config0_reactors": config0,
+            "reactors_4096": reactors,
             "clocks": clk,
             "fma_probe": probe,
             "cpu_baseline": cpu,
