@@ -13,17 +13,6 @@
 
 namespace chem {
 
-// dZ (bf16) = dH * GELU'(Z) with dH fp32 [M x N] (ld), Z fp32 (ld)
-__global__ void k_gelu_backward(int64_t M, int N, const float *__restrict__ dH, int ldh,
-                                const float *__restrict__ Z, int ldz, __nv_bfloat16 *__restrict__ dZ,
-                                int lddz) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= M * N) return;
-  const int64_t m = idx / N;
-  const int n = (int)(idx % N);
-  dZ[m * lddz + n] = __float2bfloat16(dH[m * ldh + n] * gelu_grad_f(Z[m * ldz + n]));
-}
-
 // MSE over the first `nout` columns: loss += sum (y - t)^2 / (M nout); dY = 2 (y - t) / (M nout)
 // (bf16, padded columns zero).  loss is accumulated with one atomic per block.
 __global__ void k_mse(int64_t M, int nout, int ldy, const float *__restrict__ Y,
@@ -104,16 +93,19 @@ __global__ void k_adam(int64_t n, float *__restrict__ w, const float *__restrict
   }
 }
 
-// Adam with the step's learning rate and bias corrections read from a device schedule:
-// sched[3 t .. 3 t + 2] = {lr, 1 - b1^(t+1), 1 - b2^(t+1)} at t = *step (a CUDA graph of one
-// training step replays with the counter advancing on the device).
-__global__ void k_adam_sched(int64_t n, float *__restrict__ w, const float *__restrict__ g,
-                             float *__restrict__ m, float *__restrict__ v, const float *__restrict__ sched,
-                             const int64_t *__restrict__ step, float b1, float b2, float eps,
-                             __nv_bfloat16 *__restrict__ w_bf, __nv_bfloat16 *__restrict__ wT_bf, int rows,
-                             int cols) {
+// Adam on every parameter (the segments of AdamSegs) with the step's learning rate and
+// bias corrections read from a device schedule: sched[3 t .. 3 t + 2] = {lr, 1 - b1^(t+1),
+// 1 - b2^(t+1)} at t = *step (a CUDA graph of one training step replays with the counter
+// advancing on the device).
+__global__ void k_adam_sched_all(int64_t n, float *__restrict__ w, const float *__restrict__ g,
+                                 float *__restrict__ m, float *__restrict__ v, const float *__restrict__ sched,
+                                 const int64_t *__restrict__ step, float b1, float b2, float eps,
+                                 const __grid_constant__ AdamSegs sg) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  int j = 0;
+  while (j < kAdamSegs - 1 && i >= sg.end[j]) ++j;
+  const int64_t li = i - (j ? sg.end[j - 1] : 0);
   const float *sc = sched + 3 * *step;
   const float lr = sc[0], bc1 = sc[1], bc2 = sc[2];
   const float gi = g[i];
@@ -123,10 +115,10 @@ __global__ void k_adam_sched(int64_t n, float *__restrict__ w, const float *__re
   v[i] = vi;
   const float wi = w[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
   w[i] = wi;
-  if (w_bf) w_bf[i] = __float2bfloat16(wi);
-  if (wT_bf) {
-    const int64_t r = i / cols, c = i % cols;
-    wT_bf[c * rows + r] = __float2bfloat16(wi);
+  if (sg.w_bf[j]) sg.w_bf[j][li] = __float2bfloat16(wi);
+  if (sg.wT_bf[j]) {
+    const int64_t r = li / sg.cols[j], c = li % sg.cols[j];
+    sg.wT_bf[j][c * sg.rows[j] + r] = __float2bfloat16(wi);
   }
 }
 
@@ -166,11 +158,6 @@ __global__ void k_to_bf16(int64_t n, const float *__restrict__ in, __nv_bfloat16
 
 static unsigned blocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
-cudaError_t launch_gelu_backward(int64_t M, int N, const float *dH, int ldh, const float *Z, int ldz,
-                                 __nv_bfloat16 *dZ, int lddz, cudaStream_t s) {
-  k_gelu_backward<<<blocks(M * N, 256), 256, 0, s>>>(M, N, dH, ldh, Z, ldz, dZ, lddz);
-  return cudaGetLastError();
-}
 cudaError_t launch_mse(int64_t M, int nout, int ldy, const float *Y, const float *Tg, int ldt,
                        __nv_bfloat16 *dY, int lddy, float *loss, cudaStream_t s) {
   k_mse<<<blocks(M * lddy, 256), 256, 0, s>>>(M, nout, ldy, Y, Tg, ldt, dY, lddy, loss);
@@ -200,10 +187,10 @@ cudaError_t launch_gather_rows(int64_t nrows, int ncol, const int32_t *idx, cons
   k_gather_rows<<<blocks(nrows * ncol, 256), 256, 0, s>>>(nrows, ncol, idx, in, ldin, out, ldout);
   return cudaGetLastError();
 }
-cudaError_t launch_adam_sched(int64_t n, float *w, const float *g, float *m, float *v, const float *sched,
-                              const int64_t *step, float b1, float b2, float eps, __nv_bfloat16 *w_bf,
-                              __nv_bfloat16 *wT_bf, int rows, int cols, cudaStream_t s) {
-  k_adam_sched<<<blocks(n, 256), 256, 0, s>>>(n, w, g, m, v, sched, step, b1, b2, eps, w_bf, wT_bf, rows, cols);
+cudaError_t launch_adam_sched_all(int64_t n, float *w, const float *g, float *m, float *v, const float *sched,
+                                  const int64_t *step, float b1, float b2, float eps, const AdamSegs &segs,
+                                  cudaStream_t s) {
+  k_adam_sched_all<<<blocks(n, 256), 256, 0, s>>>(n, w, g, m, v, sched, step, b1, b2, eps, segs);
   return cudaGetLastError();
 }
 cudaError_t launch_gather_rows_step(int64_t nrows, int ncol, const int32_t *idx, const int64_t *step,

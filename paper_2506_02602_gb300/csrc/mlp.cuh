@@ -32,11 +32,13 @@ struct GemmArgs {
   int split;
   int64_t split_ld;
   int *err;  // nullable device word: set to 1 if a bounded wait of the kernel ran out
+  // nullable: Cb receives bf16(x * GELU'(dgelu_z[m * ldz + n])) instead of bf16(x) or
+  // bf16(GELU(x)) (the backward pass's dZ = dH * GELU'(Z), fused into the dH GEMM)
+  const float *dgelu_z;
+  int64_t ldz;
 };
 
 cudaError_t launch_gemm(const GemmArgs &g, cudaStream_t s);
-cudaError_t launch_gelu_backward(int64_t M, int N, const float *dH, int ldh, const float *Z, int ldz,
-                                 __nv_bfloat16 *dZ, int lddz, cudaStream_t s);
 cudaError_t launch_mse(int64_t M, int nout, int ldy, const float *Y, const float *Tg, int ldt,
                        __nv_bfloat16 *dY, int lddy, float *loss, cudaStream_t s);
 cudaError_t launch_reduce_splits(int64_t n, int nsplit, const float *part, int64_t split_ld,
@@ -53,9 +55,19 @@ cudaError_t launch_gather_rows(int64_t nrows, int ncol, const int32_t *idx, cons
 cudaError_t launch_to_bf16(int64_t n, const float *in, __nv_bfloat16 *out, cudaStream_t s);
 // The device-scheduled pieces of a graph-captured training step: Adam with {lr, 1 - b1^t,
 // 1 - b2^t} read from sched[3 * (*step)], the batch gather of step *step, the counter.
-cudaError_t launch_adam_sched(int64_t n, float *w, const float *g, float *m, float *v, const float *sched,
-                              const int64_t *step, float b1, float b2, float eps, __nv_bfloat16 *w_bf,
-                              __nv_bfloat16 *wT_bf, int rows, int cols, cudaStream_t s);
+// One Adam launch over every parameter of the network: segment j covers
+// [end[j - 1], end[j]) of w, g, m, v (end[-1] = 0); a weight segment also writes its bf16
+// copy w_bf (rows x cols, k contiguous) and transpose wT_bf (null for the biases).
+constexpr int kAdamSegs = 8;  // a weight and a bias segment per layer
+struct AdamSegs {
+  int64_t end[kAdamSegs];
+  __nv_bfloat16 *w_bf[kAdamSegs];
+  __nv_bfloat16 *wT_bf[kAdamSegs];
+  int rows[kAdamSegs], cols[kAdamSegs];
+};
+cudaError_t launch_adam_sched_all(int64_t n, float *w, const float *g, float *m, float *v, const float *sched,
+                                  const int64_t *step, float b1, float b2, float eps, const AdamSegs &segs,
+                                  cudaStream_t s);
 cudaError_t launch_gather_rows_step(int64_t nrows, int ncol, const int32_t *idx, const int64_t *step,
                                     int64_t nbatch, const float *in, int ldin, float *out, int ldout,
                                     cudaStream_t s);

@@ -14,7 +14,7 @@
 // tensor cores work on chunk c; a stage is refilled once the commit of the MMAs that read
 // it has arrived.  Epilogue: each warp reads 32 accumulator lanes (its lane quarter,
 // tcgen05.ld 32x32b) for a quarter of the columns and applies alpha, bias, accumulation
-// into Cf, GELU and the FP32 / BF16 stores.
+// into Cf, GELU (or the product with GELU' of a given Z) and the FP32 / BF16 stores.
 //
 // Every mbarrier wait is bounded; a wait that runs out sets *err (when given), the CTA
 // issues nothing more, and still frees its tensor memory.
@@ -242,7 +242,9 @@ __device__ __forceinline__ void gemm_body(const GemmTc &p, unsigned char *sm, ui
             x += bn;
             if (g.accumulate) x += g.Cf[m * g.ldc + n];
             if (g.Cf) g.Cf[m * g.ldc + n] = x;
-            if (g.Cb) g.Cb[m * g.ldcb + n] = __float2bfloat16(g.gelu ? gelu_f(x) : x);
+            if (g.Cb)
+              g.Cb[m * g.ldcb + n] = __float2bfloat16(g.dgelu_z ? x * gelu_grad_f(g.dgelu_z[m * g.ldz + n])
+                                                               : (g.gelu ? gelu_f(x) : x));
           }
         }
         __syncwarp();

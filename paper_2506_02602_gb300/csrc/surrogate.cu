@@ -221,6 +221,8 @@ static cudaError_t layer_forward(Surrogate *s, int l, int64_t M, const __nv_bflo
 // Split-K factor of the weight-gradient GEMMs (the batch is their reduction dimension)
 // and the row slices of the bias-gradient sums.
 constexpr int kGradSplit = 16;
+// Training steps per replayed CUDA graph (the host launches one graph per this many steps).
+constexpr int kGraphSteps = 8;
 
 struct TrainBufs {
   float *Xb = nullptr, *Tb = nullptr, *Y = nullptr, *loss = nullptr, *part = nullptr;
@@ -301,16 +303,18 @@ static cudaError_t forward_backward(Surrogate *s, TrainBufs &b, int64_t B, cudaS
     SCHK(launch_bias_grad(B, N, G, N, b.part, kGradSplit, s->grad + s->off_b[l], st));
     if (l == 0) break;
     // dHin[m, k] = sum_n G[m, n] W[n, k] (W^T stored [K x N])
+    // and in the same epilogue G for layer l-1: dZ = dHin * GELU'(Z_{l-1}) (bf16); the fp32
+    // dHin itself is stored only for a trace
     GemmArgs gx{};
     gx.M = B; gx.N = K; gx.K = N;
     gx.A = G; gx.sam = N; gx.sak = 1;
     gx.B = s->WT[l]; gx.sbn = N; gx.sbk = 1;
     gx.alpha = 1.0f;
-    gx.Cf = b.dH; gx.ldc = K;
+    gx.Cf = (tr && tr->dH) ? b.dH : nullptr; gx.ldc = K;
+    gx.Cb = b.dZ; gx.ldcb = K;
+    gx.dgelu_z = b.Z[l - 1]; gx.ldz = K;
     gx.err = s->tc_err;
     SCHK(launch_gemm(gx, st));
-    // G for layer l-1: dZ = dHin * GELU'(Z_{l-1})
-    SCHK(launch_gelu_backward(B, K, b.dH, K, b.Z[l - 1], K, b.dZ, K, st));
     if (tr) {
       SCHK(trace_copy(tr->dH ? tr->dH + (l - 1) * slab : nullptr, b.dH, slab * sizeof(float), st));
       SCHK(trace_copy(tr->G ? tr->G + (l - 1) * slab : nullptr, b.dZ, slab * sizeof(__nv_bfloat16), st));
@@ -658,11 +662,11 @@ int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
   if (e == cudaSuccess) e = launch_normalize(n, kSurFeat, kSurIn, X, s->dev_norm, s->dev_norm + 16, nullptr, st);
   if (e == cudaSuccess) e = launch_normalize(n, NSP, kSurOut, Tg, s->dev_norm + 32, s->dev_norm + 48, nullptr, st);
   if (e != cudaSuccess) { cleanup(); return sur_cuda(ctx, e, "normalising"); }
-  // epochs of shuffled batches.  One training step (the batch gather, forward, loss,
-  // backward, Adam) is captured once as a CUDA graph on a private stream and replayed
-  // for every batch: the batch offset, the learning rate of the cosine schedule and
-  // Adam's bias corrections come from a step counter on the device and a schedule table
-  // computed here, so the replays need no host arguments.
+  // epochs of shuffled batches.  The training step (the batch gather, forward, loss,
+  // backward, Adam) is captured as CUDA graphs on a private stream, of one step and of
+  // kGraphSteps steps, and replayed for every batch: the batch offset, the learning rate
+  // of the cosine schedule and Adam's bias corrections come from a step counter on the
+  // device and a schedule table computed here, so the replays need no host arguments.
   const int64_t nb = n / B;
   const int64_t total = nb * cfg.epochs;
   std::vector<float> hsched((size_t)(3 * (total > 0 ? total : 1)));
@@ -679,15 +683,16 @@ int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
   int32_t *hperm = nullptr;  // pinned staging of the permutations, two slots
   float *hloss = nullptr;    // pinned per-epoch loss sums
   cudaStream_t ps = nullptr;
-  cudaGraph_t graph[2] = {nullptr, nullptr};
-  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaGraph_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t up_done[2] = {nullptr, nullptr};
   auto release_graph = [&]() {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 4; ++i) {
       if (exec[i]) cudaGraphExecDestroy(exec[i]);
       if (graph[i]) cudaGraphDestroy(graph[i]);
-      if (up_done[i]) cudaEventDestroy(up_done[i]);
     }
+    for (int i = 0; i < 2; ++i)
+      if (up_done[i]) cudaEventDestroy(up_done[i]);
     if (ps) cudaStreamDestroy(ps);
     cudaFree(dsched);
     cudaFree(dstep);
@@ -707,26 +712,39 @@ int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
   if (e == cudaSuccess) e = gemm_prepare();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // features and statistics are done
   int32_t *idxs[2] = {idx, idx2};
-  for (int gi = 0; gi < 2 && e == cudaSuccess && total > 0; ++gi) {
-    e = cudaStreamBeginCapture(ps, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) break;
+  static_assert(kAdamSegs == 2 * kSurLayers, "one weight and one bias segment per layer");
+  AdamSegs sg{};  // Adam on every parameter in one launch (the layout W0 b0 W1 b1 ...)
+  for (int l = 0; l < kSurLayers; ++l) {
+    sg.end[2 * l] = s->off_b[l];
+    sg.end[2 * l + 1] = s->off_b[l] + kSurN[l];
+    sg.w_bf[2 * l] = s->W[l];
+    sg.wT_bf[2 * l] = s->WT[l];
+    sg.rows[2 * l] = kSurN[l];
+    sg.cols[2 * l] = kSurK[l];
+    sg.rows[2 * l + 1] = 1;
+    sg.cols[2 * l + 1] = kSurN[l];
+  }
+  auto capture_step = [&](int gi) {
     cudaError_t ce = launch_gather_rows_step(B, kSurIn, idxs[gi], dstep, nb, X, kSurIn, b.Xb, kSurIn, ps);
     if (ce == cudaSuccess) ce = launch_gather_rows_step(B, kSurOut, idxs[gi], dstep, nb, Tg, kSurOut, b.Tb, kSurOut, ps);
     if (ce == cudaSuccess) ce = forward_backward(s, b, B, ps);
-    for (int l = 0; l < kSurLayers && ce == cudaSuccess; ++l) {
-      const int64_t nw = (int64_t)kSurN[l] * kSurK[l];
-      ce = launch_adam_sched(nw, s->param + s->off_W[l], s->grad + s->off_W[l], s->m + s->off_W[l],
-                             s->v + s->off_W[l], dsched, dstep, 0.9f, 0.999f, 1e-8f, s->W[l], s->WT[l], kSurN[l],
-                             kSurK[l], ps);
-      if (ce == cudaSuccess)
-        ce = launch_adam_sched(kSurN[l], s->param + s->off_b[l], s->grad + s->off_b[l], s->m + s->off_b[l],
-                               s->v + s->off_b[l], dsched, dstep, 0.9f, 0.999f, 1e-8f, nullptr, nullptr, 1,
-                               kSurN[l], ps);
-    }
+    if (ce == cudaSuccess)
+      ce = launch_adam_sched_all(kSurParams, s->param, s->grad, s->m, s->v, dsched, dstep, 0.9f, 0.999f, 1e-8f, sg,
+                                 ps);
     if (ce == cudaSuccess) ce = launch_step_inc(dstep, ps);
-    e = cudaStreamEndCapture(ps, &graph[gi]);
+    return ce;
+  };
+  // graph g = gi (one step) and g = 2 + gi (kGraphSteps steps) for permutation buffer gi:
+  // an epoch replays the long graph nb / kGraphSteps times and the short one for the rest,
+  // so the host launches a graph per kGraphSteps steps, not per step
+  for (int g = 0; g < 4 && e == cudaSuccess && total > 0; ++g) {
+    e = cudaStreamBeginCapture(ps, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) break;
+    cudaError_t ce = cudaSuccess;
+    for (int k = 0; k < (g < 2 ? 1 : kGraphSteps) && ce == cudaSuccess; ++k) ce = capture_step(g & 1);
+    e = cudaStreamEndCapture(ps, &graph[g]);
     if (e == cudaSuccess) e = ce;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec[gi], graph[gi], 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec[g], graph[g], 0);
   }
   // the host shuffles epoch ep + 1 while the GPU replays epoch ep: permutations alternate
   // between two device buffers (one graph each) and two pinned staging slots
@@ -743,7 +761,9 @@ int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
   for (int ep = 0; ep < cfg.epochs && e == cudaSuccess; ++ep) {
     const int cur = ep & 1, nxt = cur ^ 1;
     e = cudaMemsetAsync(b.loss, 0, sizeof(float), ps);
-    for (int64_t bi = 0; bi < nb && e == cudaSuccess; ++bi) e = cudaGraphLaunch(exec[cur], ps);
+    for (int64_t bi = 0; bi + kGraphSteps <= nb && e == cudaSuccess; bi += kGraphSteps)
+      e = cudaGraphLaunch(exec[2 + cur], ps);
+    for (int64_t bi = nb - nb % kGraphSteps; bi < nb && e == cudaSuccess; ++bi) e = cudaGraphLaunch(exec[cur], ps);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hloss + ep, b.loss, sizeof(float), cudaMemcpyDeviceToHost, ps);
     if (e == cudaSuccess && ep + 1 < cfg.epochs) {
       // the staging slot of epoch ep + 1 was last copied for epoch ep - 1
