@@ -231,20 +231,37 @@ __device__ __forceinline__ void gemm_body(const GemmTc &p, unsigned char *sm, ui
         const int64_t n = n0 + cb + lane;
         if (lane < CW && n < g.N) {
           const float bn = (g.bias && g.split <= 1) ? g.bias[n] : 0.0f;
-          for (int rr = 0; rr < 32; ++rr) {
-            const int64_t m = m0 + 32 * q + rr;
-            if (m >= g.M) break;
-            float x = tp[rr * 33 + lane] * g.alpha;
-            if (g.split > 1) {
-              g.Cf[(int64_t)blockIdx.z * g.split_ld + m * g.ldc + n] = x;
-              continue;
+          const int64_t mq = m0 + 32 * q;
+          if (g.split > 1) {
+            for (int rr = 0; rr < 32 && mq + rr < g.M; ++rr)
+              g.Cf[(int64_t)blockIdx.z * g.split_ld + (mq + rr) * g.ldc + n] = tp[rr * 33 + lane] * g.alpha;
+          } else if (g.dgelu_z) {
+            // the 32 rows' Z first, all loads in flight together, then the products
+            float z[32];
+#pragma unroll
+            for (int rr = 0; rr < 32; ++rr)
+              z[rr] = mq + rr < g.M ? __ldg(g.dgelu_z + (mq + rr) * g.ldz + n) : 0.0f;
+#pragma unroll
+            for (int rr = 0; rr < 32; ++rr) {
+              if (mq + rr < g.M) {
+                const int64_t m = mq + rr;
+                float x = tp[rr * 33 + lane] * g.alpha;
+                x += bn;
+                if (g.accumulate) x += g.Cf[m * g.ldc + n];
+                if (g.Cf) g.Cf[m * g.ldc + n] = x;
+                if (g.Cb) g.Cb[m * g.ldcb + n] = __float2bfloat16(x * gelu_grad_f(z[rr]));
+              }
             }
-            x += bn;
-            if (g.accumulate) x += g.Cf[m * g.ldc + n];
-            if (g.Cf) g.Cf[m * g.ldc + n] = x;
-            if (g.Cb)
-              g.Cb[m * g.ldcb + n] = __float2bfloat16(g.dgelu_z ? x * gelu_grad_f(g.dgelu_z[m * g.ldz + n])
-                                                               : (g.gelu ? gelu_f(x) : x));
+          } else {
+            for (int rr = 0; rr < 32; ++rr) {
+              const int64_t m = mq + rr;
+              if (m >= g.M) break;
+              float x = tp[rr * 33 + lane] * g.alpha;
+              x += bn;
+              if (g.accumulate) x += g.Cf[m * g.ldc + n];
+              if (g.Cf) g.Cf[m * g.ldc + n] = x;
+              if (g.Cb) g.Cb[m * g.ldcb + n] = __float2bfloat16(g.gelu ? gelu_f(x) : x);
+            }
           }
         }
         __syncwarp();
