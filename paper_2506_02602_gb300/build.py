@@ -28,7 +28,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v
 # One library per compiled mechanism structure (csrc/mech_*.cuh): the 9-species /
 # 21-reaction mechanism with the learned surrogate, and the 13-species / 27-reaction one
 # (the paper's mechanism size) whose surrogate entry points are stubs.
-_SURROGATE = ("mlp.cu", "mlp_fused.cu", "mlp_tc.cu", "surrogate.cu", "surrogate_kernels.cu")
+_SURROGATE = ("mlp.cu", "mlp_fused.cu", "mlp_tc.cu", "mlp_gemm_tc.cu", "surrogate.cu", "surrogate_kernels.cu")
 LIBS = {
     "h2o2_9": {"lib": LIB, "defines": [], "skip": ("surrogate_stub.cu",), "build": BUILD},
     "h2o2_13": {"lib": os.path.join(PKG, "libchem_h2o2_13.so"), "defines": ["-DCHEM_MECH_H2O2_13"],

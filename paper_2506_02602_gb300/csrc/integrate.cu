@@ -68,14 +68,14 @@ __global__ void k_state_from_TPY(const __grid_constant__ MechTables mt, int64_t 
   e[i] = R_U * e_over_R(m, Ti);
 }
 
-// Blocks per SM of the 32- and 64-thread shapes.  The mixed two-register kernel of the
-// 9-species structure runs them at 32 warps per SM (64 registers, spilling to L1): the
-// FP64 pipe's latency is hidden by more warps rather than by registers, and the 1M-cell
-// detonation slice ran 3.8 % faster than at 16 warps (128 registers).  The fp64 variant
-// (fp64 state and rates), the full-storage comparators and the 13-species structure keep
-// 16 warps: the fp64 kernel measured 7 % slower at 32.
+// Blocks per SM of the 32- and 64-thread shapes.  The mixed two-register kernel runs them
+// at 32 warps per SM (64 registers, spilling to L1 and L2): the FP64 pipe's latency is
+// hidden by more warps rather than by registers, and the 1M-cell detonation slice ran
+// 3.8 % faster than at 16 warps (128 registers) with the 9-species structure, 4.3 % with
+// the 13-species one.  The fp64 variant (fp64 state and rates) and the full-storage
+// comparators keep 16 warps: the fp64 kernel measured 7 % slower at 32.
 template <int V, int SCH>
-constexpr int kDense = (V == CHEM_VARIANT_MIXED && SCH == CHEM_SCHEME_LSRK && NSP <= 9) ? 2 : 1;
+constexpr int kDense = (V == CHEM_VARIANT_MIXED && SCH == CHEM_SCHEME_LSRK) ? 2 : 1;
 
 template <int V, int SCH>
 static void launch_shape(const MechTables &mt, const CellArgs &a, const StepParams &p, int block,
