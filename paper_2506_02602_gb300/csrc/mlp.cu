@@ -139,17 +139,6 @@ __global__ void k_step_inc(int64_t *step) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *step += 1;
 }
 
-// out[r, :] = in[idx[r], :] for ncol columns (float)
-__global__ void k_gather_rows(int64_t nrows, int ncol, const int32_t *__restrict__ idx,
-                              const float *__restrict__ in, int ldin, float *__restrict__ out,
-                              int ldout) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nrows * ncol) return;
-  const int64_t r = t / ncol;
-  const int c = (int)(t % ncol);
-  out[r * ldout + c] = in[(int64_t)idx[r] * ldin + c];
-}
-
 // bf16 copy of a float matrix (for the gathered input features)
 __global__ void k_to_bf16(int64_t n, const float *__restrict__ in, __nv_bfloat16 *__restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -180,11 +169,6 @@ cudaError_t launch_adam(int64_t n, float *w, const float *g, float *m, float *v,
                         int rows, int cols, cudaStream_t s) {
   const float bc1 = 1.0f - powf(b1, (float)step), bc2 = 1.0f - powf(b2, (float)step);
   k_adam<<<blocks(n, 256), 256, 0, s>>>(n, w, g, m, v, lr, b1, b2, eps, bc1, bc2, w_bf, wT_bf, rows, cols);
-  return cudaGetLastError();
-}
-cudaError_t launch_gather_rows(int64_t nrows, int ncol, const int32_t *idx, const float *in, int ldin,
-                               float *out, int ldout, cudaStream_t s) {
-  k_gather_rows<<<blocks(nrows * ncol, 256), 256, 0, s>>>(nrows, ncol, idx, in, ldin, out, ldout);
   return cudaGetLastError();
 }
 cudaError_t launch_adam_sched_all(int64_t n, float *w, const float *g, float *m, float *v, const float *sched,

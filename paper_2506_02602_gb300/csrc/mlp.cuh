@@ -50,8 +50,6 @@ cudaError_t launch_bias_grad(int64_t M, int N, const __nv_bfloat16 *dZ, int ld, 
 cudaError_t launch_adam(int64_t n, float *w, const float *g, float *m, float *v, float lr, float b1,
                         float b2, float eps, int step, __nv_bfloat16 *w_bf, __nv_bfloat16 *wT_bf,
                         int rows, int cols, cudaStream_t s);
-cudaError_t launch_gather_rows(int64_t nrows, int ncol, const int32_t *idx, const float *in,
-                               int ldin, float *out, int ldout, cudaStream_t s);
 cudaError_t launch_to_bf16(int64_t n, const float *in, __nv_bfloat16 *out, cudaStream_t s);
 // The device-scheduled pieces of a graph-captured training step: Adam with {lr, 1 - b1^t,
 // 1 - b2^t} read from sched[3 * (*step)], the batch gather of step *step, the counter.
