@@ -399,7 +399,8 @@ int chem_surrogate_train(chem_ctx *ctx, const chem_pairs *pairs, int64_t npairs,
  * Advance the state over dt with the surrogate (chem_state as in chem_integrate).  Per
  * cell: features -> network -> inverse transform -> fp64 projection -> fp64 temperature
  * -> gate (feature range, element residual, negativity, temperature solve, |dT|) ->
- * error test: with the integrator's right-hand side at Y0, Y1 and the Hermite midpoint
+ * error test: with the integrator's right-hand side (evaluated in fp32: an estimator)
+ * at Y0, Y1 and the Hermite midpoint
  * Ym = (Y0 + Y1)/2 + dt/8 (F0 - F1), Simpson's defect D = Y1 - Y0 - dt/6 (F0 + 4 Fm + F1)
  * gives the temperature-error estimate sum_k |u_k(T1) - e| |D_k| / c_v(T1), which must
  * not exceed err_tol * T1 (u_k the species internal energies per mass) times
@@ -443,7 +444,7 @@ int chem_surrogate_infer_batched(chem_ctx *ctx, const chem_state *state, int64_t
                                  const chem_surrogate_gate *gate, void *stream,
                                  uint8_t *d_fallback_mask, chem_stats *d_stats);
 
-/* Write / read the trained network (parameters, Box-Cox lambda, normalisation and/* Write / read the trained network (parameters, Box-Cox lambda, normalisation and
+/* Write / read the trained network (parameters, Box-Cox lambda, normalisation and
  * feature ranges) to / from a binary file.  Synchronous.  Errors: I/O -> CHEM_ERR_INVALID;
  * save without a network -> CHEM_ERR_STATE. */
 int chem_surrogate_save(chem_ctx *ctx, const char *path);
@@ -506,7 +507,6 @@ int chem_surrogate_project(chem_ctx *ctx, int64_t n, const double *d_Y0, const d
                            int64_t ldY, double *d_Yout, void *stream);
 
 /*
- * The network alone on B rows/*
  * The network alone on B rows (a check of the kernels; not a call of the paper's
  * method): d_X [B x 16] normalised features (fp32 device), d_Y [B x 16] outputs (fp32
  * device, out; columns 9..15 zero).  impl: 0 = the kernel inference uses (tcgen05
