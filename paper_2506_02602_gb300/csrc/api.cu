@@ -431,7 +431,8 @@ int chem_integrate_batched(chem_ctx *ctx, const chem_state *state, int64_t ncell
   if (rc) return rc;
   BatchArgs a{state->d_rho, state->d_e, state->d_Y, state->ldY, state->d_T, state->d_h,
               state->d_status, state->d_nsteps, ncells, batch->d_box_offset, batch->d_box_dt,
-              batch->d_box_nsub, batch->nboxes, o.d_cost_hint, d_stats};
+              batch->d_box_nsub, batch->nboxes, o.d_cost_hint, d_stats,
+              /*nq_dev=*/nullptr, /*ok_status=*/CHEM_CELL_OK};
   StepParams p{0.0, rtol, atol, ctx->opt.max_steps};
   auto issue = [&](cudaStream_t st) -> cudaError_t {
     if (d_stats) {

@@ -407,7 +407,8 @@ extern "C" int chem_integrate_batched_noalloc(chem_ctx *ctx, const chem_state *s
   sc.bucket = reinterpret_cast<uint8_t *>(b + 512 + kNoAllocMaxCells * sizeof(int32_t));
   BatchArgs a{state->d_rho, state->d_e, state->d_Y, state->ldY, state->d_T, state->d_h,
               state->d_status, state->d_nsteps, ncells, batch->d_box_offset, batch->d_box_dt,
-              batch->d_box_nsub, batch->nboxes, o.d_cost_hint, d_stats};
+              batch->d_box_nsub, batch->nboxes, o.d_cost_hint, d_stats,
+              /*nq_dev=*/nullptr, /*ok_status=*/CHEM_CELL_OK};
   StepParams p{0.0, rtol, atol, chem_ctx_max_steps(ctx)};
   // launch_batched clears the bucket counts (cudaMemsetAsync) and resets the cursor
   // (k_scan, or cudaMemsetAsync in natural order) before the kernels read them
