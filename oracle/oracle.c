@@ -594,6 +594,8 @@ int32_t oracle_integrate_scheme(int32_t scheme, const omech *m, int64_t n, const
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 8)
+#else
+  (void)nthreads;
 #endif
   for (int64_t i = 0; i < n; ++i) {
     double X[OR_MAXN];
