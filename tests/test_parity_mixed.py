@@ -110,7 +110,8 @@ def test_detonation_slice_mixed_vs_fp64_full_grid(ctx):
 @pytest.mark.parametrize("variant", ["mixed", "fp64"])
 def test_one_pass_shapes_agree(variant):
     """The one-pass kernel's compiled shapes (block_size 32, 64: 16 warps per SM at 128
-    registers; 128: 12 warps) run the same arithmetic: the same cell outcomes as the
+    registers for fp64, 32 warps at 64 registers for mixed; 128: 12 warps) run the same
+    arithmetic: the same cell outcomes as the
     oracle, and agreement to rounding in 99 % of the cells (multiply-adds may contract
     differently by shape; the rest are reactors igniting within the step, where a
     rounding-seeded change of the step sequence moves the ignition time)."""
