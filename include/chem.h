@@ -125,7 +125,8 @@ typedef struct {
   int32_t variant;     /* chem_variant [CHEM_VARIANT_FP64] */
   int32_t max_steps;   /* attempted-step limit per cell and call [100000] */
   int32_t block_size;  /* threads per block of the one-pass integration kernel: 32 or 64
-                          (16 warps per SM, 128 registers a thread), 128 (12 warps,
+                          (16 warps per SM, 128 registers a thread; 32 warps at 64
+                          registers for the mixed two-register scheme), 128 (12 warps,
                           170 registers) or 256 (8 warps, 255 registers); other values
                           take 128 [0: 64 for the mixed variant, 128 for fp64] */
   int32_t scheme;      /* chem_scheme [CHEM_SCHEME_LSRK]; the comparators serve
